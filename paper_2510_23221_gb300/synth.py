@@ -1,0 +1,213 @@
+"""Seeded synthetic layered-chip workloads.
+
+This module only draws inputs: chip geometry and materials, power-density
+maps and combination coefficients.  It holds none of the method's arithmetic
+(no conductances, no right-hand sides, no solves), so both the CUDA path and
+the FP64 CPU oracle may use it.
+
+The paper's own matrices come from FEM meshes of hand-made floorplans
+(Sec. V-A) that are not available; these layered chips stand in for them.
+Recipe (all distributions seeded through ``numpy.random.default_rng``):
+
+* cell size 100 um x 100 um laterally, 50 um per layer, one cell per layer;
+* 32x32x4 reference stack: silicon k=150, TIM k=5, spreader k=400,
+  substrate k=20 W/m/K (top to bottom), top convective h=1e4 W/m^2/K at
+  300 K, every other face adiabatic;
+* other stacks draw each layer's k log-uniform in [1, 400] W/m/K;
+* power maps live on the top (silicon) layer, in W/m^2: either a sum of 1-5
+  rectangles of uniform density (sides uniform in 1..n/2 cells, density
+  log-uniform in [1e5, 1e7]) or one Gaussian hotspot (amplitude log-uniform
+  in [1e5, 1e7], sigma uniform in [2, 16] cells, centre uniform);
+* combination coefficients C ~ N(0, 1), rounded to the nearest bfloat16
+  value (round-half-even) so that every consumer sees the same exact operand.
+
+Seeds: chip j of workload c uses ``1_000_000 * c + j``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+CELL_DX = 100e-6
+CELL_DY = 100e-6
+CELL_DZ = 50e-6
+T_AMBIENT = 300.0
+
+
+@dataclass
+class Chip:
+    """One layered chip on a structured nx x ny x nz grid (z = 0 is the top)."""
+
+    nx: int
+    ny: int
+    layer_nz: np.ndarray          # int32 [n_layers]: cells per layer along z
+    layer_dz: np.ndarray          # float64 [n_layers]: thickness of one cell, m
+    layer_k: np.ndarray           # float64 [n_layers]: conductivity, W/m/K
+    dx: float = CELL_DX
+    dy: float = CELL_DY
+    h_top: float = 1e4            # W/m^2/K, 0 = adiabatic
+    h_bottom: float = 0.0
+    h_side: float = 0.0
+    t_ambient: float = T_AMBIENT
+    k_cell: Optional[np.ndarray] = None   # float64 [nz][ny][nx] overrides layer_k
+
+    @property
+    def nz(self) -> int:
+        return int(np.sum(self.layer_nz))
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def cell_dz(self) -> np.ndarray:
+        """Thickness of every z-row of cells (float64 [nz])."""
+        return np.repeat(np.asarray(self.layer_dz, np.float64),
+                         np.asarray(self.layer_nz, np.int64))
+
+    def cell_k(self) -> np.ndarray:
+        """Per-cell conductivity as float64 [nz][ny][nx]."""
+        if self.k_cell is not None:
+            return np.asarray(self.k_cell, np.float64).reshape(self.nz, self.ny, self.nx)
+        kz = np.repeat(np.asarray(self.layer_k, np.float64),
+                       np.asarray(self.layer_nz, np.int64))
+        return np.broadcast_to(kz[:, None, None], (self.nz, self.ny, self.nx)).copy()
+
+
+@dataclass
+class Workload:
+    """Chips, their power maps and combination coefficients."""
+
+    name: str
+    chips: List[Chip]
+    density: List[np.ndarray]     # per chip float64 [s][ny][nx], W/m^2 on the top layer
+    coeffs: List[np.ndarray]      # per chip float64 [s][M], bfloat16-exact
+    s: int
+    M: int
+    rtol: float
+    extra: dict = field(default_factory=dict)
+
+
+def round_to_bf16(x: np.ndarray) -> np.ndarray:
+    """Round float64 values to the nearest bfloat16 value (ties to even).
+
+    bfloat16 keeps 8 significant bits; frexp gives a mantissa in [0.5, 1),
+    so scaling by 2**8 and rounding half-to-even keeps exactly 8 bits.
+    """
+    x = np.asarray(x, np.float64)
+    m, e = np.frexp(x)
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+def _log_uniform(rng, lo, hi, size=None):
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), size))
+
+
+def rect_power_map(rng, nx: int, ny: int) -> np.ndarray:
+    """Sum of 1-5 rectangles of uniform density (W/m^2), float64 [ny][nx]."""
+    out = np.zeros((ny, nx), np.float64)
+    for _ in range(int(rng.integers(1, 6))):
+        w = int(rng.integers(1, max(1, nx // 2) + 1))
+        h = int(rng.integers(1, max(1, ny // 2) + 1))
+        x0 = int(rng.integers(0, nx - w + 1))
+        y0 = int(rng.integers(0, ny - h + 1))
+        out[y0:y0 + h, x0:x0 + w] += _log_uniform(rng, 1e5, 1e7)
+    return out
+
+
+def gauss_power_map(rng, nx: int, ny: int) -> np.ndarray:
+    """One Gaussian hotspot (W/m^2), float64 [ny][nx], sampled at cell centres."""
+    amp = _log_uniform(rng, 1e5, 1e7)
+    sig = rng.uniform(2.0, 16.0)
+    cx = rng.uniform(0.0, nx)
+    cy = rng.uniform(0.0, ny)
+    xs = np.arange(nx) + 0.5
+    ys = np.arange(ny) + 0.5
+    r2 = (xs[None, :] - cx) ** 2 + (ys[:, None] - cy) ** 2
+    return amp * np.exp(-r2 / (2.0 * sig * sig))
+
+
+def power_maps(rng, nx: int, ny: int, s: int, mix: bool) -> np.ndarray:
+    """s power maps; with ``mix`` each map is a rectangle set or a hotspot (50/50)."""
+    maps = []
+    for _ in range(s):
+        if mix and rng.uniform() < 0.5:
+            maps.append(gauss_power_map(rng, nx, ny))
+        else:
+            maps.append(rect_power_map(rng, nx, ny))
+    return np.stack(maps) if maps else np.zeros((0, ny, nx))
+
+
+def coefficients(rng, s: int, M: int) -> np.ndarray:
+    """C ~ N(0,1) of shape [s][M], rounded to bfloat16-exact float64."""
+    return round_to_bf16(rng.standard_normal((s, M)))
+
+
+def _layered_chip(rng, nx, ny, n_layers, h_top) -> Chip:
+    return Chip(nx=nx, ny=ny,
+                layer_nz=np.ones(n_layers, np.int32),
+                layer_dz=np.full(n_layers, CELL_DZ),
+                layer_k=_log_uniform(rng, 1.0, 400.0, n_layers),
+                h_top=float(h_top))
+
+
+def reference_stack_chip() -> Chip:
+    """32x32x4 chip: silicon / TIM / spreader / substrate, top Robin h=1e4."""
+    return Chip(nx=32, ny=32, layer_nz=np.ones(4, np.int32),
+                layer_dz=np.full(4, CELL_DZ),
+                layer_k=np.array([150.0, 5.0, 400.0, 20.0]), h_top=1e4)
+
+
+def small_fp64_workload(M: int = 64) -> Workload:
+    """32x32x4 reference stack, s=8 rectangle maps, M=64, solved to 1e-12."""
+    rng = np.random.default_rng(1_000_000 * 1 + 0)
+    chip = reference_stack_chip()
+    dens = power_maps(rng, chip.nx, chip.ny, 8, mix=False)
+    C = coefficients(rng, 8, M)
+    return Workload("chip32x32x4_s8_M64_fp64", [chip], [dens], [C], s=8, M=M, rtol=1e-12)
+
+
+def single_chip_workload(nx=128, ny=128, n_layers=8, s=32, M=5000,
+                         cfg=2, rtol=1e-6, name=None) -> Workload:
+    """One chip with log-uniform layer k, mixed rectangle/hotspot maps."""
+    rng = np.random.default_rng(1_000_000 * cfg + 0)
+    chip = _layered_chip(rng, nx, ny, n_layers, 1e4)
+    dens = power_maps(rng, nx, ny, s, mix=True)
+    C = coefficients(rng, s, M)
+    name = name or f"chip{nx}x{ny}x{n_layers}_s{s}_M{M}"
+    return Workload(name, [chip], [dens], [C], s=s, M=M, rtol=rtol)
+
+
+def batched_workload(n_chips: int = 256, s: int = 16, M: int = 20,
+                     sides=(64, 96, 128, 192, 256), cfg=3, rtol=1e-6) -> Workload:
+    """Uneven chips: square side from ``sides``, 4-12 layers, h in [1e3, 1e5]."""
+    chips, dens, Cs = [], [], []
+    for j in range(n_chips):
+        rng = np.random.default_rng(1_000_000 * cfg + j)
+        side = int(rng.choice(np.asarray(sides)))
+        nl = int(rng.integers(4, 13))
+        h = rng.uniform(1e3, 1e5)
+        chip = _layered_chip(rng, side, side, nl, h)
+        chips.append(chip)
+        dens.append(power_maps(rng, side, side, s, mix=True))
+        Cs.append(coefficients(rng, s, M))
+    return Workload(f"batch{n_chips}_s{s}_M{M}", chips, dens, Cs, s=s, M=M, rtol=rtol)
+
+
+def large_chip_workload(M: int = 10000, s: int = 64) -> Workload:
+    """512x512x16 chip, 16 log-uniform layers, s=64, M fields."""
+    return single_chip_workload(512, 512, 16, s=s, M=M, cfg=5,
+                                name=f"chip512x512x16_s{s}_M{M}")
+
+
+def random_small_chip(seed: int, nx: int, ny: int, n_layers: int,
+                      h_top=1e4, h_bottom=0.0, h_side=0.0,
+                      layer_nz=None) -> Chip:
+    """Small chip for tests: random layer k and thickness jitter."""
+    rng = np.random.default_rng(seed)
+    lnz = np.ones(n_layers, np.int32) if layer_nz is None else np.asarray(layer_nz, np.int32)
+    return Chip(nx=nx, ny=ny, layer_nz=lnz,
+                layer_dz=CELL_DZ * rng.uniform(0.5, 2.0, n_layers),
+                layer_k=_log_uniform(rng, 1.0, 400.0, n_layers),
+                h_top=h_top, h_bottom=h_bottom, h_side=h_side)

@@ -1,0 +1,125 @@
+"""Planted mistakes in the oracle must each be caught by at least one pin.
+
+Every mutant below is a plausible slip (a dropped half-cell factor, a wrong
+sign, a wrong operand or index).  The mutant replaces one oracle function,
+the pins of ``test_oracle_pins`` run against it, and at least one of them
+must fail.  Nothing here touches a GPU.
+"""
+import numpy as np
+import pytest
+
+from oracle import blockoa_oracle as orc
+from paper_2510_23221_gb300 import synth
+from tests import test_oracle_pins as pins
+
+
+def _run_pins():
+    """Run every pin once; return the names of the pins that failed."""
+    failed = []
+    checks = [
+        ("slab_chain", pins.test_slab_resistor_chain_closed_form),
+        ("slab_continuous", pins.test_slab_converges_to_continuous_solution),
+        ("ladder_x", lambda: pins.test_lateral_ladder_closed_form("x")),
+        ("ladder_y", lambda: pins.test_lateral_ladder_closed_form("y")),
+        ("rhs", pins.test_rhs_total_power_and_placement),
+        ("finite_termination", pins.test_finite_termination),
+        ("textbook_cg", pins.test_single_column_equals_textbook_cg),
+        ("deflation", pins.test_deflation_duplicate_and_zero_columns),
+        ("combine_apply", pins.test_combine_and_apply_brute_force),
+        ("linearity", pins.test_linearity_and_pair_consistency),
+        ("pivoted_cholesky", pins.test_pivoted_cholesky_against_library),
+    ]
+    for chip in pins._chips():
+        checks.append(("spd", lambda c=chip: pins.test_operator_symmetric_bitwise_and_spd(c)))
+        checks.append(("energy", lambda c=chip: pins.test_energy_balance(c)))
+        checks.append(("dense_direct", lambda c=chip: pins.test_block_cg_matches_dense_direct(c)))
+    for name, fn in checks:
+        try:
+            fn()
+        except Exception:
+            failed.append(name)
+    return failed
+
+
+REAL = {name: getattr(orc, name) for name in
+        ("rhs", "block_cg", "face_conductances", "_gram_solve", "_series")}
+
+
+def test_unmutated_oracle_passes_every_pin():
+    assert _run_pins() == []
+
+
+def _mut_series_full_width(area, half_a, k_a, half_b, k_b):
+    return area / (half_a / k_a + half_b / k_b)
+
+
+def _mut_robin_no_half_cell(area, d, k, h):
+    return area / (1.0 / h)
+
+
+def _mut_robin_full_cell(area, d, k, h):
+    return area / (d / k + 1.0 / h)
+
+
+def _mut_rhs_bottom_layer(chip, density):
+    B = REAL["rhs"](chip, density)
+    top = chip.nx * chip.ny
+    out = np.zeros_like(B)
+    out[chip.n - top:] = B[:top]
+    return out
+
+
+def _mut_combine_no_transpose(U, C):
+    return np.asarray(U, np.float64) @ np.asarray(C, np.float64)
+
+
+def _make_bcg_mutant(kind):
+    real = REAL["block_cg"]
+
+    def mutant(A, B, X0=None, rtol=1e-12, maxiter=10000, deflate_tol=1e-14, record=None):
+        orig_solve = REAL["_gram_solve"]
+        calls = {"n": 0}
+
+        def solve(kept, L, d, Y):
+            calls["n"] += 1
+            z = orig_solve(kept, L, d, Y)
+            if kind == "beta_sign" and calls["n"] % 2 == 0:
+                return -z
+            if kind == "alpha_scale" and calls["n"] % 2 == 1:
+                return 0.5 * z
+            return z
+
+        orc._gram_solve = solve
+        try:
+            return real(A, B, X0, rtol, maxiter, deflate_tol, record)
+        finally:
+            orc._gram_solve = orig_solve
+
+    return mutant
+
+
+def _mut_gz_wrong_index(chip):
+    f = REAL["face_conductances"](chip)
+    k = chip.cell_k()
+    dz = chip.cell_dz()[:, None, None]
+    f["gz"] = REAL["_series"](chip.dx * chip.dy, dz[:-1], k[:-1], dz[:-1], k[1:])
+    return f
+
+
+MUTANTS = {
+    "series_full_width": ("_series", _mut_series_full_width),
+    "robin_no_half_cell": ("_robin", _mut_robin_no_half_cell),
+    "robin_full_cell": ("_robin", _mut_robin_full_cell),
+    "rhs_bottom_layer": ("rhs", _mut_rhs_bottom_layer),
+    "combine_no_transpose": ("combine", _mut_combine_no_transpose),
+    "beta_sign": ("block_cg", _make_bcg_mutant("beta_sign")),
+    "alpha_scale": ("block_cg", _make_bcg_mutant("alpha_scale")),
+    "gz_wrong_index": ("face_conductances", _mut_gz_wrong_index),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(name, monkeypatch):
+    attr, fn = MUTANTS[name]
+    monkeypatch.setattr(orc, attr, fn)
+    assert _run_pins(), f"mutant {name} passed every pin"
