@@ -1,0 +1,195 @@
+/*
+ * blockoa.h -- C ABI of libblockoa.so, the GB300 (sm_103a) hot path of
+ * BlocKOA: block Krylov basis solve, combination, operator action.
+ *
+ * Paper: "Accelerating IC Thermal Simulation Data Generation via Block
+ * Krylov and Operator Action" (arXiv 2510.23221).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Unknowns are excess temperature theta = T - t_ambient in K; rows of the
+ *   operator are in W/K; right-hand sides are cell powers in W.
+ * - Cells of one chip are numbered a = (z * ny + y) * nx + x, z = 0 is the
+ *   top (silicon) layer.  Several chips are concatenated chip after chip;
+ *   blockoa_operator_size() gives each chip's cell offset.
+ * - Block vectors (B, X, U) are cell-major with the s columns fastest:
+ *   element (cell a of chip c, column j) sits at [(off_c + a) * s + j].
+ * - Fields (T, q) are field-major per chip: element (field m, cell a of
+ *   chip c) sits at [off_c * M + m * n_c + a].
+ * - Coefficients C are [chip][s][M] row-major, float64 values that are
+ *   exactly representable in bfloat16 when the MIXED path is used.
+ * - Every pointer named "device" is a CUDA device pointer owned by the
+ *   caller; the library never frees or reallocates it.  Pointers named
+ *   "host" are ordinary host memory.  The operator object is owned by the
+ *   library and holds its own device workspace until blockoa_destroy().
+ * - Calls are asynchronous on `stream` unless stated otherwise.
+ * - Every call returns a blockoa_status; nothing crosses the ABI as an
+ *   exception and the library never exits the process.  On error, outputs
+ *   are unspecified but statistics structures are filled in.
+ */
+#ifndef BLOCKOA_H
+#define BLOCKOA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL means the legacy default stream. */
+typedef struct CUstream_st *blockoa_stream;
+
+typedef enum {
+  BLOCKOA_OK = 0,
+  BLOCKOA_ERR_INVALID = 1,        /* bad argument, checked on the host before any launch */
+  BLOCKOA_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  BLOCKOA_ERR_BREAKDOWN = 3,      /* NaN/Inf, or Gram matrix of rank 0 with columns unconverged */
+  BLOCKOA_ERR_NOT_CONVERGED = 4,  /* iteration limit reached before every column met rtol */
+  BLOCKOA_ERR_TIMEOUT = 5,        /* a bounded device wait gave up */
+  BLOCKOA_ERR_OOM = 6             /* device allocation failed */
+} blockoa_status;
+
+/* Arithmetic of a call. */
+typedef enum {
+  BLOCKOA_FP64 = 0,   /* every step in float64 */
+  BLOCKOA_MIXED = 1   /* float32 vectors and stencil, float64 Gram/Cholesky and
+                         refinement, bfloat16x3 tensor-core combination */
+} blockoa_precision;
+
+/*
+ * One layered chip (Sec. V-A; the steady heat equation of Eq. 1 on a
+ * rectangular prism with the Robin condition of Sec. II-A).
+ * All pointers are host pointers read during blockoa_assemble() only.
+ */
+typedef struct {
+  int nx, ny;                 /* lateral cells, >= 1 */
+  int n_layers;               /* >= 1 */
+  const int *layer_nz;        /* [n_layers] cells per layer along z, >= 1 */
+  const double *layer_dz;     /* [n_layers] thickness of one cell of the layer, m, > 0 */
+  const double *layer_k;      /* [n_layers] conductivity, W/m/K, > 0; ignored if k_cell != NULL */
+  const double *k_cell;       /* optional [nz][ny][nx] per-cell conductivity, W/m/K */
+  double dx, dy;              /* lateral cell size, m, > 0 */
+  double h_top, h_bottom, h_side; /* convective coefficients, W/m^2/K; 0 = adiabatic */
+  double t_ambient;           /* K; reporting only (unknowns are excess temperature) */
+} blockoa_chip_desc;
+
+typedef struct {
+  double rtol;          /* per-column ||B_j - A X_j|| / ||B_j|| target, > 0 */
+  int maxiter;          /* limit on block iterations (summed over refinement steps) */
+  int precision;        /* blockoa_precision */
+  double inner_rtol;    /* MIXED: residual reduction asked of each float32 inner solve (<= 0: 1e-3) */
+  int max_refine;       /* MIXED: limit on float64 refinement steps (<= 0: 12) */
+  double deflate_tol;   /* pivot threshold on the scaled Gram (<= 0: 1e-14 FP64, 1e-6 float32 inner) */
+  const double *x0;     /* device [n_total][s] initial guess, or NULL for zero */
+  int check_every;      /* block iterations between convergence polls by the host (<= 0: 8) */
+} blockoa_solve_opts;
+
+typedef struct {
+  int status;           /* blockoa_status of this chip */
+  int iters;            /* block iterations (summed over refinement steps) */
+  int refine_steps;     /* float64 true-residual evaluations after the start */
+  int deflated_cols;    /* columns dropped by deflation, summed over iterations */
+  double relres_max;    /* max_j ||B_j - A X_j|| / ||B_j|| from a float64 true residual */
+} blockoa_solve_stats;
+
+typedef struct blockoa_operator blockoa_operator;
+
+/*
+ * Discretise n_chips chips (Eq. 1 -> Eq. 2; Sec. II-B) with a cell-centred
+ * 7-point finite-volume stencil in flux form:
+ *   (A theta)_a = sum_b G_ab (theta_a - theta_b) + Gb_a theta_a,
+ *   G_ab = S_f / (d_a/(2 k_a) + d_b/(2 k_b)),  Gb = S_f / (d/(2k) + 1/h).
+ * Face conductances are computed on the device in float64 (and rounded to
+ * float32 copies).  `chips` is a host array read before return.
+ * On success *out receives a new operator (free with blockoa_destroy).
+ * Errors: ERR_INVALID (bad descriptor), ERR_OOM, ERR_CUDA.
+ */
+int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips, blockoa_stream stream,
+                     blockoa_operator **out);
+
+/* Sizes of chip `chip` (host outputs, any may be NULL).  Synchronous. */
+int blockoa_operator_size(const blockoa_operator *op, int chip, int64_t *n_cells,
+                          int64_t *cell_offset, int *nx, int *ny, int *nz);
+
+/* Total cells over all chips and number of chips (host outputs). */
+int blockoa_operator_total(const blockoa_operator *op, int64_t *n_total, int *n_chips);
+
+/*
+ * Right-hand sides b of Eq. 2: cell power = density * dx * dy in the top
+ * cell row (z = 0), zero elsewhere.
+ * density: device float64 [chip][s][ny][nx] (W/m^2), chips concatenated.
+ * B: device float64 block vector [n_total][s] (written in full).
+ */
+int blockoa_build_rhs(const blockoa_operator *op, const double *density, double *B, int s,
+                      blockoa_stream stream);
+
+/*
+ * Block conjugate gradient on A_c X_c = B_c for every chip c at once
+ * (Eq. 3-4, Sec. III-A): all s columns of a chip share one Krylov space.
+ * Each iteration: Q = A P; Gamma = P^T Q; Jacobi-scaled pivoted Cholesky of
+ * Gamma with deflation of pivots <= deflate_tol; alpha = Gamma^-1 P^T R;
+ * X += P alpha; R -= Q alpha; beta = -Gamma^-1 Q^T R; P = R + P beta.
+ * MIXED runs that loop in float32 (Gram products accumulated to float64)
+ * inside float64 iterative refinement on the true residual B - A X.
+ * Stops when every column meets ||B_j - A X_j|| <= rtol ||B_j||.
+ * B, X: device float64 [n_total][s]; 1 <= s <= 64.  X is overwritten.
+ * stats: host array [n_chips], always written.
+ * Synchronous: returns after the solve, because it fills `stats`.
+ * Errors: ERR_INVALID, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_OOM, ERR_CUDA
+ * (the worst chip status is returned).
+ */
+int blockoa_block_solve(blockoa_operator *op, const double *B, double *X, int s,
+                        const blockoa_solve_opts *opts, blockoa_solve_stats *stats,
+                        blockoa_stream stream);
+
+/*
+ * New temperature fields T = U C (Eq. 5, Sec. III-B, with the noise term
+ * off and no normalisation: unknowns are excess temperatures, so every
+ * combination keeps the homogeneous Robin/adiabatic conditions).
+ * U: device float64 [n_total][s]; C: device float64 [chip][s][M].
+ * T: device fields [chip][M][n_c], float64 for FP64, float32 for MIXED.
+ * MIXED splits U into three bfloat16 planes and multiplies on the tensor
+ * cores (tcgen05) with float32 accumulation; C must be bfloat16-exact.
+ */
+int blockoa_combine(blockoa_operator *op, const double *U, const double *C, void *T, int s,
+                    int M, int dtype, blockoa_stream stream);
+
+/*
+ * Operator action q = A T (Eq. 6, Sec. III-C) on M fields of every chip.
+ * T, q: device fields [chip][M][n_c]; float64 for FP64, float32 for MIXED.
+ * T and q must not overlap.
+ */
+int blockoa_apply_operator(const blockoa_operator *op, const void *T, void *q, int M,
+                           int dtype, blockoa_stream stream);
+
+/*
+ * Pair consistency of generated data (Sec. IV-B: the operator action adds
+ * no solver error): e_pair[c*M + m] = ||A T_m - q_m|| / ||q_m|| with A
+ * applied in float64 to the stored field T_m.
+ * T, q: device fields as in blockoa_apply_operator (dtype selects float64
+ * or float32 storage); e_pair: device float64 [n_chips * M].
+ */
+int blockoa_pair_check(const blockoa_operator *op, const void *T, const void *q, int M,
+                       int dtype, double *e_pair, blockoa_stream stream);
+
+/*
+ * Copy chip `chip`'s float64 face conductances to host arrays laid out like
+ * the oracle's: gx [nz][ny][nx-1], gy [nz][ny-1][nx], gz [nz-1][ny][nx],
+ * gb [nz][ny][nx] (any pointer may be NULL).  Synchronous.  For tests.
+ */
+int blockoa_export_conductances(const blockoa_operator *op, int chip, double *gx, double *gy,
+                                double *gz, double *gb);
+
+/* Free the operator and its workspace (NULL is a no-op).  Synchronises the device. */
+void blockoa_destroy(blockoa_operator *op);
+
+/* Static description of a status code. */
+const char *blockoa_status_string(int status);
+
+/* Text of the last CUDA error seen by the calling thread ("" if none). */
+const char *blockoa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BLOCKOA_H */

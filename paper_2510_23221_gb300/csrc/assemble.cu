@@ -1,0 +1,376 @@
+// Operator assembly (Eq. 1 -> Eq. 2, Sec. II-B), right-hand sides (Eq. 2),
+// operator lifetime, status strings and shared host utilities.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace blockoa {
+
+static thread_local char g_last_error[256] = "";
+
+void set_last_error(cudaError_t e, const char *where) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+}
+
+int cuda_status(cudaError_t e, const char *where) {
+  if (e == cudaSuccess) return BLOCKOA_OK;
+  set_last_error(e, where);
+  cudaGetLastError();  // clear a non-sticky error so later calls can proceed
+  return e == cudaErrorMemoryAllocation ? BLOCKOA_ERR_OOM : BLOCKOA_ERR_CUDA;
+}
+
+static cudaMemPool_t device_pool(int dev) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev < 0 || dev >= 64) return nullptr;
+  if (!pools[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;  // keep freed blocks for reuse by later calls
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
+int pool_alloc(blockoa_operator *op, void **p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  if (bytes == 0) return BLOCKOA_OK;
+  cudaError_t e = op->pool ? cudaMallocFromPoolAsync(p, bytes, op->pool, st)
+                           : cudaMallocAsync(p, bytes, st);
+  if (e != cudaSuccess) return cuda_status(e, "workspace allocation");
+  return BLOCKOA_OK;
+}
+
+void pool_free(void *p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+std::vector<Unit> make_units(const blockoa_operator *op, long long cells) {
+  std::vector<Unit> units;
+  for (int c = 0; c < op->n_chips; ++c) {
+    const ChipDev &ch = op->chips[c];
+    for (long long b = 0; b < ch.n; b += cells) {
+      Unit u;
+      u.chip = c;
+      u.pad = 0;
+      u.begin = ch.off + b;
+      u.end = ch.off + (b + cells < ch.n ? b + cells : ch.n);
+      units.push_back(u);
+    }
+  }
+  return units;
+}
+
+long long pick_unit_cells(const blockoa_operator *op, long long align, long long min_cells,
+                          int target_ctas) {
+  long long want = (op->n_total + target_ctas - 1) / target_ctas;
+  if (want < min_cells) want = min_cells;
+  return (want + align - 1) / align * align;
+}
+
+// ---------------------------------------------------------------- assembly
+struct ChipPhys {
+  double dx, dy, h_top, h_bottom, h_side;
+  long long zoff;       // first z-row of the chip in the z tables
+  long long kcell_off;  // offset into the per-cell k array, or -1
+};
+
+// Face conductance S / (d_a/(2 k_a) + d_b/(2 k_b)), float64 without contraction.
+__device__ __forceinline__ double series_g(double area, double da, double ka, double db,
+                                           double kb) {
+  double ra = __ddiv_rn(da, __dmul_rn(2.0, ka));
+  double rb = __ddiv_rn(db, __dmul_rn(2.0, kb));
+  return __ddiv_rn(area, __dadd_rn(ra, rb));
+}
+
+// Robin face conductance S / (d/(2k) + 1/h).
+__device__ __forceinline__ double robin_g(double area, double d, double k, double h) {
+  double r = __dadd_rn(__ddiv_rn(d, __dmul_rn(2.0, k)), __ddiv_rn(1.0, h));
+  return __ddiv_rn(area, r);
+}
+
+__global__ void assemble_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chips,
+                                const ChipPhys *__restrict__ phys, const double *__restrict__ zk,
+                                const double *__restrict__ zdz, const double *__restrict__ kcell,
+                                double *__restrict__ g64, float *__restrict__ g32) {
+  const Unit u = units[blockIdx.x];
+  const ChipDev ch = chips[u.chip];
+  const ChipPhys ph = phys[u.chip];
+  const long long nxny = (long long)ch.nx * ch.ny;
+  for (long long a = u.begin + threadIdx.x; a < u.end; a += blockDim.x) {
+    const long long loc = a - ch.off;
+    const int x = (int)(loc % ch.nx);
+    const int y = (int)((loc / ch.nx) % ch.ny);
+    const int z = (int)(loc / nxny);
+    auto kof = [&](long long l, int zz) -> double {
+      return ph.kcell_off >= 0 ? kcell[ph.kcell_off + l] : zk[ph.zoff + zz];
+    };
+    const double ka = kof(loc, z);
+    const double dz = zdz[ph.zoff + z];
+    double cx = 0.0, cy = 0.0, cz = 0.0, cb = 0.0;
+    if (x + 1 < ch.nx) cx = series_g(__dmul_rn(ph.dy, dz), ph.dx, ka, ph.dx, kof(loc + 1, z));
+    if (y + 1 < ch.ny) cy = series_g(__dmul_rn(ph.dx, dz), ph.dy, ka, ph.dy, kof(loc + ch.nx, z));
+    if (z + 1 < ch.nz)
+      cz = series_g(__dmul_rn(ph.dx, ph.dy), dz, ka, zdz[ph.zoff + z + 1], kof(loc + nxny, z + 1));
+    // Robin faces, summed in the order top, bottom, x-low, x-high, y-low, y-high.
+    if (ph.h_top > 0.0 && z == 0) cb = __dadd_rn(cb, robin_g(__dmul_rn(ph.dx, ph.dy), dz, ka, ph.h_top));
+    if (ph.h_bottom > 0.0 && z == ch.nz - 1)
+      cb = __dadd_rn(cb, robin_g(__dmul_rn(ph.dx, ph.dy), dz, ka, ph.h_bottom));
+    if (ph.h_side > 0.0) {
+      if (x == 0) cb = __dadd_rn(cb, robin_g(__dmul_rn(ph.dy, dz), ph.dx, ka, ph.h_side));
+      if (x == ch.nx - 1) cb = __dadd_rn(cb, robin_g(__dmul_rn(ph.dy, dz), ph.dx, ka, ph.h_side));
+      if (y == 0) cb = __dadd_rn(cb, robin_g(__dmul_rn(ph.dx, dz), ph.dy, ka, ph.h_side));
+      if (y == ch.ny - 1) cb = __dadd_rn(cb, robin_g(__dmul_rn(ph.dx, dz), ph.dy, ka, ph.h_side));
+    }
+    reinterpret_cast<double4 *>(g64)[a] = make_double4(cx, cy, cz, cb);
+    reinterpret_cast<float4 *>(g32)[a] =
+        make_float4((float)cx, (float)cy, (float)cz, (float)cb);
+  }
+}
+
+// ---------------------------------------------------------------- right-hand sides
+struct RhsChip {
+  double area;          // dx * dy
+  long long dens_off;   // offset of the chip's [s][ny][nx] density block
+};
+
+__global__ void build_rhs_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chips,
+                                 const RhsChip *__restrict__ rc, const double *__restrict__ dens,
+                                 double *__restrict__ B, int s) {
+  const Unit u = units[blockIdx.x];
+  const ChipDev ch = chips[u.chip];
+  const RhsChip r = rc[u.chip];
+  const long long nxny = (long long)ch.nx * ch.ny;
+  const long long total = (u.end - u.begin) * s;
+  for (long long t = threadIdx.x; t < total; t += blockDim.x) {
+    const long long a = u.begin + t / s;
+    const int j = (int)(t % s);
+    const long long loc = a - ch.off;
+    double v = 0.0;
+    if (loc < nxny) v = __dmul_rn(dens[r.dens_off + (long long)j * nxny + loc], r.area);
+    B[a * s + j] = v;
+  }
+}
+
+}  // namespace blockoa
+
+using namespace blockoa;
+
+// ---------------------------------------------------------------- C ABI
+extern "C" const char *blockoa_status_string(int status) {
+  switch (status) {
+    case BLOCKOA_OK: return "ok";
+    case BLOCKOA_ERR_INVALID: return "invalid argument";
+    case BLOCKOA_ERR_CUDA: return "CUDA error";
+    case BLOCKOA_ERR_BREAKDOWN: return "breakdown (NaN/Inf or rank-0 Gram matrix)";
+    case BLOCKOA_ERR_NOT_CONVERGED: return "not converged within maxiter";
+    case BLOCKOA_ERR_TIMEOUT: return "device wait timed out";
+    case BLOCKOA_ERR_OOM: return "out of device memory";
+    default: return "unknown status";
+  }
+}
+
+extern "C" const char *blockoa_last_error(void) { return g_last_error; }
+
+static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+static bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
+
+extern "C" int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips,
+                                blockoa_stream stream, blockoa_operator **out) {
+  if (!out) return BLOCKOA_ERR_INVALID;
+  *out = nullptr;
+  if (!chips || n_chips <= 0) return BLOCKOA_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+
+  // Validate on the host and build tables.
+  std::vector<ChipDev> tab(n_chips);
+  std::vector<ChipPhys> phys(n_chips);
+  std::vector<double> zk, zdz, kcell;
+  long long off = 0;
+  for (int c = 0; c < n_chips; ++c) {
+    const blockoa_chip_desc &d = chips[c];
+    if (d.nx < 1 || d.ny < 1 || d.n_layers < 1 || !d.layer_nz || !d.layer_dz) return BLOCKOA_ERR_INVALID;
+    if (!d.k_cell && !d.layer_k) return BLOCKOA_ERR_INVALID;
+    if (!finite_pos(d.dx) || !finite_pos(d.dy)) return BLOCKOA_ERR_INVALID;
+    if (!finite_nonneg(d.h_top) || !finite_nonneg(d.h_bottom) || !finite_nonneg(d.h_side))
+      return BLOCKOA_ERR_INVALID;
+    long long nz = 0;
+    ChipPhys ph;
+    ph.dx = d.dx; ph.dy = d.dy; ph.h_top = d.h_top; ph.h_bottom = d.h_bottom; ph.h_side = d.h_side;
+    ph.zoff = (long long)zk.size();
+    for (int l = 0; l < d.n_layers; ++l) {
+      if (d.layer_nz[l] < 1 || !finite_pos(d.layer_dz[l])) return BLOCKOA_ERR_INVALID;
+      double kl = d.layer_k ? d.layer_k[l] : 1.0;
+      if (!d.k_cell && !finite_pos(kl)) return BLOCKOA_ERR_INVALID;
+      for (int r = 0; r < d.layer_nz[l]; ++r) {
+        zk.push_back(kl);
+        zdz.push_back(d.layer_dz[l]);
+      }
+      nz += d.layer_nz[l];
+    }
+    if (nz > (1 << 30)) return BLOCKOA_ERR_INVALID;
+    long long n = (long long)d.nx * d.ny * nz;
+    if (n > (1LL << 40)) return BLOCKOA_ERR_INVALID;
+    ph.kcell_off = -1;
+    if (d.k_cell) {
+      ph.kcell_off = (long long)kcell.size();
+      for (long long i = 0; i < n; ++i) {
+        if (!finite_pos(d.k_cell[i])) return BLOCKOA_ERR_INVALID;
+        kcell.push_back(d.k_cell[i]);
+      }
+    }
+    tab[c].nx = d.nx; tab[c].ny = d.ny; tab[c].nz = (int)nz; tab[c].pad = 0;
+    tab[c].n = n; tab[c].off = off;
+    phys[c] = ph;
+    off += n;
+  }
+
+  blockoa_operator *op = new blockoa_operator();
+  cudaGetDevice(&op->device);
+  op->pool = device_pool(op->device);
+  op->n_chips = n_chips;
+  op->n_total = off;
+  op->chips = tab;
+  op->cell_area.resize(n_chips);
+  for (int c = 0; c < n_chips; ++c) op->cell_area[c] = chips[c].dx * chips[c].dy;
+
+  std::vector<Unit> units = make_units(op, 4096);
+  void *d_units = nullptr, *d_phys = nullptr, *d_zk = nullptr, *d_zdz = nullptr, *d_kc = nullptr;
+  int rc = BLOCKOA_OK;
+  auto fail = [&](int code) {
+    pool_free(d_units, st); pool_free(d_phys, st); pool_free(d_zk, st);
+    pool_free(d_zdz, st); pool_free(d_kc, st);
+    blockoa_destroy(op);
+    return code;
+  };
+  cudaError_t e;
+  e = cudaMalloc((void **)&op->d_chips, sizeof(ChipDev) * n_chips);
+  if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc chips"));
+  e = cudaMalloc((void **)&op->g64, sizeof(double) * 4 * op->n_total);
+  if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc g64"));
+  e = cudaMalloc((void **)&op->g32, sizeof(float) * 4 * op->n_total);
+  if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc g32"));
+  if ((rc = pool_alloc(op, &d_units, sizeof(Unit) * units.size(), st))) return fail(rc);
+  if ((rc = pool_alloc(op, &d_phys, sizeof(ChipPhys) * n_chips, st))) return fail(rc);
+  if ((rc = pool_alloc(op, &d_zk, sizeof(double) * zk.size(), st))) return fail(rc);
+  if ((rc = pool_alloc(op, &d_zdz, sizeof(double) * zdz.size(), st))) return fail(rc);
+  if (!kcell.empty() && (rc = pool_alloc(op, &d_kc, sizeof(double) * kcell.size(), st)))
+    return fail(rc);
+  // Host tables are pageable; cudaMemcpyAsync from pageable memory returns
+  // only after the source has been consumed, so the vectors may die after.
+  e = cudaMemcpyAsync(op->d_chips, tab.data(), sizeof(ChipDev) * n_chips, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_units, units.data(), sizeof(Unit) * units.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_phys, phys.data(), sizeof(ChipPhys) * n_chips, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_zk, zk.data(), sizeof(double) * zk.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_zdz, zdz.data(), sizeof(double) * zdz.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && d_kc) e = cudaMemcpyAsync(d_kc, kcell.data(), sizeof(double) * kcell.size(), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail(cuda_status(e, "upload chip tables"));
+  assemble_kernel<<<(unsigned)units.size(), 256, 0, st>>>(
+      (const Unit *)d_units, op->d_chips, (const ChipPhys *)d_phys, (const double *)d_zk,
+      (const double *)d_zdz, (const double *)d_kc, op->g64, op->g32);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(cuda_status(e, "assemble_kernel"));
+  pool_free(d_units, st); pool_free(d_phys, st); pool_free(d_zk, st);
+  pool_free(d_zdz, st); pool_free(d_kc, st);
+  *out = op;
+  return BLOCKOA_OK;
+}
+
+extern "C" int blockoa_operator_size(const blockoa_operator *op, int chip, int64_t *n_cells,
+                                     int64_t *cell_offset, int *nx, int *ny, int *nz) {
+  if (!op || chip < 0 || chip >= op->n_chips) return BLOCKOA_ERR_INVALID;
+  const ChipDev &c = op->chips[chip];
+  if (n_cells) *n_cells = c.n;
+  if (cell_offset) *cell_offset = c.off;
+  if (nx) *nx = c.nx;
+  if (ny) *ny = c.ny;
+  if (nz) *nz = c.nz;
+  return BLOCKOA_OK;
+}
+
+extern "C" int blockoa_operator_total(const blockoa_operator *op, int64_t *n_total, int *n_chips) {
+  if (!op) return BLOCKOA_ERR_INVALID;
+  if (n_total) *n_total = op->n_total;
+  if (n_chips) *n_chips = op->n_chips;
+  return BLOCKOA_OK;
+}
+
+extern "C" int blockoa_build_rhs(const blockoa_operator *op, const double *density, double *B,
+                                 int s, blockoa_stream stream) {
+  if (!op || s < 0) return BLOCKOA_ERR_INVALID;
+  if (s == 0) return BLOCKOA_OK;
+  if (!density || !B) return BLOCKOA_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<RhsChip> rcs(op->n_chips);
+  long long doff = 0;
+  for (int c = 0; c < op->n_chips; ++c) {
+    rcs[c].area = op->cell_area[c];
+    rcs[c].dens_off = doff;
+    doff += (long long)s * op->chips[c].nx * op->chips[c].ny;
+  }
+  std::vector<Unit> units = make_units(op, 2048);
+  blockoa_operator *mop = const_cast<blockoa_operator *>(op);
+  void *d_units = nullptr, *d_rc = nullptr;
+  int rc = pool_alloc(mop, &d_units, sizeof(Unit) * units.size(), st);
+  if (!rc) rc = pool_alloc(mop, &d_rc, sizeof(RhsChip) * rcs.size(), st);
+  if (rc) { pool_free(d_units, st); pool_free(d_rc, st); return rc; }
+  cudaError_t e = cudaMemcpyAsync(d_units, units.data(), sizeof(Unit) * units.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_rc, rcs.data(), sizeof(RhsChip) * rcs.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    build_rhs_kernel<<<(unsigned)units.size(), 256, 0, st>>>((const Unit *)d_units, op->d_chips,
+                                                           (const RhsChip *)d_rc, density, B, s);
+    e = cudaGetLastError();
+  }
+  pool_free(d_units, st);
+  pool_free(d_rc, st);
+  return cuda_status(e, "build_rhs");
+}
+
+extern "C" int blockoa_export_conductances(const blockoa_operator *op, int chip, double *gx,
+                                           double *gy, double *gz, double *gb) {
+  if (!op || chip < 0 || chip >= op->n_chips) return BLOCKOA_ERR_INVALID;
+  const ChipDev &c = op->chips[chip];
+  std::vector<double> g((size_t)c.n * 4);
+  BLOCKOA_CUDA(cudaDeviceSynchronize());
+  BLOCKOA_CUDA(cudaMemcpy(g.data(), op->g64 + 4 * c.off, sizeof(double) * 4 * c.n,
+                          cudaMemcpyDeviceToHost));
+  size_t ix = 0, iy = 0, iz = 0;
+  for (int z = 0; z < c.nz; ++z)
+    for (int y = 0; y < c.ny; ++y)
+      for (int x = 0; x < c.nx; ++x) {
+        size_t a = ((size_t)z * c.ny + y) * c.nx + x;
+        if (gx && x + 1 < c.nx) gx[ix] = g[4 * a + 0];
+        if (x + 1 < c.nx) ++ix;
+        if (gy && y + 1 < c.ny) gy[iy] = g[4 * a + 1];
+        if (y + 1 < c.ny) ++iy;
+        if (gz && z + 1 < c.nz) gz[iz] = g[4 * a + 2];
+        if (z + 1 < c.nz) ++iz;
+        if (gb) gb[a] = g[4 * a + 3];
+      }
+  return BLOCKOA_OK;
+}
+
+extern "C" void blockoa_destroy(blockoa_operator *op) {
+  if (!op) return;
+  cudaDeviceSynchronize();
+  free_solve_ws(op->solve_ws);
+  if (op->d_chips) cudaFree(op->d_chips);
+  if (op->g64) cudaFree(op->g64);
+  if (op->g32) cudaFree(op->g32);
+  cudaGetLastError();
+  delete op;
+}

@@ -1,0 +1,1093 @@
+// Block conjugate gradient for the basis solutions (Eq. 3-4, Sec. III-A).
+//
+// All s right-hand sides of a chip share its operator A and one Krylov
+// space.  One iteration, per chip:
+//   Q = A P,   Gamma = P^T Q,   rho = P^T R                 (spmm_gram)
+//   factor D Gamma D (D = diag(Gamma)^-1/2) by diagonal-pivoted Cholesky,
+//   deflate pivots <= tol, alpha = Gamma^-1 rho             (small_solve, alpha)
+//   X += P alpha,  R -= Q alpha,  W = Q^T R,  ||R_j||^2     (update_gram)
+//   beta = -Gamma^-1 W, per-column convergence test         (small_solve, beta)
+//   P = R + P beta                                          (p_update)
+// Deflated columns get zero rows in alpha and beta.
+//
+// Precision.  FP64 runs the loop in float64.  MIXED runs it in float32 with
+// the Gram products folded into compensated float32 sums and reduced in
+// float64, the s x s factorisation and solves in float64, inside float64
+// iterative refinement on the true residual B - A X.
+//
+// Layout.  Block vectors are [n_total][S] with S in {8, 16, 32, 64} (the
+// caller's s columns zero-padded).  A CTA processes one unit: a contiguous
+// range of one chip's cells, in tiles of TC cells (TPC threads per cell, 16
+// bytes of columns per thread).  Gram partials are reduced inside the CTA
+// and added to per-chip float64 accumulators.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <type_traits>
+#include <vector>
+
+#include "common.cuh"
+
+namespace blockoa {
+
+// ---------------------------------------------------------------- geometry
+// A thread owns CPT = 4 consecutive cells x V columns (16 bytes of each of
+// the four rows).  TPR threads span the S columns and TCG thread groups span
+// the TC = 4 * TCG cells of a tile.  Tiles are staged in shared memory
+// transposed, [column][cell] with a padded row of LD cells, so every step of
+// the s x s products reads 16-byte vectors of four cells: the updates read
+// three vectors per 32 FMAs, the Gram blocks eight vectors per 64 FMAs.
+template <typename T, int S>
+struct BK {
+  static constexpr int V = 16 / (int)sizeof(T);  // columns per thread
+  static constexpr int CPT = 4;                  // cells per thread
+  static constexpr int TPR = S / V;              // threads across the columns
+  static constexpr int TCG = 256 / TPR;          // thread groups along the cells
+  static constexpr int TC = TCG * CPT;           // cells per tile
+  static constexpr int LD = TC;                  // row of a transposed tile (swizzled)
+  static constexpr int NB = S / 4;               // 4x4 Gram blocks per side
+  static constexpr int NT = NB * NB;             // threads per Gram group
+  static constexpr int NG = 256 / NT;            // Gram groups (split the tile's cells)
+  static constexpr int GC = TC / NG;             // cells per group and tile
+  static_assert(TPR >= 1 && TC % 4 == 0 && NG >= 1 && GC % 4 == 0, "bad block geometry");
+  static_assert((TC / V) % 8 == 0, "swizzle needs at least eight 16-byte units per row");
+};
+
+template <typename T>
+__device__ __forceinline__ void vload(T *dst, const T *src);
+template <>
+__device__ __forceinline__ void vload<float>(float *d, const float *s) {
+  float4 v = *reinterpret_cast<const float4 *>(s);
+  d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void vload<double>(double *d, const double *s) {
+  double2 v = *reinterpret_cast<const double2 *>(s);
+  d[0] = v.x; d[1] = v.y;
+}
+template <typename T>
+__device__ __forceinline__ void vstore(T *dst, const T *src);
+template <>
+__device__ __forceinline__ void vstore<float>(float *d, const float *s) {
+  *reinterpret_cast<float4 *>(d) = make_float4(s[0], s[1], s[2], s[3]);
+}
+template <>
+__device__ __forceinline__ void vstore<double>(double *d, const double *s) {
+  *reinterpret_cast<double2 *>(d) = make_double2(s[0], s[1]);
+}
+// Transposed tiles are [column][cell] rows of LD = TC cells.  The 16-byte
+// units of a row are XOR-swizzled with (row / 4) & 7 so that the transposed
+// writes (rows four apart), the update reads (one row, four units) and the
+// 4x4 Gram reads (four or eight rows, one unit) each spread over all eight
+// 16-byte bank groups.
+template <typename T>
+__device__ __forceinline__ int swz(int row, int cell) {
+  constexpr int V = 16 / sizeof(T);
+  return (((cell / V) ^ ((row >> 2) & 7)) * V) + (cell % V);
+}
+// four consecutive cells (multiple of 4) of a tile row
+template <typename T, int LD>
+__device__ __forceinline__ void ld4(T *d, const T *tile, int row, int cell) {
+  const T *r = tile + row * LD;
+  vload<T>(d, r + swz<T>(row, cell));
+  if (sizeof(T) == 8) vload<T>(d + 2, r + swz<T>(row, cell + 2));
+}
+template <typename T, int LD>
+__device__ __forceinline__ void st4(T *tile, const T *s, int row, int cell) {
+  T *r = tile + row * LD;
+  vstore<T>(r + swz<T>(row, cell), s);
+  if (sizeof(T) == 8) vstore<T>(r + swz<T>(row, cell + 2), s + 2);
+}
+
+__device__ __forceinline__ float4 coef_ld(const float *g, long long a) {
+  return __ldg(reinterpret_cast<const float4 *>(g) + a);
+}
+__device__ __forceinline__ double4 coef_ld(const double *g, long long a) {
+  const double2 lo = __ldg(reinterpret_cast<const double2 *>(g) + 2 * a);
+  const double2 hi = __ldg(reinterpret_cast<const double2 *>(g) + 2 * a + 1);
+  return make_double4(lo.x, lo.y, hi.x, hi.y);
+}
+
+// Load this thread's 4 cells x V columns of a [cell][S] block (zeros past `end`).
+template <typename T, int S>
+__device__ __forceinline__ void load_block(T (&x)[4][16 / sizeof(T)], const T *G, long long c0,
+                                           long long end, int j0) {
+  constexpr int V = 16 / sizeof(T);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (c0 + k < end) vload<T>(x[k], G + (c0 + k) * S + j0);
+    else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) x[k][v] = T(0);
+    }
+  }
+}
+template <typename T, int S>
+__device__ __forceinline__ void store_block(T *G, const T (&x)[4][16 / sizeof(T)], long long c0,
+                                            long long end, int j0) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (c0 + k < end) vstore<T>(G + (c0 + k) * S + j0, x[k]);
+}
+// Write the block transposed into a [column][cell] tile at local cell cl0.
+template <typename T, int LD>
+__device__ __forceinline__ void put_tile(T *tile, const T (&x)[4][16 / sizeof(T)], int cl0, int j0) {
+  constexpr int V = 16 / sizeof(T);
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    T col[4] = {x[0][v], x[1][v], x[2][v], x[3][v]};
+    st4<T, LD>(tile, col, j0 + v, cl0);
+  }
+}
+
+// acc[a*4+b] += sum over this group's cells of A[i0+a][c] * B[j0+b][c]
+// for transposed tiles A, B.
+template <typename T, int S>
+__device__ __forceinline__ void gram_tile(T *acc, const T *A, const T *B, int i0, int j0, int grp) {
+  using G = BK<T, S>;
+  const int cbeg = grp * G::GC;
+#pragma unroll 2
+  for (int c = cbeg; c < cbeg + G::GC; c += 4) {
+    T a[4][4], b[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ld4<T, G::LD>(a[q], A, i0 + q, c);
+      ld4<T, G::LD>(b[q], B, j0 + q, c);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[q * 4 + r] += a[q][k] * b[r][k];
+  }
+}
+
+// Reduce the NG groups' 4x4 blocks in shared memory and add the S x S
+// result to the chip's float64 accumulator.  float partial sums (each over
+// at most a few hundred cells of one CTA) are combined across groups with
+// error-free transformations, so an entry costs one float64 conversion and
+// one float64 atomic per CTA; float64 arithmetic runs at 1/64 of the float32
+// rate on this part.
+template <typename T, int S>
+__device__ void gram_flush(const T *acc, double *red, double *dst) {
+  using G = BK<T, S>;
+  const int t = threadIdx.x;
+  const int g = t / G::NT, w = t % G::NT;
+  const int i0 = (w / G::NB) * 4, j0 = (w % G::NB) * 4;
+  T *rt = reinterpret_cast<T *>(red);
+#pragma unroll
+  for (int e = 0; e < 16; ++e) rt[g * S * S + (i0 + e / 4) * S + j0 + (e % 4)] = acc[e];
+  __syncthreads();
+  for (int e = t; e < S * S; e += 256) {
+    if constexpr (sizeof(T) == 4) {
+      float hi = 0.f, lo = 0.f;
+      for (int gg = 0; gg < G::NG; ++gg) {
+        const float v = rt[gg * S * S + e];
+        const float sum = hi + v;
+        const float bp = sum - hi;
+        lo += (hi - (sum - bp)) + (v - bp);
+        hi = sum;
+      }
+      atomicAdd(dst + e, (double)hi + (double)lo);
+    } else {
+      double sum = 0.0;
+      for (int gg = 0; gg < G::NG; ++gg) sum += rt[gg * S * S + e];
+      atomicAdd(dst + e, sum);
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int S>
+constexpr size_t tile_bytes() { return (size_t)S * BK<T, S>::LD * sizeof(T); }
+constexpr size_t kRedBytes = 256 * 16 * sizeof(double);
+
+// ---------------------------------------------------------------- kernels
+// Q = A P on the block layout; Gamma += P^T Q and rho += P^T R per chip.
+template <typename T, int S>
+__global__ void __launch_bounds__(256)
+spmm_gram_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chips,
+                 const ChipSolveState *__restrict__ state, const T *__restrict__ g,
+                 const T *__restrict__ P, const T *__restrict__ R, T *__restrict__ Q,
+                 double *__restrict__ gram, double *__restrict__ rho) {
+  using G = BK<T, S>;
+  constexpr int V = G::V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *sP = reinterpret_cast<T *>(smem);
+  T *sQ = sP + S * G::LD;
+  T *sR = sQ + S * G::LD;
+  double *red = reinterpret_cast<double *>(sR + S * G::LD);
+  const Unit u = units[blockIdx.x];
+  if (!state[u.chip].active) return;
+  const ChipDev ch = chips[u.chip];
+  const int nx = ch.nx, ny = ch.ny, nz = ch.nz, nxny = nx * ny;
+  const int t = threadIdx.x;
+  const int j0 = (t % G::TPR) * V, cl0 = (t / G::TPR) * 4;
+  const int grp = t / G::NT, w = t % G::NT;
+  const int i0 = (w / G::NB) * 4, k0 = (w % G::NB) * 4;
+  T aq[16], ar[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) { aq[e] = T(0); ar[e] = T(0); }
+  for (long long base = u.begin; base < u.end; base += G::TC) {
+    T pc[4][V], qv[4][V], rv[4][V];
+    load_block<T, S>(pc, P, base + cl0, u.end, j0);
+    load_block<T, S>(rv, R, base + cl0, u.end, j0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const long long a = base + cl0 + k;
+#pragma unroll
+      for (int v = 0; v < V; ++v) qv[k][v] = T(0);
+      if (a < u.end) {
+        const int loc = (int)(a - ch.off);
+        const int x = loc % nx, y = (loc / nx) % ny, z = loc / nxny;
+        const auto c4 = coef_ld(g, a);
+#pragma unroll
+        for (int v = 0; v < V; ++v) qv[k][v] = c4.w * pc[k][v];
+        auto nb = [&](long long b, T gg) {
+          T o[V];
+          vload<T>(o, P + b * S + j0);
+#pragma unroll
+          for (int v = 0; v < V; ++v) qv[k][v] += gg * (pc[k][v] - o[v]);
+        };
+        if (x + 1 < nx) nb(a + 1, c4.x);
+        if (x > 0) nb(a - 1, coef_ld(g, a - 1).x);
+        if (y + 1 < ny) nb(a + nx, c4.y);
+        if (y > 0) nb(a - nx, coef_ld(g, a - nx).y);
+        if (z + 1 < nz) nb(a + nxny, c4.z);
+        if (z > 0) nb(a - nxny, coef_ld(g, a - nxny).z);
+      }
+    }
+    store_block<T, S>(Q, qv, base + cl0, u.end, j0);
+    put_tile<T, G::LD>(sP, pc, cl0, j0);
+    put_tile<T, G::LD>(sQ, qv, cl0, j0);
+    put_tile<T, G::LD>(sR, rv, cl0, j0);
+    __syncthreads();
+    gram_tile<T, S>(aq, sP, sQ, i0, k0, grp);
+    gram_tile<T, S>(ar, sP, sR, i0, k0, grp);
+    __syncthreads();
+  }
+  gram_flush<T, S>(aq, red, gram + (long long)u.chip * S * S);
+  gram_flush<T, S>(ar, red, rho + (long long)u.chip * S * S);
+}
+
+// X += P alpha, R -= Q alpha; W += Q^T R_new and rn2 += ||R_new_j||^2.
+template <typename T, int S>
+__global__ void __launch_bounds__(256)
+update_gram_kernel(const Unit *__restrict__ units, const ChipSolveState *__restrict__ state,
+                   const T *__restrict__ alpha, const T *__restrict__ P, const T *__restrict__ Q,
+                   T *__restrict__ X, T *__restrict__ R, double *__restrict__ wgram,
+                   double *__restrict__ rn2) {
+  using G = BK<T, S>;
+  constexpr int V = G::V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *sP = reinterpret_cast<T *>(smem);
+  T *sQ = sP + S * G::LD;
+  T *sR = sQ + S * G::LD;
+  T *sA = sR + S * G::LD;
+  double *red = reinterpret_cast<double *>(sA + S * S);
+  const Unit u = units[blockIdx.x];
+  if (!state[u.chip].active) return;
+  const int t = threadIdx.x;
+  const T *al = alpha + (long long)u.chip * S * S;
+  for (int e = t; e < S * S; e += 256) sA[e] = al[e];
+  const int j0 = (t % G::TPR) * V, cl0 = (t / G::TPR) * 4;
+  const int grp = t / G::NT, w = t % G::NT;
+  const int i0 = (w / G::NB) * 4, k0 = (w % G::NB) * 4;
+  T aw[16], rn[V];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) aw[e] = T(0);
+#pragma unroll
+  for (int v = 0; v < V; ++v) rn[v] = T(0);
+  for (long long base = u.begin; base < u.end; base += G::TC) {
+    {
+      T pv[4][V], qv[4][V];
+      load_block<T, S>(pv, P, base + cl0, u.end, j0);
+      load_block<T, S>(qv, Q, base + cl0, u.end, j0);
+      put_tile<T, G::LD>(sP, pv, cl0, j0);
+      put_tile<T, G::LD>(sQ, qv, cl0, j0);
+    }
+    T xv[4][V], rv[4][V];
+    load_block<T, S>(xv, X, base + cl0, u.end, j0);
+    load_block<T, S>(rv, R, base + cl0, u.end, j0);
+    __syncthreads();
+#pragma unroll 4
+    for (int i = 0; i < S; ++i) {
+      T p4[4], q4[4], av[V];
+      ld4<T, G::LD>(p4, sP, i, cl0);
+      ld4<T, G::LD>(q4, sQ, i, cl0);
+      vload<T>(av, sA + i * S + j0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          xv[k][v] += p4[k] * av[v];
+          rv[k][v] -= q4[k] * av[v];
+        }
+    }
+    store_block<T, S>(X, xv, base + cl0, u.end, j0);
+    store_block<T, S>(R, rv, base + cl0, u.end, j0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int v = 0; v < V; ++v) rn[v] += rv[k][v] * rv[k][v];  // zero past the end
+    put_tile<T, G::LD>(sR, rv, cl0, j0);
+    __syncthreads();
+    gram_tile<T, S>(aw, sQ, sR, i0, k0, grp);
+    __syncthreads();
+  }
+  gram_flush<T, S>(aw, red, wgram + (long long)u.chip * S * S);
+  // column norms: threads with equal (t % TPR) own the same columns
+  T *rt = reinterpret_cast<T *>(red);
+#pragma unroll
+  for (int v = 0; v < V; ++v) rt[t * V + v] = rn[v];
+  __syncthreads();
+  if (t < G::TPR) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      double sum = 0.0;
+      T hi = T(0), lo = T(0);
+      for (int tt = t; tt < 256; tt += G::TPR) {
+        const T x = rt[tt * V + v];
+        const T s2 = hi + x;
+        const T bp = s2 - hi;
+        lo += (hi - (s2 - bp)) + (x - bp);
+        hi = s2;
+      }
+      sum = (double)hi + (double)lo;
+      atomicAdd(rn2 + (long long)u.chip * S + t * V + v, sum);
+    }
+  }
+}
+
+// P = R + P beta (one tile per CTA).
+template <typename T, int S>
+__global__ void __launch_bounds__(256)
+p_update_kernel(const Unit *__restrict__ units, const ChipSolveState *__restrict__ state,
+                const T *__restrict__ beta, const T *__restrict__ R, T *__restrict__ P) {
+  using G = BK<T, S>;
+  constexpr int V = G::V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *sP = reinterpret_cast<T *>(smem);
+  T *sB = sP + S * G::LD;
+  const Unit u = units[blockIdx.x];
+  if (!state[u.chip].active) return;
+  const int t = threadIdx.x;
+  const T *be = beta + (long long)u.chip * S * S;
+  for (int e = t; e < S * S; e += 256) sB[e] = be[e];
+  const int j0 = (t % G::TPR) * V, cl0 = (t / G::TPR) * 4;
+  for (long long base = u.begin; base < u.end; base += G::TC) {
+    {
+      T pv[4][V];
+      load_block<T, S>(pv, P, base + cl0, u.end, j0);
+      put_tile<T, G::LD>(sP, pv, cl0, j0);
+    }
+    T rv[4][V];
+    load_block<T, S>(rv, R, base + cl0, u.end, j0);
+    __syncthreads();
+#pragma unroll 4
+    for (int i = 0; i < S; ++i) {
+      T p4[4], bv[V];
+      ld4<T, G::LD>(p4, sP, i, cl0);
+      vload<T>(bv, sB + i * S + j0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int v = 0; v < V; ++v) rv[k][v] += p4[k] * bv[v];
+    }
+    store_block<T, S>(P, rv, base + cl0, u.end, j0);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- small s x s solves
+// Per chip, in float64: Jacobi-scaled, diagonal-pivoted Cholesky of the
+// Gram matrix with deflation (factor kernel, one CTA per chip), then
+// alpha = Gamma^-1 rho and beta = -Gamma^-1 W by substitution (solve
+// kernels, S/4 CTAs per chip, one warp per right-hand-side column).  One
+// thread evaluates each pivot's square root and reciprocal; substitutions
+// multiply by the stored reciprocals.  Accumulators are cleared by the
+// kernel that runs after their last reader: the factor kernel clears W and
+// ||R||^2 (read by the previous beta solve), the beta solve clears Gamma and
+// rho (read by the factor kernel and the alpha solve).
+struct SmallArgs {
+  ChipSolveState *state;
+  double *gram;     // [chip][S][S] Gamma accumulator
+  double *rho;      // [chip][S][S] rho = P^T R accumulator
+  double *wg;       // [chip][S][S] W = Q^T R accumulator
+  double *rn2;      // [chip][S] ||R_j||^2 accumulator
+  const double *target2;  // [chip][S] squared per-column targets
+  double *lfac;     // [chip][S][S] pivot-ordered lower-triangular factor L[i][k]
+  double *rinv;     // [chip][S] 1 / L[i][i]
+  int *perm;        // [chip][S] kept columns in pivot order
+  double *dsc;      // [chip][S] scaling diagonal
+  int *rank;        // [chip]
+  void *alpha;      // [chip][S][S] in the loop's precision
+  void *beta;       // [chip][S][S]
+  int s;            // caller's columns (for deflation counts)
+  int maxiter;      // limit on total iterations per chip
+  double tol;       // deflation threshold on scaled pivots
+};
+
+// 2^e as a float64 for -1022 <= e <= 1023.
+__device__ __forceinline__ double pow2(int e) {
+  return __longlong_as_double((long long)(e + 1023) << 52);
+}
+// 1/sqrt(x) in float64 for normal x > 0.  x = m 4^h with m in [1, 4) (exact
+// power-of-two scaling), float seed for m (about 2^-23 relative error), then
+// one Newton step y <- y (3 - m y^2) / 2, which squares the relative error
+// (about 2^-45).  Each float64 instruction holds this part's float64 pipe for
+// a whole warp's worth of cycles, so the pivot path keeps them few.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  const int ex = (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
+  const int h = ex >> 1;
+  const double m = x * pow2(-2 * h);
+  const double y = (double)rsqrtf((float)m);
+  return (y * fma(-0.5 * m, y * y, 1.5)) * pow2(-h);
+}
+
+template <int S>
+__host__ __device__ constexpr size_t factor_smem_bytes() { return 2 * sizeof(double) * S * (S + 1); }
+
+template <int S>
+__global__ void __launch_bounds__(256) factor_kernel(SmallArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double (*W)[S + 1] = reinterpret_cast<double (*)[S + 1]>(smem);   // scaled Gram, lower triangle
+  double (*Lc)[S + 1] = W + S;                                      // Lc[k][row]: column k of L
+  __shared__ double d[S];
+  __shared__ int perm[S];
+  __shared__ int removed[S];
+  __shared__ double rv[S];
+  __shared__ int s_piv, s_bad;
+  __shared__ double s_sq, s_inv;
+  const int c = blockIdx.x;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  ChipSolveState &st = A.state[c];
+  if (!st.active) return;
+  if (t == 0) s_bad = 0;
+  __syncthreads();
+  const double *gacc = A.gram + (long long)c * S * S;
+  for (int e = t; e < S * S; e += 256) {
+    const int a = e / S, b = e % S;
+    if (b <= a) {
+      const double v = 0.5 * (gacc[a * S + b] + gacc[b * S + a]);
+      if (!isfinite(v)) s_bad = 1;
+      W[a][b] = v;
+    }
+  }
+  // W and ||R||^2 of the previous iteration were consumed by its beta solve
+  for (int e = t; e < S * S; e += 256) A.wg[(long long)c * S * S + e] = 0.0;
+  if (t < S) A.rn2[(long long)c * S + t] = 0.0;
+  __syncthreads();
+  if (t < S) {
+    const double w = W[t][t];
+    d[t] = (w > 1e-290 && isfinite(w)) ? rsqrt_nr(w) : 0.0;
+    removed[t] = d[t] == 0.0;
+  }
+  __syncthreads();
+  for (int e = t; e < S * S; e += 256) {
+    const int a = e / S, b = e % S;
+    if (b <= a) W[a][b] *= d[a] * d[b];
+  }
+  __syncthreads();
+  int k = 0;
+  for (; k < S; ++k) {
+    if (warp == 0) {
+      // largest remaining scaled diagonal, lowest index on ties; positive
+      // float64 values order like their bit patterns read as int64
+      long long best = LLONG_MIN;
+      int bi = S;
+      for (int i = lane; i < S; i += 32) {
+        const long long v = __double_as_longlong(W[i][i]);
+        if (!removed[i] && v > best) { best = v; bi = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        s_piv = bi;
+        const double bv = __longlong_as_double(best);
+        const bool ok = bi < S && best > 0 && bv > A.tol;
+        const double y = ok ? rsqrt_nr(bv) : 0.0;
+        s_inv = y;
+        s_sq = bv * y;
+        if (!ok) s_piv = S;
+      }
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p >= S) break;
+    const double sq = s_sq, inv = s_inv;
+    if (t < S) Lc[k][t] = removed[t] ? 0.0 : (t == p ? sq : (t > p ? W[t][p] : W[p][t]) * inv);
+    __syncthreads();
+    if (t == 0) { removed[p] = 1; perm[k] = p; rv[k] = inv; }
+    // rank-1 update of the remaining rows (row per warp; removed rows skipped)
+    for (int a = warp; a < S; a += 8) {
+      if (removed[a] || a == p) continue;
+      const double la = Lc[k][a];
+      for (int b = lane; b <= a; b += 32) W[a][b] -= la * Lc[k][b];
+    }
+    __syncthreads();
+  }
+  const int r = k;
+  // Substitution factors, pivot order, scaled by the reciprocal pivots so a
+  // substitution step is one fused multiply-add:
+  //   F[i][k] = L[i][k] / L[k][k]  (i > k, forward),
+  //   F[i][k] = L[k][i] / L[k][k]  (i < k, backward),  F[i][i] = 0.
+  double *L = A.lfac + (long long)c * S * S;
+  for (int e = t; e < S * S; e += 256) {
+    const int i = e / S, kk = e % S;
+    double v = 0.0;
+    if (i < r && kk < r && i > kk) v = Lc[kk][perm[i]] * rv[kk];
+    else if (i < r && kk < r && i < kk) v = Lc[i][perm[kk]] * rv[kk];
+    L[e] = v;
+  }
+  if (t < S) {
+    A.dsc[(long long)c * S + t] = d[t];
+    A.perm[(long long)c * S + t] = t < r ? perm[t] : -1;
+    A.rinv[(long long)c * S + t] = t < r ? rv[t] : 0.0;
+  }
+  if (t == 0) {
+    A.rank[c] = r;
+    st.rank = r;
+    st.deflated += (A.s - r) > 0 ? (A.s - r) : 0;
+    if (s_bad || r == 0) {
+      st.status = BLOCKOA_ERR_BREAKDOWN;
+      st.active = 0;
+    }
+  }
+}
+
+// Gamma_KK Z = RHS_K for four columns per CTA (one warp each); deflated rows
+// of the result are zero.  The beta solve's CTA 0 also clears Gamma and rho
+// and runs the per-column convergence test of the updated residual.
+template <typename T, int S, bool ALPHA>
+__global__ void __launch_bounds__(32) trsolve_kernel(SmallArgs A) {
+  constexpr int NSPLIT = S;
+  constexpr int RL = (S + 31) / 32;  // rows per lane
+  __shared__ double L[S][S + 1];
+  __shared__ double rinv[S], d[S];  // rinv is 0 past the rank
+  __shared__ int perm[S];
+  const int c = blockIdx.x / NSPLIT;
+  const int split = blockIdx.x % NSPLIT;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  ChipSolveState &st = A.state[c];
+  if (!st.active) return;
+  const int r = A.rank[c];
+  const double *Lg = A.lfac + (long long)c * S * S;
+  for (int e = t; e < S * S; e += 32) L[e / S][e % S] = Lg[e];
+  for (int i = t; i < S; i += 32) {
+    rinv[i] = A.rinv[(long long)c * S + i];
+    d[i] = A.dsc[(long long)c * S + i];
+    perm[i] = A.perm[(long long)c * S + i];
+  }
+  __syncthreads();
+  const double *rhs = (ALPHA ? A.rho : A.wg) + (long long)c * S * S;
+  T *out = reinterpret_cast<T *>(ALPHA ? A.alpha : A.beta) + (long long)c * S * S;
+  const int j = split;
+  (void)warp;
+  double y[RL];
+  int pr[RL];
+#pragma unroll
+  for (int q = 0; q < RL; ++q) {
+    const int i = lane + 32 * q;
+    pr[q] = (i < r) ? perm[i] : -1;
+    y[q] = (i < r) ? d[pr[q]] * rhs[(long long)pr[q] * S + j] : 0.0;
+  }
+  // L z = y: y_i -= (L_ik / L_kk) y_k, then z = y / diag(L)
+  for (int k = 0; k < r; ++k) {
+    const double yk = __shfl_sync(0xffffffffu, y[k >> 5], k & 31);
+#pragma unroll
+    for (int q = 0; q < RL; ++q) {
+      const int i = lane + 32 * q;
+      const double f = (i > k && i < S) ? L[i < S ? i : 0][k] : 0.0;
+      y[q] -= f * yk;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < RL; ++q) y[q] *= rinv[min(lane + 32 * q, S - 1)];
+  // L^T x = z: z_i -= (L_ki / L_kk) z_k, then x = z / diag(L)
+  for (int k = r - 1; k >= 0; --k) {
+    const double yk = __shfl_sync(0xffffffffu, y[k >> 5], k & 31);
+#pragma unroll
+    for (int q = 0; q < RL; ++q) {
+      const int i = lane + 32 * q;
+      const double f = (i < k) ? L[i][k] : 0.0;
+      y[q] -= f * yk;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < RL; ++q) y[q] *= rinv[min(lane + 32 * q, S - 1)];
+#pragma unroll
+  for (int q = 0; q < RL; ++q) {
+    const int i = lane + 32 * q;
+    if (i < S) out[(long long)i * S + j] = T(0);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < RL; ++q) {
+    const int i = lane + 32 * q;
+    if (i < r) out[(long long)pr[q] * S + j] = (T)((ALPHA ? 1.0 : -1.0) * d[pr[q]] * y[q]);
+  }
+  if (ALPHA || split != 0) return;
+  for (int e = t; e < S * S; e += 32) {
+    A.gram[(long long)c * S * S + e] = 0.0;
+    A.rho[(long long)c * S * S + e] = 0.0;
+  }
+  __shared__ int s_conv, s_bad;
+  if (t == 0) { s_conv = 1; s_bad = 0; }
+  __syncthreads();
+  for (int i = t; i < S; i += 32) {
+    const double v = A.rn2[(long long)c * S + i];
+    if (!isfinite(v)) s_bad = 1;
+    if (!(v <= A.target2[(long long)c * S + i])) s_conv = 0;
+  }
+  __syncthreads();
+  if (t == 0) {
+    st.iters += 1;
+    if (s_bad) {
+      st.status = BLOCKOA_ERR_BREAKDOWN;
+      st.active = 0;
+    } else if (s_conv) {
+      st.status = BLOCKOA_OK;
+      st.active = 0;
+    } else if (st.iters >= A.maxiter) {
+      st.status = BLOCKOA_ERR_NOT_CONVERGED;
+      st.active = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- glue kernels
+// dst[a][j] = src[a][j] for j < s, 0 for s <= j < S (float64).
+__global__ void pad_cols_kernel(const double *__restrict__ src, double *__restrict__ dst,
+                                long long n, int s, int S) {
+  const long long total = n * S;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long a = i / S;
+    const int j = (int)(i % S);
+    dst[i] = (src && j < s) ? src[a * s + j] : 0.0;
+  }
+}
+
+__global__ void unpad_cols_kernel(const double *__restrict__ src, double *__restrict__ dst,
+                                  long long n, int s, int S) {
+  const long long total = n * s;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    dst[i] = src[(i / s) * S + (i % s)];
+  }
+}
+
+// Squared column norms of a float64 block per chip: out[chip][j] += sum_a v^2.
+template <int S>
+__global__ void col_norms_kernel(const Unit *__restrict__ units, const double *__restrict__ V,
+                                 double *__restrict__ out) {
+  const Unit u = units[blockIdx.x];
+  const int j = threadIdx.x % S;
+  const int r0 = threadIdx.x / S;
+  constexpr int RPB = 256 / S;
+  double s = 0.0;
+  for (long long a = u.begin + r0; a < u.end; a += RPB) {
+    const double v = V[a * S + j];
+    s += v * v;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x < S) {
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < 256; k += S) acc += red[k];
+    atomicAdd(out + (long long)u.chip * S + threadIdx.x, acc);
+  }
+}
+
+// Start an inner solve on A D = R64: R = R64 / sigma_j, P = R, D = 0.
+template <typename T, int S>
+__global__ void inner_init_kernel(const Unit *__restrict__ units, const int *__restrict__ outer_active,
+                                  const double *__restrict__ R64, const double *__restrict__ inv_sigma,
+                                  T *__restrict__ R, T *__restrict__ P, T *__restrict__ D) {
+  const Unit u = units[blockIdx.x];
+  if (!outer_active[u.chip]) return;
+  const double *is = inv_sigma + (long long)u.chip * S;
+  for (long long i = u.begin * S + threadIdx.x; i < u.end * S; i += blockDim.x) {
+    const T v = (T)(R64[i] * is[i % S]);
+    R[i] = v;
+    P[i] = v;
+    D[i] = T(0);
+  }
+}
+
+// X64 += sigma_j D.
+template <typename T, int S>
+__global__ void accumulate_kernel(const Unit *__restrict__ units, const int *__restrict__ outer_active,
+                                  const double *__restrict__ sigma, const T *__restrict__ D,
+                                  double *__restrict__ X64) {
+  const Unit u = units[blockIdx.x];
+  if (!outer_active[u.chip]) return;
+  const double *sg = sigma + (long long)u.chip * S;
+  for (long long i = u.begin * S + threadIdx.x; i < u.end * S; i += blockDim.x)
+    X64[i] += sg[i % S] * (double)D[i];
+}
+
+// ---------------------------------------------------------------- workspace
+struct SolveWS {
+  int S = 0, prec = -1;
+  long long n = 0;
+  int n_chips = 0;
+  // float64 block vectors
+  double *B64 = nullptr, *X64 = nullptr, *R64 = nullptr;
+  // loop vectors in the loop's precision
+  void *D = nullptr, *R = nullptr, *P = nullptr, *Q = nullptr;
+  // per-chip small buffers
+  double *gram = nullptr, *rho = nullptr, *wg = nullptr, *rn2 = nullptr, *rn64 = nullptr,
+         *bn2 = nullptr, *target2 = nullptr, *sigma = nullptr, *inv_sigma = nullptr,
+         *lfac = nullptr, *dsc = nullptr, *rinv = nullptr;
+  int *perm = nullptr, *rank = nullptr, *outer_active = nullptr;
+  void *alpha = nullptr, *beta = nullptr;
+  ChipSolveState *state = nullptr;
+  Unit *units = nullptr;        // loop units
+  int n_units = 0;
+  Unit *units_tile = nullptr;   // one tile per unit (P update)
+  int n_units_tile = 0;
+  Unit *units_small = nullptr;  // elementwise units
+  int n_units_small = 0;
+  // host staging (pinned)
+  ChipSolveState *h_state = nullptr;
+  double *h_small = nullptr;    // [4][chip][S] staging
+  int *h_active = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_iters = 0, graph_maxiter = -1, graph_s = -1;
+  double graph_tol = -1.0;
+  std::vector<void *> allocs;
+};
+
+void free_solve_ws(void *p) {
+  SolveWS *ws = (SolveWS *)p;
+  if (!ws) return;
+  if (ws->graph) cudaGraphExecDestroy(ws->graph);
+  if (ws->cap) cudaStreamDestroy(ws->cap);
+  for (void *a : ws->allocs) cudaFree(a);
+  if (ws->h_state) cudaFreeHost(ws->h_state);
+  if (ws->h_small) cudaFreeHost(ws->h_small);
+  if (ws->h_active) cudaFreeHost(ws->h_active);
+  cudaGetLastError();
+  delete ws;
+}
+
+template <typename P>
+static cudaError_t ws_alloc(SolveWS *ws, P **p, size_t bytes) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes < 16 ? 16 : bytes);
+  if (e == cudaSuccess) {
+    ws->allocs.push_back(q);
+    *p = (P *)q;
+  }
+  return e;
+}
+
+template <typename T, int S>
+constexpr size_t spmm_smem() { return 3 * tile_bytes<T, S>() + kRedBytes; }
+template <typename T, int S>
+constexpr size_t update_smem() { return 3 * tile_bytes<T, S>() + S * S * sizeof(T) + kRedBytes; }
+template <typename T, int S>
+constexpr size_t pupdate_smem() { return tile_bytes<T, S>() + S * S * sizeof(T); }
+
+template <typename T, int S>
+static void set_smem_limits() {
+  static bool done = false;
+  if (done) return;
+  done = true;
+  cudaFuncSetAttribute(spmm_gram_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)spmm_smem<T, S>());
+  cudaFuncSetAttribute(update_gram_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)update_smem<T, S>());
+  cudaFuncSetAttribute(p_update_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pupdate_smem<T, S>());
+  cudaFuncSetAttribute(factor_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)factor_smem_bytes<S>());
+}
+
+// One block-CG iteration for every active chip.
+template <typename T, int S>
+static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const SmallArgs &sa,
+                             cudaStream_t st) {
+  const T *g = sizeof(T) == 4 ? (const T *)op->g32 : (const T *)op->g64;
+  const unsigned nsolve = (unsigned)(ws->n_chips * S);
+  spmm_gram_kernel<T, S><<<ws->n_units, 256, spmm_smem<T, S>(), st>>>(
+      ws->units, op->d_chips, ws->state, g, (const T *)ws->P, (const T *)ws->R, (T *)ws->Q,
+      ws->gram, ws->rho);
+  factor_kernel<S><<<ws->n_chips, 256, factor_smem_bytes<S>(), st>>>(sa);
+  trsolve_kernel<T, S, true><<<nsolve, 32, 0, st>>>(sa);
+  update_gram_kernel<T, S><<<ws->n_units, 256, update_smem<T, S>(), st>>>(
+      ws->units, ws->state, (const T *)ws->alpha, (const T *)ws->P, (const T *)ws->Q,
+      (T *)ws->D, (T *)ws->R, ws->wg, ws->rn2);
+  trsolve_kernel<T, S, false><<<nsolve, 32, 0, st>>>(sa);
+  p_update_kernel<T, S><<<ws->n_units_tile, 256, pupdate_smem<T, S>(), st>>>(
+      ws->units_tile, ws->state, (const T *)ws->beta, (const T *)ws->R, (T *)ws->P);
+}
+
+template <typename T, int S>
+static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
+                      const blockoa_solve_opts *o, blockoa_solve_stats *stats, cudaStream_t st) {
+  const int prec = sizeof(T) == 4 ? BLOCKOA_MIXED : BLOCKOA_FP64;
+  const int nc = op->n_chips;
+  const long long n = op->n_total;
+  SolveWS *ws = (SolveWS *)op->solve_ws;
+  if (!ws || ws->S != S || ws->prec != prec || ws->n != n) {
+    free_solve_ws(ws);
+    op->solve_ws = nullptr;
+    ws = new SolveWS();
+    op->solve_ws = ws;
+    ws->S = S; ws->prec = prec; ws->n = n; ws->n_chips = nc;
+    const size_t blk64 = sizeof(double) * (size_t)n * S, blkT = sizeof(T) * (size_t)n * S;
+    const size_t sm = sizeof(double) * (size_t)nc * S * S, sv = sizeof(double) * (size_t)nc * S;
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->B64, blk64));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->X64, blk64));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->R64, blk64));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->D, blkT));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->R, blkT));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->P, blkT));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->Q, blkT));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->gram, sm));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->rho, sm));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->wg, sm));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->lfac, sm));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->alpha, sizeof(T) * (size_t)nc * S * S));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->beta, sizeof(T) * (size_t)nc * S * S));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->rn2, sv));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->rn64, sv));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->bn2, sv));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->target2, sv));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->sigma, sv));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->inv_sigma, sv));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->dsc, sv));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->rinv, sv));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->perm, sizeof(int) * (size_t)nc * S));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->rank, sizeof(int) * (size_t)nc));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->outer_active, sizeof(int) * (size_t)nc));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->state, sizeof(ChipSolveState) * (size_t)nc));
+    // loop units: about two CTAs per SM over all chips, whole tiles
+    using G = BK<T, S>;
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, op->device);
+    long long cells = pick_unit_cells(op, G::TC, 2 * G::TC, 3 * nsm);
+    std::vector<Unit> units = make_units(op, cells);
+    ws->n_units = (int)units.size();
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->units, sizeof(Unit) * units.size()));
+    BLOCKOA_CUDA(cudaMemcpy(ws->units, units.data(), sizeof(Unit) * units.size(), cudaMemcpyHostToDevice));
+    std::vector<Unit> ut = make_units(op, G::TC);
+    ws->n_units_tile = (int)ut.size();
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->units_tile, sizeof(Unit) * ut.size()));
+    BLOCKOA_CUDA(cudaMemcpy(ws->units_tile, ut.data(), sizeof(Unit) * ut.size(), cudaMemcpyHostToDevice));
+    std::vector<Unit> us = make_units(op, 2048);
+    ws->n_units_small = (int)us.size();
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->units_small, sizeof(Unit) * us.size()));
+    BLOCKOA_CUDA(cudaMemcpy(ws->units_small, us.data(), sizeof(Unit) * us.size(), cudaMemcpyHostToDevice));
+    BLOCKOA_CUDA(cudaMallocHost((void **)&ws->h_state, sizeof(ChipSolveState) * nc));
+    BLOCKOA_CUDA(cudaMallocHost((void **)&ws->h_small, sizeof(double) * 4 * (size_t)nc * S));
+    BLOCKOA_CUDA(cudaMallocHost((void **)&ws->h_active, sizeof(int) * nc));
+    BLOCKOA_CUDA(cudaStreamCreateWithFlags(&ws->cap, cudaStreamNonBlocking));
+    BLOCKOA_CUDA(cudaMemset(ws->gram, 0, sm));
+    BLOCKOA_CUDA(cudaMemset(ws->rho, 0, sm));
+    BLOCKOA_CUDA(cudaMemset(ws->wg, 0, sm));
+    BLOCKOA_CUDA(cudaMemset(ws->rn2, 0, sv));
+    BLOCKOA_CUDA(cudaMemset(ws->lfac, 0, sm));
+    BLOCKOA_CUDA(cudaMemset(ws->rank, 0, sizeof(int) * (size_t)nc));
+    BLOCKOA_CUDA(cudaMemset(ws->perm, 0, sizeof(int) * (size_t)nc * S));
+    set_smem_limits<T, S>();
+  }
+
+  const double rtol = o->rtol;
+  const int maxiter = o->maxiter;
+  const double inner_rtol = prec == BLOCKOA_MIXED ? (o->inner_rtol > 0 ? o->inner_rtol : 1e-3) : 0.0;
+  const int max_refine = o->max_refine > 0 ? o->max_refine : 12;
+  const double tol = o->deflate_tol > 0 ? o->deflate_tol : (prec == BLOCKOA_MIXED ? 1e-6 : 1e-14);
+  const int check_every = o->check_every > 0 ? o->check_every : 8;
+
+  SmallArgs sa;
+  sa.state = ws->state; sa.gram = ws->gram; sa.rho = ws->rho; sa.wg = ws->wg; sa.rn2 = ws->rn2;
+  sa.target2 = ws->target2; sa.lfac = ws->lfac; sa.rinv = ws->rinv; sa.perm = ws->perm;
+  sa.dsc = ws->dsc; sa.rank = ws->rank; sa.alpha = ws->alpha; sa.beta = ws->beta;
+  sa.s = s; sa.maxiter = maxiter; sa.tol = tol;
+
+  // Build (or reuse) the graph of `check_every` iterations.
+  if (!ws->graph || ws->graph_iters != check_every || ws->graph_maxiter != maxiter ||
+      ws->graph_s != s || ws->graph_tol != tol) {
+    if (ws->graph) { cudaGraphExecDestroy(ws->graph); ws->graph = nullptr; }
+    cudaGraph_t graph = nullptr;
+    BLOCKOA_CUDA(cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < check_every; ++k) launch_iteration<T, S>(op, ws, sa, ws->cap);
+    cudaError_t e = cudaStreamEndCapture(ws->cap, &graph);
+    if (e != cudaSuccess) return cuda_status(e, "capture block-CG iterations");
+    e = cudaGraphInstantiate(&ws->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_status(e, "instantiate block-CG graph");
+    ws->graph_iters = check_every;
+    ws->graph_maxiter = maxiter;
+    ws->graph_s = s;
+    ws->graph_tol = tol;
+  }
+
+  // Inputs: padded B and X0, ||B_j||^2.
+  const unsigned eb = (unsigned)std::min<long long>((n * S + 255) / 256, 4096);
+  pad_cols_kernel<<<eb, 256, 0, st>>>(B, ws->B64, n, s, S);
+  pad_cols_kernel<<<eb, 256, 0, st>>>(o->x0, ws->X64, n, s, S);
+  BLOCKOA_CUDA(cudaMemsetAsync(ws->bn2, 0, sizeof(double) * nc * S, st));
+  col_norms_kernel<S><<<ws->n_units_small, 256, 0, st>>>(ws->units_small, ws->B64, ws->bn2);
+  BLOCKOA_CUDA(cudaGetLastError());
+  std::vector<double> bn2((size_t)nc * S);
+  BLOCKOA_CUDA(cudaMemcpyAsync(ws->h_small, ws->bn2, sizeof(double) * nc * S, cudaMemcpyDeviceToHost, st));
+  BLOCKOA_CUDA(cudaStreamSynchronize(st));
+  memcpy(bn2.data(), ws->h_small, sizeof(double) * nc * S);
+
+  std::vector<int> status(nc, BLOCKOA_OK), done(nc, 0), iters(nc, 0), refine(nc, 0), defl(nc, 0);
+  std::vector<double> relres(nc, 0.0), prev_relres(nc, INFINITY);
+  std::vector<double> sig((size_t)nc * S), isig((size_t)nc * S), tgt((size_t)nc * S);
+  for (int step = 0;; ++step) {
+    // True float64 residual R64 = B - A X64 and its column norms.
+    BLOCKOA_CUDA(cudaMemsetAsync(ws->rn64, 0, sizeof(double) * nc * S, st));
+    int rc = launch_residual64(op, ws->B64, ws->X64, ws->R64, S, ws->rn64, st);
+    if (rc) return rc;
+    BLOCKOA_CUDA(cudaMemcpyAsync(ws->h_small, ws->rn64, sizeof(double) * nc * S, cudaMemcpyDeviceToHost, st));
+    BLOCKOA_CUDA(cudaStreamSynchronize(st));
+    int n_active = 0;
+    for (int c = 0; c < nc; ++c) {
+      double worst = 0.0;
+      bool conv = true, finite = true;
+      for (int j = 0; j < S; ++j) {
+        const double r2 = ws->h_small[(size_t)c * S + j], b2 = bn2[(size_t)c * S + j];
+        if (!std::isfinite(r2)) finite = false;
+        const double rel = b2 > 0 ? std::sqrt(r2 / b2) : (r2 > 0 ? INFINITY : 0.0);
+        worst = std::max(worst, rel);
+        if (!(rel <= rtol)) conv = false;
+        const double sg = std::sqrt(r2);
+        sig[(size_t)c * S + j] = sg;
+        isig[(size_t)c * S + j] = sg > 0 ? 1.0 / sg : 0.0;
+        double t_in = sg > 0 ? rtol * std::sqrt(b2) / sg : 1.0;
+        if (prec == BLOCKOA_MIXED) t_in = std::max(inner_rtol, 0.5 * t_in);
+        tgt[(size_t)c * S + j] = t_in * t_in;
+      }
+      relres[c] = worst;
+      if (done[c]) continue;
+      if (!finite) { status[c] = BLOCKOA_ERR_BREAKDOWN; done[c] = 1; continue; }
+      if (conv) { status[c] = BLOCKOA_OK; done[c] = 1; continue; }
+      // Give up when the iteration budget is spent, or when a refinement
+      // step failed to halve the true residual (float64 attainable accuracy).
+      if (refine[c] >= max_refine || iters[c] >= maxiter || (refine[c] > 0 && worst > 0.5 * prev_relres[c])) {
+        status[c] = BLOCKOA_ERR_NOT_CONVERGED;
+        done[c] = 1;
+        continue;
+      }
+      prev_relres[c] = worst;
+      ++n_active;
+    }
+    if (n_active == 0) break;
+    // Upload sigma, targets and chip states for the inner solve.
+    for (int c = 0; c < nc; ++c) {
+      ws->h_active[c] = !done[c];
+      ChipSolveState &cs = ws->h_state[c];
+      memset(&cs, 0, sizeof(cs));
+      cs.active = !done[c];
+      cs.status = BLOCKOA_OK;
+      cs.iters = iters[c];
+      cs.deflated = defl[c];
+    }
+    double *stage = ws->h_small + (size_t)nc * S;
+    memcpy(stage, sig.data(), sizeof(double) * nc * S);
+    memcpy(stage + (size_t)nc * S, isig.data(), sizeof(double) * nc * S);
+    memcpy(stage + 2 * (size_t)nc * S, tgt.data(), sizeof(double) * nc * S);
+    BLOCKOA_CUDA(cudaMemcpyAsync(ws->sigma, stage, sizeof(double) * nc * S, cudaMemcpyHostToDevice, st));
+    BLOCKOA_CUDA(cudaMemcpyAsync(ws->inv_sigma, stage + (size_t)nc * S, sizeof(double) * nc * S, cudaMemcpyHostToDevice, st));
+    BLOCKOA_CUDA(cudaMemcpyAsync(ws->target2, stage + 2 * (size_t)nc * S, sizeof(double) * nc * S, cudaMemcpyHostToDevice, st));
+    BLOCKOA_CUDA(cudaMemcpyAsync(ws->outer_active, ws->h_active, sizeof(int) * nc, cudaMemcpyHostToDevice, st));
+    BLOCKOA_CUDA(cudaMemcpyAsync(ws->state, ws->h_state, sizeof(ChipSolveState) * nc, cudaMemcpyHostToDevice, st));
+    {
+      const size_t sm = sizeof(double) * (size_t)nc * S * S, sv = sizeof(double) * (size_t)nc * S;
+      BLOCKOA_CUDA(cudaMemsetAsync(ws->gram, 0, sm, st));
+      BLOCKOA_CUDA(cudaMemsetAsync(ws->rho, 0, sm, st));
+      BLOCKOA_CUDA(cudaMemsetAsync(ws->wg, 0, sm, st));
+      BLOCKOA_CUDA(cudaMemsetAsync(ws->rn2, 0, sv, st));
+    }
+    inner_init_kernel<T, S><<<ws->n_units_small, 256, 0, st>>>(
+        ws->units_small, ws->outer_active, ws->R64, ws->inv_sigma, (T *)ws->R, (T *)ws->P, (T *)ws->D);
+    BLOCKOA_CUDA(cudaGetLastError());
+    // Inner block-CG iterations, polled every `check_every` iterations.
+    for (;;) {
+      BLOCKOA_CUDA(cudaGraphLaunch(ws->graph, st));
+      BLOCKOA_CUDA(cudaMemcpyAsync(ws->h_state, ws->state, sizeof(ChipSolveState) * nc, cudaMemcpyDeviceToHost, st));
+      BLOCKOA_CUDA(cudaStreamSynchronize(st));
+      bool any = false;
+      for (int c = 0; c < nc; ++c) any = any || ws->h_state[c].active;
+      if (!any) break;
+    }
+    accumulate_kernel<T, S><<<ws->n_units_small, 256, 0, st>>>(ws->units_small, ws->outer_active,
+                                                               ws->sigma, (const T *)ws->D, ws->X64);
+    BLOCKOA_CUDA(cudaGetLastError());
+    for (int c = 0; c < nc; ++c) {
+      if (done[c]) continue;
+      const ChipSolveState &cs = ws->h_state[c];
+      iters[c] = cs.iters;
+      defl[c] = cs.deflated;
+      refine[c] += 1;
+      if (cs.status == BLOCKOA_ERR_BREAKDOWN) { status[c] = cs.status; done[c] = 1; }
+    }
+  }
+  unpad_cols_kernel<<<eb, 256, 0, st>>>(ws->X64, X, n, s, S);
+  BLOCKOA_CUDA(cudaGetLastError());
+  BLOCKOA_CUDA(cudaStreamSynchronize(st));
+  int worst = BLOCKOA_OK;
+  for (int c = 0; c < nc; ++c) {
+    stats[c].status = status[c];
+    stats[c].iters = iters[c];
+    stats[c].refine_steps = refine[c];
+    stats[c].deflated_cols = defl[c];
+    stats[c].relres_max = relres[c];
+    if (status[c] != BLOCKOA_OK && (worst == BLOCKOA_OK || status[c] == BLOCKOA_ERR_BREAKDOWN))
+      worst = status[c];
+  }
+  return worst;
+}
+
+}  // namespace blockoa
+
+using namespace blockoa;
+
+extern "C" int blockoa_block_solve(blockoa_operator *op, const double *B, double *X, int s,
+                                   const blockoa_solve_opts *opts, blockoa_solve_stats *stats,
+                                   blockoa_stream stream) {
+  if (!op || !opts || !stats || s < 0 || s > 64) return BLOCKOA_ERR_INVALID;
+  for (int c = 0; c < op->n_chips; ++c) {
+    stats[c].status = BLOCKOA_ERR_INVALID;
+    stats[c].iters = stats[c].refine_steps = stats[c].deflated_cols = 0;
+    stats[c].relres_max = 0.0;
+  }
+  if (!(opts->rtol > 0.0) || opts->maxiter < 0) return BLOCKOA_ERR_INVALID;
+  if (opts->precision != BLOCKOA_FP64 && opts->precision != BLOCKOA_MIXED) return BLOCKOA_ERR_INVALID;
+  if (s == 0) {
+    for (int c = 0; c < op->n_chips; ++c) stats[c].status = BLOCKOA_OK;
+    return BLOCKOA_OK;
+  }
+  if (!B || !X) return BLOCKOA_ERR_INVALID;
+  const int S = s <= 8 ? 8 : s <= 16 ? 16 : s <= 32 ? 32 : 64;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (opts->precision == BLOCKOA_FP64) {
+    switch (S) {
+      case 8: return solve_impl<double, 8>(op, B, X, s, opts, stats, st);
+      case 16: return solve_impl<double, 16>(op, B, X, s, opts, stats, st);
+      case 32: return solve_impl<double, 32>(op, B, X, s, opts, stats, st);
+      default: return solve_impl<double, 64>(op, B, X, s, opts, stats, st);
+    }
+  }
+  switch (S) {
+    case 8: return solve_impl<float, 8>(op, B, X, s, opts, stats, st);
+    case 16: return solve_impl<float, 16>(op, B, X, s, opts, stats, st);
+    case 32: return solve_impl<float, 32>(op, B, X, s, opts, stats, st);
+    default: return solve_impl<float, 64>(op, B, X, s, opts, stats, st);
+  }
+}

@@ -1,0 +1,113 @@
+// New temperature fields T = U C (Eq. 5, Sec. III-B) and the C-ABI entry
+// points for the combination and the operator action (Eq. 6).
+//
+// FP64: float64 SIMT dot products of length s per output (this kernel).
+// MIXED: bfloat16x3 on the tensor cores (combine_tc.cu).
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace blockoa {
+
+struct CombTile {
+  int chip, pad;
+  long long begin;  // first cell (global numbering) of a 256-cell tile
+};
+
+constexpr int CT_CELLS = 256;
+constexpr int CT_FIELDS = 32;
+
+// T[m][a] = sum_j U[a][j] C[j][m] for a 256-cell tile and 32 fields.
+template <typename T, int S>
+__global__ void __launch_bounds__(CT_CELLS)
+combine_simt_kernel(const CombTile *__restrict__ tiles, const ChipDev *__restrict__ chips,
+                    const double *__restrict__ U, const double *__restrict__ C,
+                    T *__restrict__ Tout, int s, int M) {
+  __shared__ T sC[S][CT_FIELDS];
+  const CombTile tile = tiles[blockIdx.x];
+  const ChipDev ch = chips[tile.chip];
+  const int m0 = blockIdx.y * CT_FIELDS;
+  const int nf = min(CT_FIELDS, M - m0);
+  const double *Cc = C + (long long)tile.chip * s * M;
+  for (int e = threadIdx.x; e < S * CT_FIELDS; e += CT_CELLS) {
+    const int j = e / CT_FIELDS, f = e % CT_FIELDS;
+    sC[j][f] = (j < s && f < nf) ? (T)Cc[(long long)j * M + m0 + f] : T(0);
+  }
+  __syncthreads();
+  const long long a = tile.begin + threadIdx.x;
+  if (a >= ch.off + ch.n) return;
+  T u[S];
+#pragma unroll
+  for (int j = 0; j < S; ++j) u[j] = j < s ? (T)U[a * s + j] : T(0);
+  T *out = Tout + ch.off * (long long)M + (a - ch.off);
+  for (int f = 0; f < nf; ++f) {
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < S; ++j) acc += u[j] * sC[j][f];
+    out[(long long)(m0 + f) * ch.n] = acc;
+  }
+}
+
+int launch_combine(blockoa_operator *op, const double *U, const double *C, void *Tout, int s, int M,
+                   int dtype, cudaStream_t st) {
+  if (dtype == BLOCKOA_MIXED) return launch_combine_tc(op, U, C, (float *)Tout, s, M, st);
+  std::vector<CombTile> tiles;
+  for (int c = 0; c < op->n_chips; ++c)
+    for (long long b = 0; b < op->chips[c].n; b += CT_CELLS)
+      tiles.push_back({c, 0, op->chips[c].off + b});
+  void *d_tiles = nullptr;
+  int rc = pool_alloc(op, &d_tiles, sizeof(CombTile) * tiles.size(), st);
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(CombTile) * tiles.size(),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    dim3 grid((unsigned)tiles.size(), (unsigned)((M + CT_FIELDS - 1) / CT_FIELDS));
+    const CombTile *dt = (const CombTile *)d_tiles;
+    const int S = s <= 8 ? 8 : s <= 16 ? 16 : s <= 32 ? 32 : 64;
+#define BLOCKOA_COMB(TT, SS) \
+  combine_simt_kernel<TT, SS><<<grid, CT_CELLS, 0, st>>>(dt, op->d_chips, U, C, (TT *)Tout, s, M)
+    switch (S) {
+      case 8: BLOCKOA_COMB(double, 8); break;
+      case 16: BLOCKOA_COMB(double, 16); break;
+      case 32: BLOCKOA_COMB(double, 32); break;
+      default: BLOCKOA_COMB(double, 64); break;
+    }
+#undef BLOCKOA_COMB
+    e = cudaGetLastError();
+  }
+  pool_free(d_tiles, st);
+  return cuda_status(e, "combine");
+}
+
+}  // namespace blockoa
+
+using namespace blockoa;
+
+static bool valid_dtype(int d) { return d == BLOCKOA_FP64 || d == BLOCKOA_MIXED; }
+
+extern "C" int blockoa_combine(blockoa_operator *op, const double *U, const double *C, void *T,
+                               int s, int M, int dtype, blockoa_stream stream) {
+  if (!op || s < 1 || s > 64 || M < 0 || !valid_dtype(dtype)) return BLOCKOA_ERR_INVALID;
+  if (M == 0) return BLOCKOA_OK;
+  if (!U || !C || !T) return BLOCKOA_ERR_INVALID;
+  if (dtype == BLOCKOA_FP64 && (M + CT_FIELDS - 1) / CT_FIELDS > 65535) return BLOCKOA_ERR_INVALID;
+  return launch_combine(op, U, C, T, s, M, dtype, (cudaStream_t)stream);
+}
+
+extern "C" int blockoa_apply_operator(const blockoa_operator *op, const void *T, void *q, int M,
+                                      int dtype, blockoa_stream stream) {
+  if (!op || M < 0 || !valid_dtype(dtype)) return BLOCKOA_ERR_INVALID;
+  if (M == 0) return BLOCKOA_OK;
+  if (!T || !q || T == q) return BLOCKOA_ERR_INVALID;
+  if ((M + 7) / 8 > 65535) return BLOCKOA_ERR_INVALID;
+  return launch_apply_fields(op, T, q, M, dtype, (cudaStream_t)stream);
+}
+
+extern "C" int blockoa_pair_check(const blockoa_operator *op, const void *T, const void *q, int M,
+                                  int dtype, double *e_pair, blockoa_stream stream) {
+  if (!op || M < 0 || !valid_dtype(dtype)) return BLOCKOA_ERR_INVALID;
+  if (M == 0) return BLOCKOA_OK;
+  if (!T || !q || !e_pair || M > 65535) return BLOCKOA_ERR_INVALID;
+  return launch_pair_check(op, T, q, M, dtype, e_pair, (cudaStream_t)stream);
+}

@@ -1,0 +1,345 @@
+// T = U C on the tensor cores (Eq. 5, Sec. III-B), bfloat16x3 with float32
+// accumulation in tensor memory (tcgen05, sm_103a).
+//
+// The float64 basis U is split into three bfloat16 planes
+//   hi = bf16(u),  mid = bf16(u - hi),  lo = bf16(u - hi - mid)
+// (relative residual below 2^-24 |u|), C is bfloat16-exact, and
+//   T = [lo | mid | hi] [C; C; C]
+// is one GEMM with K = 3 S' (S' = s rounded up to 16), the small planes first
+// so that they enter the float32 accumulator before the large ones.
+//
+// Data path: split kernels write U and C directly as shared-memory images
+// of the tcgen05 canonical K-major layout without swizzle (8 x 16-byte core
+// matrices; element (r, k) of a tile at (r/8)*SBO + (k/8)*128 + (r%8)*16 +
+// (k%8)*2 with SBO = (K/8)*128), 128 cells per A tile and 256 fields per B
+// chunk.  The GEMM kernel moves each image with one bulk copy
+// (cp.async.bulk, completion on an mbarrier), one thread issues
+// tcgen05.mma kind::f16 (M = 128, N = 256, K = 16 per instruction) into a
+// 256-column TMEM accumulator, and four warps drain it with tcgen05.ld into
+// coalesced streaming stores of T (each warp owns 32 cells, i.e. 128 bytes
+// of one field per store).  Every mbarrier wait is bounded.
+#include <cuda_bf16.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace blockoa {
+
+constexpr int TC_M = 128;       // cells per tile (MMA M, TMEM lanes)
+constexpr int TC_N = 256;       // fields per chunk (MMA N, TMEM columns)
+constexpr int TC_THREADS = 128;
+
+__host__ __device__ inline int tc_kpad(int s) { return (s + 15) / 16 * 16; }
+
+// byte offset of element (r, k) in a K-major no-swizzle tcgen05 operand image
+__host__ __device__ inline long long tc_img_off(int r, int k, int K) {
+  return (long long)(r >> 3) * (K / 8) * 128 + (long long)(k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+struct TcTile {
+  int chip;
+  int ncells;       // valid cells in this tile (<= 128)
+  long long cell0;  // first cell (global numbering)
+  long long img;    // index of the tile's image in the U buffer
+};
+
+// ---------------------------------------------------------------- split kernels
+// One thread writes one 16-byte row segment (8 consecutive k) of a tile image.
+__global__ void split_u_kernel(const TcTile *__restrict__ tiles, int n_tiles,
+                               const double *__restrict__ U, int s, int Sp,
+                               __nv_bfloat16 *__restrict__ img) {
+  const int K = 3 * Sp;
+  const long long per_tile = (long long)TC_M * (K / 8);
+  const long long total = per_tile * n_tiles;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(i / per_tile);
+    const int rem = (int)(i % per_tile);
+    const int r = rem / (K / 8), k0 = (rem % (K / 8)) * 8;
+    const TcTile tile = tiles[t];
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = k0 + q;
+      const int plane = k / Sp, j = k % Sp;   // 0 = lo, 1 = mid, 2 = hi
+      double u = 0.0;
+      if (r < tile.ncells && j < s) u = U[(tile.cell0 + r) * s + j];
+      const __nv_bfloat16 hi = __double2bfloat16(u);
+      const double r1 = u - (double)__bfloat162float(hi);
+      const __nv_bfloat16 mid = __double2bfloat16(r1);
+      const double r2 = r1 - (double)__bfloat162float(mid);
+      const __nv_bfloat16 lo = __double2bfloat16(r2);
+      v[q] = plane == 2 ? hi : (plane == 1 ? mid : lo);
+    }
+    char *dst = reinterpret_cast<char *>(img) + tile.img * (long long)TC_M * K * 2 + tc_img_off(r, k0, K);
+    *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(v);
+  }
+}
+
+// B images: chunk q of chip c holds fields [256 q, 256 q + 256) as rows and
+// [C; C; C] as K.
+__global__ void split_c_kernel(const double *__restrict__ C, int n_chips, int s, int Sp, int M,
+                               int n_chunks, __nv_bfloat16 *__restrict__ img) {
+  const int K = 3 * Sp;
+  const long long per_chunk = (long long)TC_N * (K / 8);
+  const long long total = per_chunk * n_chunks * n_chips;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long cq = i / per_chunk;   // chip * n_chunks + chunk
+    const int rem = (int)(i % per_chunk);
+    const int chip = (int)(cq / n_chunks), q = (int)(cq % n_chunks);
+    const int r = rem / (K / 8), k0 = (rem % (K / 8)) * 8;
+    const int field = q * TC_N + r;
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int j = (k0 + e) % Sp;
+      double c = 0.0;
+      if (field < M && j < s) c = C[((long long)chip * s + j) * M + field];
+      v[e] = __double2bfloat16(c);
+    }
+    char *dst = reinterpret_cast<char *>(img) + cq * (long long)TC_N * K * 2 + tc_img_off(r, k0, K);
+    *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(v);
+  }
+}
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (2LL << 30)) return false;   // about a second
+  }
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t smem_desc(const void *base, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_u32(base) >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version for tcgen05
+  // base offset 0, no swizzle (bits 61-63 = 0)
+  return d;
+}
+
+// kind::f16 instruction descriptor: bf16 A and B (K-major), f32 accumulator.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4)                    // D format: f32
+         | (1u << 7)                  // A format: bf16
+         | (1u << 10)                 // B format: bf16
+         | ((uint32_t)(n >> 3) << 17)  // N / 8
+         | ((uint32_t)(m >> 4) << 24);  // M / 16
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+#define BLOCKOA_TMEM_LD32(taddr, r)                                                               \
+  asm volatile(                                                                                   \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14," \
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"               \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),       \
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),   \
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),             \
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),             \
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])              \
+      : "r"(taddr))
+
+// ---------------------------------------------------------------- GEMM kernel
+// One CTA: one 128-cell tile of one chip, all fields in chunks of 256.
+__global__ void __launch_bounds__(TC_THREADS)
+combine_tc_kernel(const TcTile *__restrict__ tiles, const ChipDev *__restrict__ chips,
+                  const __nv_bfloat16 *__restrict__ uimg, const __nv_bfloat16 *__restrict__ cimg,
+                  float *__restrict__ Tout, int M, int Kdim, int n_chunks, int *__restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const uint32_t a_bytes = TC_M * Kdim * 2, b_bytes = TC_N * Kdim * 2;
+  unsigned char *sA = smem;
+  unsigned char *sB = smem + a_bytes;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sB + b_bytes);  // [0] loads, [1] mma
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const TcTile tile = tiles[blockIdx.x];
+  const ChipDev ch = chips[tile.chip];
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(TC_N));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t sbo = (uint32_t)(Kdim / 8) * 128;
+  const uint32_t idesc = idesc_bf16(TC_M, TC_N);
+  const char *cbase = reinterpret_cast<const char *>(cimg) + (long long)tile.chip * n_chunks * b_bytes;
+  uint32_t ld_phase = 0, mma_phase = 0;
+  if (tid == 0) {
+    mbar_expect_tx(&bars[0], a_bytes + b_bytes);
+    bulk_g2s(sA, reinterpret_cast<const char *>(uimg) + tile.img * (long long)a_bytes, a_bytes, &bars[0]);
+    bulk_g2s(sB, cbase, b_bytes, &bars[0]);
+  }
+  float *tbase = Tout + ch.off * (long long)M + (tile.cell0 - ch.off);
+  for (int q = 0; q < n_chunks; ++q) {
+    if (tid == 0) {
+      bool ok = mbar_wait(&bars[0], ld_phase);
+      if (ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int ks = 0; ks < Kdim / 16; ++ks) {
+          const uint64_t ad = smem_desc(sA + ks * 256, 128, sbo);
+          const uint64_t bd = smem_desc(sB + ks * 256, 128, sbo);
+          mma_bf16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+        }
+        mma_commit(&bars[1]);
+      } else {
+        s_fail = 1;
+      }
+    }
+    ld_phase ^= 1;
+    __syncthreads();
+    if (s_fail) break;
+    if (!mbar_wait(&bars[1], mma_phase)) {
+      s_fail = 1;
+    }
+    mma_phase ^= 1;
+    __syncthreads();
+    if (s_fail) break;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // the MMAs are done with sB: prefetch the next chunk while draining TMEM
+    if (tid == 0 && q + 1 < n_chunks) {
+      mbar_expect_tx(&bars[0], b_bytes);
+      bulk_g2s(sB, cbase + (long long)(q + 1) * b_bytes, b_bytes, &bars[0]);
+    }
+    const int cell = warp * 32 + lane;
+    const bool valid = cell < tile.ncells;
+    const int f0 = q * TC_N;
+    float *out = tbase + cell;
+#pragma unroll 1
+    for (int cc = 0; cc < TC_N / 32; ++cc) {
+      uint32_t r[32];
+      BLOCKOA_TMEM_LD32(tmem + ((uint32_t)(warp * 32) << 16) + cc * 32, r);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int fb = f0 + cc * 32;
+      if (valid) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (fb + i < M) __stcs(out + (long long)(fb + i) * ch.n, __uint_as_float(r[i]));
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (s_fail && tid == 0) {
+    atomicExch(err, 1);
+    // let copies and MMAs still in flight land before the memory is released
+    mbar_wait(&bars[0], ld_phase);
+    mbar_wait(&bars[1], mma_phase);
+  }
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N));
+}
+
+int launch_combine_tc(blockoa_operator *op, const double *U, const double *C, float *Tout, int s,
+                      int M, cudaStream_t st) {
+  const int Sp = tc_kpad(s), K = 3 * Sp;
+  const int n_chunks = (M + TC_N - 1) / TC_N;
+  std::vector<TcTile> tiles;
+  for (int c = 0; c < op->n_chips; ++c)
+    for (long long b = 0; b < op->chips[c].n; b += TC_M) {
+      TcTile t;
+      t.chip = c;
+      t.ncells = (int)(op->chips[c].n - b < TC_M ? op->chips[c].n - b : TC_M);
+      t.cell0 = op->chips[c].off + b;
+      t.img = (long long)tiles.size();
+      tiles.push_back(t);
+    }
+  const size_t a_bytes = (size_t)TC_M * K * 2, b_bytes = (size_t)TC_N * K * 2;
+  const size_t smem = a_bytes + b_bytes + 2 * sizeof(uint64_t) + 16;
+  void *d_tiles = nullptr, *uimg = nullptr, *cimg = nullptr, *err = nullptr;
+  int rc = pool_alloc(op, &d_tiles, sizeof(TcTile) * tiles.size(), st);
+  if (!rc) rc = pool_alloc(op, &uimg, a_bytes * tiles.size(), st);
+  if (!rc) rc = pool_alloc(op, &cimg, b_bytes * n_chunks * op->n_chips, st);
+  if (!rc) rc = pool_alloc(op, &err, sizeof(int), st);
+  auto done = [&](int code) {
+    pool_free(d_tiles, st); pool_free(uimg, st); pool_free(cimg, st); pool_free(err, st);
+    return code;
+  };
+  if (rc) return done(rc);
+  static size_t attr_smem = 0;
+  if (smem > attr_smem) {
+    cudaError_t ea = cudaFuncSetAttribute(combine_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem);
+    if (ea != cudaSuccess) return done(cuda_status(ea, "combine_tc shared memory"));
+    attr_smem = smem;
+  }
+  cudaError_t e = cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(TcTile) * tiles.size(),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    split_u_kernel<<<2048, 256, 0, st>>>((const TcTile *)d_tiles, (int)tiles.size(), U, s, Sp,
+                                         (__nv_bfloat16 *)uimg);
+    split_c_kernel<<<512, 256, 0, st>>>(C, op->n_chips, s, Sp, M, n_chunks, (__nv_bfloat16 *)cimg);
+    combine_tc_kernel<<<(unsigned)tiles.size(), TC_THREADS, smem, st>>>(
+        (const TcTile *)d_tiles, op->d_chips, (const __nv_bfloat16 *)uimg,
+        (const __nv_bfloat16 *)cimg, Tout, M, K, n_chunks, (int *)err);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return done(cuda_status(e, "combine_tc"));
+  int h_err = 0;
+  e = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return done(cuda_status(e, "combine_tc"));
+  return done(h_err ? BLOCKOA_ERR_TIMEOUT : BLOCKOA_OK);
+}
+
+}  // namespace blockoa

@@ -1,0 +1,95 @@
+// Internal declarations shared by the translation units of libblockoa.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/blockoa.h"
+
+namespace blockoa {
+
+// ---------------------------------------------------------------- chip table
+struct ChipDev {
+  int nx, ny, nz, pad;
+  long long n;    // cells of the chip
+  long long off;  // first cell of the chip in the concatenated numbering
+};
+
+// A contiguous range of one chip's cells processed by one CTA.
+struct Unit {
+  int chip, pad;
+  long long begin, end;  // global cell indices [begin, end)
+};
+
+// Per-chip state of a running block solve (device resident).
+struct ChipSolveState {
+  int active;       // 1 while the chip iterates
+  int status;       // blockoa_status
+  int iters;        // block iterations so far (this refinement step)
+  int deflated;     // columns dropped by deflation so far
+  int rank;         // kept columns in the current factorisation
+  int pad0, pad1, pad2;
+};
+
+}  // namespace blockoa
+
+struct blockoa_operator {
+  int device = 0;
+  int n_chips = 0;
+  long long n_total = 0;
+  std::vector<blockoa::ChipDev> chips;   // host copy
+  std::vector<double> cell_area;         // dx * dy per chip (m^2)
+  blockoa::ChipDev *d_chips = nullptr;   // device copy
+  double *g64 = nullptr;                 // [n_total][4]: cx, cy, cz, cb (float64)
+  float *g32 = nullptr;                  // [n_total][4]: float32 copies
+  cudaMemPool_t pool = nullptr;          // stream-ordered pool for workspaces
+  void *solve_ws = nullptr;              // block-solve workspace (blockcg.cu)
+};
+
+namespace blockoa {
+
+// ---------------------------------------------------------------- errors
+void set_last_error(cudaError_t e, const char *where);
+int cuda_status(cudaError_t e, const char *where);  // BLOCKOA_OK or ERR_CUDA/ERR_OOM
+
+#define BLOCKOA_CUDA(call)                                   \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return ::blockoa::cuda_status(e_, #call); \
+  } while (0)
+
+// Stream-ordered allocation from the operator's pool.
+int pool_alloc(blockoa_operator *op, void **p, size_t bytes, cudaStream_t st);
+void pool_free(void *p, cudaStream_t st);
+
+// Work units: every chip's cells split into ranges of at most `cells` cells.
+std::vector<Unit> make_units(const blockoa_operator *op, long long cells);
+long long pick_unit_cells(const blockoa_operator *op, long long align, long long min_cells,
+                          int target_ctas);
+
+// ---------------------------------------------------------------- kernels (host launchers)
+// stencil.cu
+int launch_apply_fields(const blockoa_operator *op, const void *T, void *q, int M, int dtype,
+                        cudaStream_t st);
+int launch_pair_check(const blockoa_operator *op, const void *T, const void *q, int M, int dtype,
+                      double *e_pair, cudaStream_t st);
+// R = B - A X (float64) on a padded block [n_total][S]; also accumulates
+// per-chip column norms ||R_j||^2 into rn2 [chip][S] (must be zeroed).
+int launch_residual64(const blockoa_operator *op, const double *B, const double *X, double *R,
+                      int S, double *rn2, cudaStream_t st);
+
+// blockcg.cu
+void free_solve_ws(void *ws);
+
+// combine_tc.cu (bfloat16x3 on tcgen05; fields in float32)
+int launch_combine_tc(blockoa_operator *op, const double *U, const double *C, float *T, int s,
+                      int M, cudaStream_t st);
+
+// combine.cu
+int launch_combine(blockoa_operator *op, const double *U, const double *C, void *T, int s, int M,
+                   int dtype, cudaStream_t st);
+
+}  // namespace blockoa

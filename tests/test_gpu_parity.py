@@ -1,0 +1,337 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative L2 per column or field unless stated):
+* assembly and right-hand sides: bit-exact (same float64 operations, no
+  contraction);
+* float64 operator action: 1e-13 (different summation order only);
+* float32 operator action on random fields: 2e-6 (a few float32 roundings of
+  terms whose magnitude is that of the result);
+* float64 combination: 1e-14; bfloat16x3 combination: 1e-6 (three 8-bit
+  planes carry 24 bits of the basis; float32 accumulation);
+* basis U: 1e-10 for the FP64 path at rtol 1e-12 (kappa ~ 7e3 times the
+  residual), 1e-9 for the mixed path refined to rtol 1e-12;
+* generated pairs: e_T, e_pair <= 1e-10 (FP64 path), <= 1e-6 (mixed path,
+  fields stored in float32).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import blockoa_oracle as orc
+from paper_2510_23221_gb300 import blockoa as bo
+from paper_2510_23221_gb300 import pipeline as pl
+from paper_2510_23221_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2510_23221_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def relcols(a, b, axis=0):
+    nb = np.linalg.norm(b, axis=axis)
+    return np.linalg.norm(a - b, axis=axis) / np.where(nb > 0, nb, 1.0)
+
+
+def small_chips():
+    return [
+        synth.random_small_chip(101, 3, 5, 2),
+        synth.random_small_chip(102, 33, 17, 5, h_top=3e4, h_bottom=2e3),
+        synth.random_small_chip(103, 9, 4, 3, h_top=0.0, h_side=5e3),
+        synth.random_small_chip(104, 7, 6, 3, h_top=1e4, h_bottom=1e3, h_side=1e3, layer_nz=[2, 1, 3]),
+        synth.reference_stack_chip(),
+    ]
+
+
+# ---------------------------------------------------------------- assembly / rhs
+@pytest.mark.parametrize("idx", range(5))
+def test_assemble_bitexact(idx):
+    chip = small_chips()[idx]
+    op = bo.assemble([chip])
+    got = bo.export_conductances(op, 0)
+    ref = orc.face_conductances(chip)
+    for k in ("gx", "gy", "gz", "gb"):
+        assert np.array_equal(got[k], ref[k]), k
+
+
+def test_assemble_batched_uneven_bitexact():
+    chips = small_chips()
+    op = bo.assemble(chips)
+    off = 0
+    for c, chip in enumerate(chips):
+        assert op.sizes[c]["off"] == off and op.sizes[c]["n"] == chip.n
+        off += chip.n
+        got = bo.export_conductances(op, c)
+        ref = orc.face_conductances(chip)
+        for k in ("gx", "gy", "gz", "gb"):
+            assert np.array_equal(got[k], ref[k])
+
+
+def test_build_rhs_exact():
+    chips = small_chips()[:3]
+    rng = np.random.default_rng(5)
+    s = 5
+    dens = [np.stack([synth.rect_power_map(rng, c.nx, c.ny) for _ in range(s)]) for c in chips]
+    op = bo.assemble(chips)
+    B = torch.empty(op.n_total * s, dtype=torch.float64, device="cuda")
+    bo.build_rhs(op, cuda(np.concatenate([d.ravel() for d in dens])), B, s)
+    Bh = B.cpu().numpy()
+    for c, chip in enumerate(chips):
+        sz = op.sizes[c]
+        assert np.array_equal(Bh[sz["off"] * s:(sz["off"] + sz["n"]) * s].reshape(-1, s),
+                              orc.rhs(chip, dens[c]))
+
+
+# ---------------------------------------------------------------- operator action
+@pytest.mark.parametrize("idx", range(5))
+def test_apply_fp64(idx):
+    chip = small_chips()[idx]
+    M = 7
+    T = np.random.default_rng(idx).standard_normal((M, chip.n))
+    op = bo.assemble([chip])
+    q = torch.empty(M * chip.n, dtype=torch.float64, device="cuda")
+    bo.apply_operator(op, cuda(T.ravel()), q, M, bo.FP64)
+    ref = orc.apply_operator(orc.assemble(chip), T)
+    assert np.all(relcols(q.cpu().numpy().reshape(M, -1), ref, axis=1) < 1e-13)
+
+
+@pytest.mark.parametrize("idx", range(5))
+def test_apply_fp32(idx):
+    chip = small_chips()[idx]
+    M = 9
+    T = np.random.default_rng(idx).standard_normal((M, chip.n)).astype(np.float32)
+    op = bo.assemble([chip])
+    q = torch.empty(M * chip.n, dtype=torch.float32, device="cuda")
+    bo.apply_operator(op, cuda(T.ravel()), q, M, bo.MIXED)
+    ref = orc.apply_operator(orc.assemble(chip), T.astype(np.float64))
+    assert np.all(relcols(q.cpu().numpy().astype(np.float64).reshape(M, -1), ref, axis=1) < 2e-6)
+
+
+def test_apply_batched_fields_layout():
+    chips = small_chips()
+    M = 3
+    op = bo.assemble(chips)
+    rng = np.random.default_rng(9)
+    Ts = [rng.standard_normal((M, c.n)) for c in chips]
+    q = torch.empty(op.n_total * M, dtype=torch.float64, device="cuda")
+    bo.apply_operator(op, cuda(np.concatenate([t.ravel() for t in Ts])), q, M, bo.FP64)
+    qh = q.cpu().numpy()
+    for c, chip in enumerate(chips):
+        sz = op.sizes[c]
+        got = qh[sz["off"] * M:(sz["off"] + sz["n"]) * M].reshape(M, -1)
+        assert np.all(relcols(got, orc.apply_operator(orc.assemble(chip), Ts[c]), axis=1) < 1e-13)
+
+
+# ---------------------------------------------------------------- combination
+@pytest.mark.parametrize("s,M", [(8, 64), (3, 5), (32, 100), (64, 33), (32, 600), (17, 513)])
+def test_combine(s, M):
+    chip = synth.random_small_chip(7, 21, 13, 3)
+    rng = np.random.default_rng(s * 100 + M)
+    U = rng.standard_normal((chip.n, s)) * 10.0 ** rng.uniform(-3, 3, s)
+    C = synth.coefficients(rng, s, M)
+    op = bo.assemble([chip])
+    ref = orc.combine(U, C)
+    T64 = torch.empty(M * chip.n, dtype=torch.float64, device="cuda")
+    bo.combine(op, cuda(U.ravel()), cuda(C.ravel()), T64, s, M, bo.FP64)
+    assert np.all(relcols(T64.cpu().numpy().reshape(M, -1), ref, axis=1) < 1e-14)
+    T32 = torch.empty(M * chip.n, dtype=torch.float32, device="cuda")
+    bo.combine(op, cuda(U.ravel()), cuda(C.ravel()), T32, s, M, bo.MIXED)
+    assert np.all(relcols(T32.cpu().numpy().astype(np.float64).reshape(M, -1), ref, axis=1) < 1e-6)
+
+
+# ---------------------------------------------------------------- block solve
+def _solve(chips, B_list, s, precision, rtol, **kw):
+    op = bo.assemble(chips)
+    B = cuda(np.concatenate([b.ravel() for b in B_list]))
+    X = torch.empty_like(B)
+    stats = bo.block_solve(op, B, X, s, rtol=rtol, precision=precision, **kw)
+    Xh = X.cpu().numpy()
+    out = []
+    for c in range(len(chips)):
+        sz = op.sizes[c]
+        out.append(Xh[sz["off"] * s:(sz["off"] + sz["n"]) * s].reshape(-1, s))
+    return out, stats
+
+
+@pytest.mark.parametrize("precision", [bo.FP64, bo.MIXED])
+@pytest.mark.parametrize("idx", range(4))
+def test_block_solve_tiny_vs_dense(idx, precision):
+    chip = small_chips()[idx]
+    B = np.random.default_rng(idx).uniform(0, 1e-2, (chip.n, 3))
+    # float64's attainable true residual on these grids is ~1e-12 (kappa ~ 1e4)
+    (X,), (st,) = _solve([chip], [B], 3, precision, 1e-11)
+    assert st.status == bo.OK and st.relres_max <= 1e-11
+    ref = np.linalg.solve(orc.assemble(chip).toarray(), B)
+    assert np.all(relcols(X, ref) < 1e-9)
+
+
+@pytest.mark.parametrize("precision", [bo.FP64, bo.MIXED])
+def test_block_solve_reference_stack(precision):
+    w = synth.small_fp64_workload()
+    chip = w.chips[0]
+    A = orc.assemble(chip)
+    B = orc.rhs(chip, w.density[0])
+    U_or, info = orc.block_cg(A, B, rtol=1e-12)
+    (X,), (st,) = _solve([chip], [B], 8, precision, 1e-12)
+    assert st.status == bo.OK and st.relres_max <= 1e-12
+    # the oracle's CSR residual and the kernel's difference-form residual
+    # each carry ~1e-13 of float64 rounding at this attainable-accuracy level
+    true_rel = relcols(A @ X, B)
+    assert np.all(true_rel <= 1.5e-12)
+    assert np.all(relcols(X, U_or) < (1e-10 if precision == bo.FP64 else 1e-9))
+    if precision == bo.FP64:
+        assert abs(st.iters - info["iters"]) <= 8, (st.iters, info["iters"])
+
+
+def test_block_solve_ragged_tiles_several_units():
+    """48x40x6 grid (ragged against every tile shape), s = 12 padded to 16."""
+    chip = synth.random_small_chip(55, 48, 40, 6)
+    rng = np.random.default_rng(55)
+    dens = np.stack([synth.power_maps(rng, 48, 40, 1, True)[0] for _ in range(12)])
+    A = orc.assemble(chip)
+    B = orc.rhs(chip, dens)
+    U_or, _ = orc.block_cg(A, B, rtol=1e-12)
+    for precision in (bo.FP64, bo.MIXED):
+        (X,), (st,) = _solve([chip], [B], 12, precision, 1e-12)
+        assert st.status == bo.OK
+        assert np.all(relcols(A @ X, B) <= 1.5e-12)
+        assert np.all(relcols(X, U_or) < 1e-9)
+
+
+@pytest.mark.parametrize("s", [1, 5, 13, 33, 64])
+def test_block_solve_column_counts(s):
+    chip = synth.random_small_chip(60 + s, 11, 9, 4)
+    B = np.random.default_rng(s).uniform(0, 1e-2, (chip.n, s))
+    (X,), (st,) = _solve([chip], [B], s, bo.MIXED, 1e-11)
+    assert st.status == bo.OK
+    ref = np.linalg.solve(orc.assemble(chip).toarray(), B)
+    assert np.all(relcols(X, ref) < 1e-8)
+
+
+def test_block_solve_batched_uneven():
+    chips = small_chips()
+    rng = np.random.default_rng(77)
+    Bs = [rng.uniform(0, 1e-2, (c.n, 4)) for c in chips]
+    for precision in (bo.FP64, bo.MIXED):
+        Xs, stats = _solve(chips, Bs, 4, precision, 1e-12)
+        for c, chip in enumerate(chips):
+            assert stats[c].status == bo.OK
+            ref = np.linalg.solve(orc.assemble(chip).toarray(), Bs[c])
+            assert np.all(relcols(Xs[c], ref) < 1e-9)
+
+
+def test_deflation_duplicate_and_zero_columns():
+    chip = synth.random_small_chip(81, 12, 10, 3)
+    B = np.random.default_rng(81).uniform(0, 1e-2, (chip.n, 6))
+    B[:, 4] = B[:, 1]
+    B[:, 5] = 0.0
+    for precision in (bo.FP64, bo.MIXED):
+        (X,), (st,) = _solve([chip], [B], 6, precision, 1e-12)
+        assert st.status == bo.OK and st.deflated_cols > 0
+        assert np.all(X[:, 5] == 0.0)
+        assert np.linalg.norm(X[:, 4] - X[:, 1]) <= 1e-10 * np.linalg.norm(X[:, 1])
+        ref = np.linalg.solve(orc.assemble(chip).toarray(), B[:, :4])
+        assert np.all(relcols(X[:, :4], ref) < 1e-9)
+
+
+def test_statuses_not_converged_and_breakdown():
+    chips = [synth.random_small_chip(91, 10, 10, 3), synth.random_small_chip(92, 8, 9, 4)]
+    rng = np.random.default_rng(91)
+    Bs = [rng.uniform(0, 1e-2, (c.n, 4)) for c in chips]
+    _, stats = _solve(chips, Bs, 4, bo.FP64, 1e-14, maxiter=3, raise_on_error=False)
+    assert all(s.status == bo.ERR_NOT_CONVERGED for s in stats)
+    assert all(s.iters == 3 for s in stats)
+    Bs[1][3, 2] = np.nan
+    Xs, stats = _solve(chips, Bs, 4, bo.MIXED, 1e-10, raise_on_error=False)
+    assert stats[0].status == bo.OK
+    assert stats[1].status == bo.ERR_BREAKDOWN
+    ref = np.linalg.solve(orc.assemble(chips[0]).toarray(), Bs[0])
+    assert np.all(relcols(Xs[0], ref) < 1e-8)
+
+
+def test_invalid_calls_return_invalid():
+    chip = synth.random_small_chip(3, 4, 4, 2)
+    op = bo.assemble([chip])
+    B = torch.zeros(chip.n * 65, dtype=torch.float64, device="cuda")
+    with pytest.raises(bo.BlockoaError) as e:
+        bo.block_solve(op, B, B.clone(), 65)
+    assert e.value.code == bo.ERR_INVALID
+    with pytest.raises(bo.BlockoaError) as e:
+        bo.block_solve(op, B, B.clone(), 4, rtol=0.0)
+    assert e.value.code == bo.ERR_INVALID
+    T = torch.zeros(chip.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(bo.BlockoaError):
+        bo.apply_operator(op, T, T, 1, bo.FP64)
+
+
+def test_empty_sizes_are_noops():
+    chip = synth.random_small_chip(4, 4, 4, 2)
+    op = bo.assemble([chip])
+    T = torch.zeros(chip.n, dtype=torch.float64, device="cuda")
+    bo.apply_operator(op, T, T.clone(), 0, bo.FP64)
+    st = bo.block_solve(op, T, T.clone(), 0)
+    assert st[0].status == bo.OK
+
+
+# ---------------------------------------------------------------- whole path
+def test_pipeline_reference_stack_fp64():
+    w = synth.small_fp64_workload()
+    res = pl.run(w, bo.FP64)
+    chip = w.chips[0]
+    out = orc.generate(chip, w.density[0], w.coeffs[0], rtol=1e-12)
+    T = pl.chip_fields(res, 0, "T").cpu().numpy()
+    q = pl.chip_fields(res, 0, "q").cpu().numpy()
+    e = orc.pair_errors(out["A"], out["U"], w.coeffs[0], T, q)
+    assert np.max(e["e_T"]) <= 1e-10 and np.max(e["e_q"]) <= 1e-10 and np.max(e["e_pair"]) <= 1e-10
+    # pair check kernel agrees with the oracle's e_pair
+    ep = torch.empty(w.M, dtype=torch.float64, device="cuda")
+    bo.pair_check(res.op, res.T, res.q, w.M, bo.FP64, ep)
+    assert np.allclose(ep.cpu().numpy(), e["e_pair"], rtol=0, atol=1e-13)
+
+
+def test_pipeline_reference_stack_mixed():
+    w = synth.small_fp64_workload()
+    res = pl.run(w, bo.MIXED, rtol=1e-12)
+    chip = w.chips[0]
+    out = orc.generate(chip, w.density[0], w.coeffs[0], rtol=1e-12)
+    T = pl.chip_fields(res, 0, "T").cpu().numpy().astype(np.float64)
+    q = pl.chip_fields(res, 0, "q").cpu().numpy().astype(np.float64)
+    e = orc.pair_errors(out["A"], out["U"], w.coeffs[0], T, q)
+    assert np.max(e["e_T"]) <= 1e-6 and np.max(e["e_pair"]) <= 1e-6
+    ep = torch.empty(w.M, dtype=torch.float64, device="cuda")
+    bo.pair_check(res.op, res.T, res.q, w.M, bo.MIXED, ep)
+    assert np.allclose(ep.cpu().numpy(), e["e_pair"], rtol=1e-6, atol=1e-12)
+
+
+def test_pipeline_full_size_128x128x8_sampled():
+    """The benchmark workload (n = 131072, s = 32, M = 5000, mixed, rtol 1e-6):
+    the oracle checks the basis residual, sampled fields of T against U C,
+    and sampled q against A T, each with its own float64 arithmetic."""
+    w = synth.single_chip_workload()
+    res = pl.run(w, bo.MIXED)
+    chip = w.chips[0]
+    A = orc.assemble(chip)
+    B = orc.rhs(chip, w.density[0])
+    U = pl.chip_block(res, 0, "U").cpu().numpy()
+    assert np.all(relcols(A @ U, B) <= 1.0001e-6)
+    T = pl.chip_fields(res, 0, "T")
+    q = pl.chip_fields(res, 0, "q")
+    C = w.coeffs[0]
+    for m in (0, 1, 2047, 2500, 4999):
+        Tm = T[m].cpu().numpy().astype(np.float64)
+        qm = q[m].cpu().numpy().astype(np.float64)
+        ref = U @ C[:, m]
+        assert np.linalg.norm(Tm - ref) <= 1e-6 * np.linalg.norm(ref)
+        Aq = A @ Tm
+        assert np.linalg.norm(Aq - qm) <= 1e-6 * np.linalg.norm(qm)
+        # energy balance of the generated pair: net source = Robin loss
+        loss = orc.boundary_loss(chip, Tm)[0]
+        assert abs(qm.sum() - loss) <= 1e-5 * np.abs(qm).sum()
