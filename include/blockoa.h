@@ -180,6 +180,27 @@ int blockoa_pair_check(const blockoa_operator *op, const void *T, const void *q,
 int blockoa_export_conductances(const blockoa_operator *op, int chip, double *gx, double *gy,
                                 double *gz, double *gb);
 
+/*
+ * Live per-kernel timing (tracing; no counterpart in the paper).  CUDA
+ * events are recorded on the launching stream around the kernels of the
+ * first block-CG iteration of every convergence poll (external event-record
+ * nodes inside the captured graph), and around every float64 residual,
+ * combination and operator-action launch.  Writes, for the first
+ * max_kernels kernel classes (host arrays, any may be NULL): the summed
+ * milliseconds of the timed launches, the number of timed launches, the
+ * number of all launches, and a static name.  Returns the number of kernel
+ * classes.  Synchronises on pending events.
+ */
+int blockoa_kernel_times(blockoa_operator *op, int max_kernels, double *timed_ms,
+                         long long *timed_launches, long long *launches, const char **names);
+
+/* Zero the per-kernel timing of the operator. */
+int blockoa_reset_kernel_times(blockoa_operator *op);
+
+/* Kernels launched by the library in this process so far (a graph launch
+ * counts each of its kernel nodes).  Host only; never fails. */
+long long blockoa_launch_count(void);
+
 /* Free the operator and its workspace (NULL is a no-op).  Synchronises the device. */
 void blockoa_destroy(blockoa_operator *op);
 

@@ -31,7 +31,8 @@ EXPORTED = (
     "blockoa_assemble", "blockoa_operator_size", "blockoa_operator_total", "blockoa_build_rhs",
     "blockoa_block_solve", "blockoa_combine", "blockoa_apply_operator", "blockoa_pair_check",
     "blockoa_export_conductances", "blockoa_destroy", "blockoa_status_string",
-    "blockoa_last_error",
+    "blockoa_last_error", "blockoa_kernel_times", "blockoa_reset_kernel_times",
+    "blockoa_launch_count",
 )
 
 
@@ -90,8 +91,15 @@ def _lib():
         lib.blockoa_status_string.restype = ct.c_char_p
         lib.blockoa_last_error.argtypes = []
         lib.blockoa_last_error.restype = ct.c_char_p
+        lib.blockoa_kernel_times.argtypes = [vp, i, ct.POINTER(ct.c_double),
+                                             ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong),
+                                             ct.POINTER(ct.c_char_p)]
+        lib.blockoa_reset_kernel_times.argtypes = [vp]
+        lib.blockoa_launch_count.argtypes = []
+        lib.blockoa_launch_count.restype = ct.c_longlong
         for name in EXPORTED:
-            if name not in ("blockoa_destroy", "blockoa_status_string", "blockoa_last_error"):
+            if name not in ("blockoa_destroy", "blockoa_status_string", "blockoa_last_error",
+                            "blockoa_launch_count"):
                 getattr(lib, name).restype = ct.c_int
         _LIB = lib
     return _LIB
@@ -260,3 +268,24 @@ def export_conductances(op: Operator, chip: int):
 
 def status_string(code: int) -> str:
     return _lib().blockoa_status_string(code).decode()
+
+
+def kernel_times(op: Operator) -> dict:
+    """Live per-kernel timing: {name: (timed_ms, timed_launches, launches)}."""
+    lib = _lib()
+    n = lib.blockoa_kernel_times(op.handle, 0, None, None, None, None)
+    ms = (ct.c_double * n)()
+    cnt = (ct.c_longlong * n)()
+    allc = (ct.c_longlong * n)()
+    names = (ct.c_char_p * n)()
+    lib.blockoa_kernel_times(op.handle, n, ms, cnt, allc, names)
+    return {names[k].decode(): (ms[k], cnt[k], allc[k]) for k in range(n)}
+
+
+def reset_kernel_times(op: Operator):
+    _check(_lib().blockoa_reset_kernel_times(op.handle), "reset_kernel_times")
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(_lib().blockoa_launch_count())

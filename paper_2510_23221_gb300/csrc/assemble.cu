@@ -10,6 +10,47 @@
 namespace blockoa {
 
 static thread_local char g_last_error[256] = "";
+std::atomic<long long> g_launches{0};
+
+void time_begin(blockoa_operator *op, cudaStream_t st, cudaEvent_t *ev) {
+  (void)op;
+  *ev = nullptr;
+  if (cudaEventCreate(ev) != cudaSuccess) { cudaGetLastError(); *ev = nullptr; return; }
+  cudaEventRecord(*ev, st);
+}
+
+void time_end(blockoa_operator *op, cudaStream_t st, int kclass, cudaEvent_t ev0) {
+  if (!ev0) return;
+  cudaEvent_t ev1 = nullptr;
+  if (cudaEventCreate(&ev1) != cudaSuccess) { cudaGetLastError(); cudaEventDestroy(ev0); return; }
+  cudaEventRecord(ev1, st);
+  op->times.pend_class.push_back(kclass);
+  op->times.pend_ev.push_back(ev0);
+  op->times.pend_ev.push_back(ev1);
+  op->times.launches[kclass] += 1;
+}
+
+void add_time(blockoa_operator *op, int kclass, double ms) {
+  op->times.ms[kclass] += ms;
+  op->times.samples[kclass] += 1;
+}
+
+void add_launches(blockoa_operator *op, int kclass, long long n) { op->times.launches[kclass] += n; }
+
+static void resolve_times(blockoa_operator *op) {
+  KernelTimes &kt = op->times;
+  for (size_t i = 0; i < kt.pend_class.size(); ++i) {
+    cudaEvent_t a = kt.pend_ev[2 * i], b = kt.pend_ev[2 * i + 1];
+    float ms = 0.f;
+    if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess)
+      add_time(op, kt.pend_class[i], ms);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+  cudaGetLastError();
+  kt.pend_class.clear();
+  kt.pend_ev.clear();
+}
 
 void set_last_error(cudaError_t e, const char *where) {
   snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
@@ -279,6 +320,7 @@ extern "C" int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips,
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_zdz, zdz.data(), sizeof(double) * zdz.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && d_kc) e = cudaMemcpyAsync(d_kc, kcell.data(), sizeof(double) * kcell.size(), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return fail(cuda_status(e, "upload chip tables"));
+  g_launches += 1;
   assemble_kernel<<<(unsigned)units.size(), 256, 0, st>>>(
       (const Unit *)d_units, op->d_chips, (const ChipPhys *)d_phys, (const double *)d_zk,
       (const double *)d_zdz, (const double *)d_kc, op->g64, op->g32);
@@ -331,6 +373,7 @@ extern "C" int blockoa_build_rhs(const blockoa_operator *op, const double *densi
   cudaError_t e = cudaMemcpyAsync(d_units, units.data(), sizeof(Unit) * units.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_rc, rcs.data(), sizeof(RhsChip) * rcs.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
+    g_launches += 1;
     build_rhs_kernel<<<(unsigned)units.size(), 256, 0, st>>>((const Unit *)d_units, op->d_chips,
                                                            (const RhsChip *)d_rc, density, B, s);
     e = cudaGetLastError();
@@ -368,9 +411,43 @@ extern "C" void blockoa_destroy(blockoa_operator *op) {
   if (!op) return;
   cudaDeviceSynchronize();
   free_solve_ws(op->solve_ws);
+  resolve_times(op);
+  if (op->apply_blocks) cudaFree(op->apply_blocks);
   if (op->d_chips) cudaFree(op->d_chips);
   if (op->g64) cudaFree(op->g64);
   if (op->g32) cudaFree(op->g32);
   cudaGetLastError();
   delete op;
 }
+
+static const char *kKernelNames[KC_COUNT] = {
+    "spmm_gram", "factor", "trsolve_alpha", "update_gram", "trsolve_beta", "p_update",
+    "residual64", "combine_tc", "split_bf16x3", "apply_fields", "combine_fp64"};
+
+extern "C" int blockoa_kernel_times(blockoa_operator *op, int max_kernels, double *timed_ms,
+                                    long long *timed_launches, long long *launches,
+                                    const char **names) {
+  if (!op || max_kernels < 0) return BLOCKOA_ERR_INVALID;
+  resolve_times(op);
+  const int n = max_kernels < KC_COUNT ? max_kernels : KC_COUNT;
+  for (int k = 0; k < n; ++k) {
+    if (timed_ms) timed_ms[k] = op->times.ms[k];
+    if (timed_launches) timed_launches[k] = op->times.samples[k];
+    if (launches) launches[k] = op->times.launches[k];
+    if (names) names[k] = kKernelNames[k];
+  }
+  return KC_COUNT;
+}
+
+extern "C" int blockoa_reset_kernel_times(blockoa_operator *op) {
+  if (!op) return BLOCKOA_ERR_INVALID;
+  resolve_times(op);
+  for (int k = 0; k < KC_COUNT; ++k) {
+    op->times.ms[k] = 0.0;
+    op->times.samples[k] = 0;
+    op->times.launches[k] = 0;
+  }
+  return BLOCKOA_OK;
+}
+
+extern "C" long long blockoa_launch_count(void) { return g_launches.load(); }

@@ -762,6 +762,7 @@ struct SolveWS {
   int *h_active = nullptr;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t graph = nullptr;
+  cudaEvent_t tev[7] = {};      // recorded around the kernels of each chunk's first iteration
   int graph_iters = 0, graph_maxiter = -1, graph_s = -1;
   double graph_tol = -1.0;
   std::vector<void *> allocs;
@@ -771,6 +772,8 @@ void free_solve_ws(void *p) {
   SolveWS *ws = (SolveWS *)p;
   if (!ws) return;
   if (ws->graph) cudaGraphExecDestroy(ws->graph);
+  for (cudaEvent_t e : ws->tev)
+    if (e) cudaEventDestroy(e);
   if (ws->cap) cudaStreamDestroy(ws->cap);
   for (void *a : ws->allocs) cudaFree(a);
   if (ws->h_state) cudaFreeHost(ws->h_state);
@@ -813,23 +816,35 @@ static void set_smem_limits() {
                        (int)factor_smem_bytes<S>());
 }
 
-// One block-CG iteration for every active chip.
+// One block-CG iteration for every active chip; with `ev`, an event is
+// recorded before each kernel and after the last (for live timing).
 template <typename T, int S>
 static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const SmallArgs &sa,
-                             cudaStream_t st) {
+                             cudaStream_t st, cudaEvent_t *ev) {
   const T *g = sizeof(T) == 4 ? (const T *)op->g32 : (const T *)op->g64;
   const unsigned nsolve = (unsigned)(ws->n_chips * S);
+  // external record nodes: the events carry timestamps when the graph runs
+  auto mark = [&](int i) {
+    if (ev) cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal);
+  };
+  mark(0);
   spmm_gram_kernel<T, S><<<ws->n_units, 256, spmm_smem<T, S>(), st>>>(
       ws->units, op->d_chips, ws->state, g, (const T *)ws->P, (const T *)ws->R, (T *)ws->Q,
       ws->gram, ws->rho);
+  mark(1);
   factor_kernel<S><<<ws->n_chips, 256, factor_smem_bytes<S>(), st>>>(sa);
+  mark(2);
   trsolve_kernel<T, S, true><<<nsolve, 32, 0, st>>>(sa);
+  mark(3);
   update_gram_kernel<T, S><<<ws->n_units, 256, update_smem<T, S>(), st>>>(
       ws->units, ws->state, (const T *)ws->alpha, (const T *)ws->P, (const T *)ws->Q,
       (T *)ws->D, (T *)ws->R, ws->wg, ws->rn2);
+  mark(4);
   trsolve_kernel<T, S, false><<<nsolve, 32, 0, st>>>(sa);
+  mark(5);
   p_update_kernel<T, S><<<ws->n_units_tile, 256, pupdate_smem<T, S>(), st>>>(
       ws->units_tile, ws->state, (const T *)ws->beta, (const T *)ws->R, (T *)ws->P);
+  mark(6);
 }
 
 template <typename T, int S>
@@ -921,8 +936,11 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       ws->graph_s != s || ws->graph_tol != tol) {
     if (ws->graph) { cudaGraphExecDestroy(ws->graph); ws->graph = nullptr; }
     cudaGraph_t graph = nullptr;
+    for (int i = 0; i < 7; ++i)
+      if (!ws->tev[i]) BLOCKOA_CUDA(cudaEventCreate(&ws->tev[i]));
     BLOCKOA_CUDA(cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < check_every; ++k) launch_iteration<T, S>(op, ws, sa, ws->cap);
+    for (int k = 0; k < check_every; ++k)
+      launch_iteration<T, S>(op, ws, sa, ws->cap, k == 0 ? ws->tev : nullptr);
     cudaError_t e = cudaStreamEndCapture(ws->cap, &graph);
     if (e != cudaSuccess) return cuda_status(e, "capture block-CG iterations");
     e = cudaGraphInstantiate(&ws->graph, graph, 0);
@@ -936,6 +954,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
 
   // Inputs: padded B and X0, ||B_j||^2.
   const unsigned eb = (unsigned)std::min<long long>((n * S + 255) / 256, 4096);
+  g_launches += 3;
   pad_cols_kernel<<<eb, 256, 0, st>>>(B, ws->B64, n, s, S);
   pad_cols_kernel<<<eb, 256, 0, st>>>(o->x0, ws->X64, n, s, S);
   BLOCKOA_CUDA(cudaMemsetAsync(ws->bn2, 0, sizeof(double) * nc * S, st));
@@ -1014,14 +1033,24 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       BLOCKOA_CUDA(cudaMemsetAsync(ws->wg, 0, sm, st));
       BLOCKOA_CUDA(cudaMemsetAsync(ws->rn2, 0, sv, st));
     }
+    g_launches += 2;
     inner_init_kernel<T, S><<<ws->n_units_small, 256, 0, st>>>(
         ws->units_small, ws->outer_active, ws->R64, ws->inv_sigma, (T *)ws->R, (T *)ws->P, (T *)ws->D);
     BLOCKOA_CUDA(cudaGetLastError());
     // Inner block-CG iterations, polled every `check_every` iterations.
     for (;;) {
+      g_launches += 6LL * check_every;
+      for (int i = 0; i < 6; ++i) add_launches(op, KC_SPMM_GRAM + i, check_every);
       BLOCKOA_CUDA(cudaGraphLaunch(ws->graph, st));
       BLOCKOA_CUDA(cudaMemcpyAsync(ws->h_state, ws->state, sizeof(ChipSolveState) * nc, cudaMemcpyDeviceToHost, st));
       BLOCKOA_CUDA(cudaStreamSynchronize(st));
+      for (int i = 0; i < 6; ++i) {   // live timing of this chunk's first iteration
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ws->tev[i], ws->tev[i + 1]) == cudaSuccess)
+          add_time(op, KC_SPMM_GRAM + i, ms);
+        else
+          cudaGetLastError();
+      }
       bool any = false;
       for (int c = 0; c < nc; ++c) any = any || ws->h_state[c].active;
       if (!any) break;
@@ -1038,6 +1067,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       if (cs.status == BLOCKOA_ERR_BREAKDOWN) { status[c] = cs.status; done[c] = 1; }
     }
   }
+  g_launches += 1;
   unpad_cols_kernel<<<eb, 256, 0, st>>>(ws->X64, X, n, s, S);
   BLOCKOA_CUDA(cudaGetLastError());
   BLOCKOA_CUDA(cudaStreamSynchronize(st));

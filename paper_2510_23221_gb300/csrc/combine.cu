@@ -67,6 +67,9 @@ int launch_combine(blockoa_operator *op, const double *U, const double *C, void 
     const int S = s <= 8 ? 8 : s <= 16 ? 16 : s <= 32 ? 32 : 64;
 #define BLOCKOA_COMB(TT, SS) \
   combine_simt_kernel<TT, SS><<<grid, CT_CELLS, 0, st>>>(dt, op->d_chips, U, C, (TT *)Tout, s, M)
+    cudaEvent_t ev;
+    time_begin(op, st, &ev);
+    g_launches += 1;
     switch (S) {
       case 8: BLOCKOA_COMB(double, 8); break;
       case 16: BLOCKOA_COMB(double, 16); break;
@@ -75,6 +78,7 @@ int launch_combine(blockoa_operator *op, const double *U, const double *C, void 
     }
 #undef BLOCKOA_COMB
     e = cudaGetLastError();
+    time_end(op, st, KC_COMBINE_FP64, ev);
   }
   pool_free(d_tiles, st);
   return cuda_status(e, "combine");

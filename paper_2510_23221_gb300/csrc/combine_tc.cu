@@ -326,13 +326,19 @@ int launch_combine_tc(blockoa_operator *op, const double *U, const double *C, fl
                                   cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
   if (e == cudaSuccess) {
+    cudaEvent_t ev0, ev1;
+    time_begin(op, st, &ev0);
+    g_launches += 3;
     split_u_kernel<<<2048, 256, 0, st>>>((const TcTile *)d_tiles, (int)tiles.size(), U, s, Sp,
                                          (__nv_bfloat16 *)uimg);
     split_c_kernel<<<512, 256, 0, st>>>(C, op->n_chips, s, Sp, M, n_chunks, (__nv_bfloat16 *)cimg);
+    time_end(op, st, KC_SPLIT, ev0);
+    time_begin(op, st, &ev1);
     combine_tc_kernel<<<(unsigned)tiles.size(), TC_THREADS, smem, st>>>(
         (const TcTile *)d_tiles, op->d_chips, (const __nv_bfloat16 *)uimg,
         (const __nv_bfloat16 *)cimg, Tout, M, K, n_chunks, (int *)err);
     e = cudaGetLastError();
+    time_end(op, st, KC_COMBINE_TC, ev1);
   }
   if (e != cudaSuccess) return done(cuda_status(e, "combine_tc"));
   int h_err = 0;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -34,6 +35,25 @@ struct ChipSolveState {
   int pad0, pad1, pad2;
 };
 
+// Kernel classes with live event timing.
+enum KernelClass {
+  KC_SPMM_GRAM = 0, KC_FACTOR, KC_TRSOLVE_ALPHA, KC_UPDATE_GRAM, KC_TRSOLVE_BETA, KC_P_UPDATE,
+  KC_RESIDUAL64, KC_COMBINE_TC, KC_SPLIT, KC_APPLY, KC_COMBINE_FP64, KC_COUNT
+};
+
+struct KernelTimes {
+  double ms[KC_COUNT] = {};           // summed duration of the timed launches
+  long long samples[KC_COUNT] = {};   // timed launches
+  long long launches[KC_COUNT] = {};  // all launches
+  // event pairs recorded around launches, resolved when the times are read
+  std::vector<int> pend_class;
+  std::vector<cudaEvent_t> pend_ev;   // 2 per pending launch
+};
+
+// Kernel launches issued by the library in this process (graph launches
+// count every kernel node).
+extern std::atomic<long long> g_launches;
+
 }  // namespace blockoa
 
 struct blockoa_operator {
@@ -47,6 +67,9 @@ struct blockoa_operator {
   float *g32 = nullptr;                  // [n_total][4]: float32 copies
   cudaMemPool_t pool = nullptr;          // stream-ordered pool for workspaces
   void *solve_ws = nullptr;              // block-solve workspace (blockcg.cu)
+  blockoa::KernelTimes times;            // live per-kernel timing
+  void *apply_blocks = nullptr;          // cached launch table of the operator action
+  int n_apply_blocks = 0;
 };
 
 namespace blockoa {
@@ -64,6 +87,12 @@ int cuda_status(cudaError_t e, const char *where);  // BLOCKOA_OK or ERR_CUDA/ER
 // Stream-ordered allocation from the operator's pool.
 int pool_alloc(blockoa_operator *op, void **p, size_t bytes, cudaStream_t st);
 void pool_free(void *p, cudaStream_t st);
+
+// Live timing: record an event pair around one launch on `st`.
+void time_begin(blockoa_operator *op, cudaStream_t st, cudaEvent_t *ev);
+void time_end(blockoa_operator *op, cudaStream_t st, int kclass, cudaEvent_t ev0);
+void add_time(blockoa_operator *op, int kclass, double ms);
+void add_launches(blockoa_operator *op, int kclass, long long n);
 
 // Work units: every chip's cells split into ranges of at most `cells` cells.
 std::vector<Unit> make_units(const blockoa_operator *op, long long cells);

@@ -107,28 +107,33 @@ apply_fields_kernel(const CellBlock *__restrict__ blocks, const ChipDev *__restr
 
 int launch_apply_fields(const blockoa_operator *op, const void *Tin, void *qout, int M, int dtype,
                         cudaStream_t st) {
-  std::vector<CellBlock> blocks;
-  for (int c = 0; c < op->n_chips; ++c)
-    for (long long b = 0; b < op->chips[c].n; b += AP_CELLS)
-      blocks.push_back({c, 0, op->chips[c].off + b});
-  void *d_blocks = nullptr;
   blockoa_operator *mop = const_cast<blockoa_operator *>(op);
-  int rc = pool_alloc(mop, &d_blocks, sizeof(CellBlock) * blocks.size(), st);
-  if (rc) return rc;
-  cudaError_t e = cudaMemcpyAsync(d_blocks, blocks.data(), sizeof(CellBlock) * blocks.size(),
-                                  cudaMemcpyHostToDevice, st);
-  constexpr int F = 8;
-  if (e == cudaSuccess) {
-    dim3 grid((unsigned)blocks.size(), (unsigned)((M + F - 1) / F));
-    if (dtype == BLOCKOA_FP64)
-      apply_fields_kernel<double, F><<<grid, AP_CELLS, 0, st>>>(
-          (const CellBlock *)d_blocks, op->d_chips, op->g64, (const double *)Tin, (double *)qout, M);
-    else
-      apply_fields_kernel<float, F><<<grid, AP_CELLS, 0, st>>>(
-          (const CellBlock *)d_blocks, op->d_chips, op->g32, (const float *)Tin, (float *)qout, M);
-    e = cudaGetLastError();
+  if (!mop->apply_blocks) {
+    // launch table: 256-cell blocks of every chip (built once per operator)
+    std::vector<CellBlock> blocks;
+    for (int c = 0; c < op->n_chips; ++c)
+      for (long long b = 0; b < op->chips[c].n; b += AP_CELLS)
+        blocks.push_back({c, 0, op->chips[c].off + b});
+    void *d = nullptr;
+    BLOCKOA_CUDA(cudaMalloc(&d, sizeof(CellBlock) * blocks.size()));
+    cudaError_t e = cudaMemcpy(d, blocks.data(), sizeof(CellBlock) * blocks.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(d); return cuda_status(e, "apply table"); }
+    mop->apply_blocks = d;
+    mop->n_apply_blocks = (int)blocks.size();
   }
-  pool_free(d_blocks, st);
+  constexpr int F = 8;
+  dim3 grid((unsigned)op->n_apply_blocks, (unsigned)((M + F - 1) / F));
+  cudaEvent_t ev;
+  time_begin(mop, st, &ev);
+  g_launches += 1;
+  if (dtype == BLOCKOA_FP64)
+    apply_fields_kernel<double, F><<<grid, AP_CELLS, 0, st>>>(
+        (const CellBlock *)op->apply_blocks, op->d_chips, op->g64, (const double *)Tin, (double *)qout, M);
+  else
+    apply_fields_kernel<float, F><<<grid, AP_CELLS, 0, st>>>(
+        (const CellBlock *)op->apply_blocks, op->d_chips, op->g32, (const float *)Tin, (float *)qout, M);
+  cudaError_t e = cudaGetLastError();
+  time_end(mop, st, KC_APPLY, ev);
   return cuda_status(e, "apply_fields");
 }
 
@@ -207,6 +212,7 @@ int launch_pair_check(const blockoa_operator *op, const void *Tin, const void *q
   if (e == cudaSuccess) {
     dim3 grid((unsigned)tiles.size(), (unsigned)M);
     dim3 block(FT_X, FT_Y);
+    g_launches += 2;
     if (dtype == BLOCKOA_FP64)
       pair_check_kernel<double><<<grid, block, 0, st>>>((const FieldTile *)d_tiles, op->d_chips,
                                                         op->g64, (const double *)Tin,
@@ -289,9 +295,12 @@ int launch_residual64(const blockoa_operator *op, const double *B, const double 
   if (rc) return rc;
   cudaError_t e = cudaMemcpyAsync(d_units, units.data(), sizeof(Unit) * units.size(),
                                   cudaMemcpyHostToDevice, st);
+  cudaEvent_t ev = nullptr;
   if (e == cudaSuccess) {
     const unsigned nb = (unsigned)units.size();
     const Unit *du = (const Unit *)d_units;
+    time_begin(mop, st, &ev);
+    g_launches += 1;
     switch (S) {
       case 8: residual64_kernel<8><<<nb, 256, 0, st>>>(du, op->d_chips, op->g64, B, X, R, rn2); break;
       case 16: residual64_kernel<16><<<nb, 256, 0, st>>>(du, op->d_chips, op->g64, B, X, R, rn2); break;
@@ -300,6 +309,7 @@ int launch_residual64(const blockoa_operator *op, const double *B, const double 
       default: pool_free(d_units, st); return BLOCKOA_ERR_INVALID;
     }
     e = cudaGetLastError();
+    time_end(mop, st, KC_RESIDUAL64, ev);
   }
   pool_free(d_units, st);
   return cuda_status(e, "residual64");

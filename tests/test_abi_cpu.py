@@ -22,7 +22,7 @@ def _declared():
     for f in os.listdir(os.path.join(ROOT, "include")):
         if f.endswith(".h"):
             text = open(os.path.join(ROOT, "include", f)).read()
-            names |= set(re.findall(r"^\s*(?:int|void|const char \*)\s*(blockoa_\w+)\s*\(", text, re.M))
+            names |= set(re.findall(r"^\s*(?:int|void|long long|const char \*)\s*(blockoa_\w+)\s*\(", text, re.M))
     return sorted(names)
 
 
