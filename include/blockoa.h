@@ -172,6 +172,28 @@ int blockoa_apply_operator(const blockoa_operator *op, const void *T, void *q, i
 int blockoa_pair_check(const blockoa_operator *op, const void *T, const void *q, int M,
                        int dtype, double *e_pair, blockoa_stream stream);
 
+/* Largest n_chips * M accepted by blockoa_pair_check_static. */
+#define BLOCKOA_STATIC_PAIR_MAX 32768
+
+/*
+ * blockoa_pair_check without any device allocation.  The paper has no
+ * counterpart; this serves callers that cannot allocate during the call:
+ * code running inside an open CUDA stream capture (a cudaMalloc would break
+ * the capture), serving processes whose device memory is reserved up front
+ * by their own pool, and fixed-budget deployments that forbid allocation
+ * after start-up.  Same arguments, layout and result as blockoa_pair_check.
+ * Its accumulators live in a fixed library-owned device array of
+ * 2 * BLOCKOA_STATIC_PAIR_MAX float64 values (512 KB per GPU that loads the
+ * library, held until the process exits); n_chips * M above
+ * BLOCKOA_STATIC_PAIR_MAX returns ERR_INVALID before anything is launched
+ * (blockoa_last_error() says why).  The first call on a device looks up that
+ * array's device address, so make it before any stream capture.  All calls
+ * on a device share the array and each clears it on its stream first: calls
+ * that overlap on the GPU race and must be serialised by the caller.
+ */
+int blockoa_pair_check_static(const blockoa_operator *op, const void *T, const void *q, int M,
+                              int dtype, double *e_pair, blockoa_stream stream);
+
 /*
  * Copy chip `chip`'s float64 face conductances to host arrays laid out like
  * the oracle's: gx [nz][ny][nx-1], gy [nz][ny-1][nx], gz [nz-1][ny][nx],
