@@ -45,7 +45,7 @@ METRIC = "verified sample pairs/s at <=1e-6 rel err, chosen vs plain FP64, one G
 UNIT = "pairs/s"
 RTOL = 1e-6
 PAIR_TOL = 1e-6
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070   # SMs x FP32 lanes x 2 flop x max SM GHz / 1000
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1000   # SMs x FP32 lanes x 2 flop x max SM GHz
 FP64_PEAK_TFLOPS = 1.25                      # GB300 float64 (vector and tensor), nominal
 
 
