@@ -183,6 +183,45 @@ __global__ void assemble_kernel(const Unit *__restrict__ units, const ChipDev *_
   }
 }
 
+// One thread per z-row of a layered chip: the row's interior face
+// conductances and the Robin conductance of every edge class, with the same
+// float64 operations (and order) as assemble_kernel.
+__global__ void layer_table_kernel(const ChipDev *__restrict__ chips, const ChipPhys *__restrict__ phys,
+                                   const double *__restrict__ zk, const double *__restrict__ zdz,
+                                   int n_chips, double *__restrict__ lt64, float *__restrict__ lt32) {
+  const int c = blockIdx.x;
+  if (c >= n_chips) return;
+  const ChipDev ch = chips[c];
+  const ChipPhys ph = phys[c];
+  if (!ch.layered) return;
+  for (int z = threadIdx.x; z < ch.nz; z += blockDim.x) {
+    const double ka = zk[ph.zoff + z], dz = zdz[ph.zoff + z];
+    double rec[kLT];
+    for (int i = 0; i < kLT; ++i) rec[i] = 0.0;
+    rec[0] = ch.nx > 1 ? series_g(__dmul_rn(ph.dy, dz), ph.dx, ka, ph.dx, ka) : 0.0;
+    rec[1] = ch.ny > 1 ? series_g(__dmul_rn(ph.dx, dz), ph.dy, ka, ph.dy, ka) : 0.0;
+    rec[2] = z + 1 < ch.nz ? series_g(__dmul_rn(ph.dx, ph.dy), dz, ka, zdz[ph.zoff + z + 1], zk[ph.zoff + z + 1]) : 0.0;
+    for (int cx = 0; cx < 4; ++cx)
+      for (int cy = 0; cy < 4; ++cy) {
+        double cb = 0.0;
+        if (ph.h_top > 0.0 && z == 0) cb = __dadd_rn(cb, robin_g(__dmul_rn(ph.dx, ph.dy), dz, ka, ph.h_top));
+        if (ph.h_bottom > 0.0 && z == ch.nz - 1)
+          cb = __dadd_rn(cb, robin_g(__dmul_rn(ph.dx, ph.dy), dz, ka, ph.h_bottom));
+        if (ph.h_side > 0.0) {
+          if (cx & 1) cb = __dadd_rn(cb, robin_g(__dmul_rn(ph.dy, dz), ph.dx, ka, ph.h_side));
+          if (cx & 2) cb = __dadd_rn(cb, robin_g(__dmul_rn(ph.dy, dz), ph.dx, ka, ph.h_side));
+          if (cy & 1) cb = __dadd_rn(cb, robin_g(__dmul_rn(ph.dx, dz), ph.dy, ka, ph.h_side));
+          if (cy & 2) cb = __dadd_rn(cb, robin_g(__dmul_rn(ph.dx, dz), ph.dy, ka, ph.h_side));
+        }
+        rec[4 + 4 * cx + cy] = cb;
+      }
+    for (int i = 0; i < kLT; ++i) {
+      lt64[(ch.lz + z) * kLT + i] = rec[i];
+      lt32[(ch.lz + z) * kLT + i] = (float)rec[i];
+    }
+  }
+}
+
 // ---------------------------------------------------------------- right-hand sides
 struct RhsChip {
   double area;          // dx * dy
@@ -274,8 +313,10 @@ extern "C" int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips,
         kcell.push_back(d.k_cell[i]);
       }
     }
-    tab[c].nx = d.nx; tab[c].ny = d.ny; tab[c].nz = (int)nz; tab[c].pad = 0;
+    tab[c].nx = d.nx; tab[c].ny = d.ny; tab[c].nz = (int)nz;
+    tab[c].layered = d.k_cell ? 0 : 1;
     tab[c].n = n; tab[c].off = off;
+    tab[c].lz = ph.zoff;
     phys[c] = ph;
     off += n;
   }
@@ -305,6 +346,10 @@ extern "C" int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips,
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc g64"));
   e = cudaMalloc((void **)&op->g32, sizeof(float) * 4 * op->n_total);
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc g32"));
+  e = cudaMalloc((void **)&op->lt64, sizeof(double) * kLT * zk.size());
+  if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc lt64"));
+  e = cudaMalloc((void **)&op->lt32, sizeof(float) * kLT * zk.size());
+  if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc lt32"));
   if ((rc = pool_alloc(op, &d_units, sizeof(Unit) * units.size(), st))) return fail(rc);
   if ((rc = pool_alloc(op, &d_phys, sizeof(ChipPhys) * n_chips, st))) return fail(rc);
   if ((rc = pool_alloc(op, &d_zk, sizeof(double) * zk.size(), st))) return fail(rc);
@@ -326,6 +371,12 @@ extern "C" int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips,
       (const double *)d_zdz, (const double *)d_kc, op->g64, op->g32);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(cuda_status(e, "assemble_kernel"));
+  g_launches += 1;
+  layer_table_kernel<<<(unsigned)n_chips, 64, 0, st>>>(op->d_chips, (const ChipPhys *)d_phys,
+                                                      (const double *)d_zk, (const double *)d_zdz,
+                                                      n_chips, op->lt64, op->lt32);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(cuda_status(e, "layer_table_kernel"));
   pool_free(d_units, st); pool_free(d_phys, st); pool_free(d_zk, st);
   pool_free(d_zdz, st); pool_free(d_kc, st);
   *out = op;
@@ -413,9 +464,12 @@ extern "C" void blockoa_destroy(blockoa_operator *op) {
   free_solve_ws(op->solve_ws);
   resolve_times(op);
   if (op->apply_blocks) cudaFree(op->apply_blocks);
+  if (op->apply_vec_blocks) cudaFree(op->apply_vec_blocks);
   if (op->d_chips) cudaFree(op->d_chips);
   if (op->g64) cudaFree(op->g64);
   if (op->g32) cudaFree(op->g32);
+  if (op->lt64) cudaFree(op->lt64);
+  if (op->lt32) cudaFree(op->lt32);
   cudaGetLastError();
   delete op;
 }

@@ -141,14 +141,14 @@ __device__ __forceinline__ void put_tile(T *tile, const T (&x)[4][16 / sizeof(T)
   }
 }
 
-// acc[a*4+b] += sum over this group's cells of A[i0+a][c] * B[j0+b][c]
+// acc[a*4+b] += sum over cells [cbeg, cbeg + nc) of A[i0+a][c] * B[j0+b][c]
 // for transposed tiles A, B.
 template <typename T, int S>
-__device__ __forceinline__ void gram_tile(T *acc, const T *A, const T *B, int i0, int j0, int grp) {
+__device__ __forceinline__ void gram_range(T *acc, const T *A, const T *B, int i0, int j0,
+                                           int cbeg, int nc) {
   using G = BK<T, S>;
-  const int cbeg = grp * G::GC;
 #pragma unroll 2
-  for (int c = cbeg; c < cbeg + G::GC; c += 4) {
+  for (int c = cbeg; c < cbeg + nc; c += 4) {
     T a[4][4], b[4][4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -162,6 +162,13 @@ __device__ __forceinline__ void gram_tile(T *acc, const T *A, const T *B, int i0
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[q * 4 + r] += a[q][k] * b[r][k];
   }
+}
+
+// Same over this group's share of the tile.
+template <typename T, int S>
+__device__ __forceinline__ void gram_tile(T *acc, const T *A, const T *B, int i0, int j0, int grp) {
+  using G = BK<T, S>;
+  gram_range<T, S>(acc, A, B, i0, j0, grp * G::GC, G::GC);
 }
 
 // Reduce the NG groups' 4x4 blocks in shared memory and add the S x S
@@ -200,6 +207,35 @@ __device__ void gram_flush(const T *acc, double *red, double *dst) {
   __syncthreads();
 }
 
+// Flush when the first NG/2 groups hold P^T Q partials and the rest P^T R.
+template <typename T, int S>
+__device__ void gram_flush_split(const T *acc, double *red, double *dst_a, double *dst_b) {
+  using G = BK<T, S>;
+  const int t = threadIdx.x;
+  const int g = t / G::NT, w = t % G::NT;
+  const int i0 = (w / G::NB) * 4, j0 = (w % G::NB) * 4;
+  T *rt = reinterpret_cast<T *>(red);
+#pragma unroll
+  for (int e = 0; e < 16; ++e) rt[g * S * S + (i0 + e / 4) * S + j0 + (e % 4)] = acc[e];
+  __syncthreads();
+  constexpr int H = G::NG / 2;
+  for (int e = t; e < S * S; e += 256) {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      T hi = T(0), lo = T(0);
+      for (int gg = half * H; gg < (half + 1) * H; ++gg) {
+        const T v = rt[gg * S * S + e];
+        const T sum = hi + v;
+        const T bp = sum - hi;
+        lo += (hi - (sum - bp)) + (v - bp);
+        hi = sum;
+      }
+      atomicAdd((half ? dst_b : dst_a) + e, (double)hi + (double)lo);
+    }
+  }
+  __syncthreads();
+}
+
 template <typename T, int S>
 constexpr size_t tile_bytes() { return (size_t)S * BK<T, S>::LD * sizeof(T); }
 constexpr size_t kRedBytes = 256 * 16 * sizeof(double);
@@ -207,7 +243,7 @@ constexpr size_t kRedBytes = 256 * 16 * sizeof(double);
 // ---------------------------------------------------------------- kernels
 // Q = A P on the block layout; Gamma += P^T Q and rho += P^T R per chip.
 template <typename T, int S>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 spmm_gram_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chips,
                  const ChipSolveState *__restrict__ state, const T *__restrict__ g,
                  const T *__restrict__ P, const T *__restrict__ R, T *__restrict__ Q,
@@ -218,7 +254,7 @@ spmm_gram_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chi
   T *sP = reinterpret_cast<T *>(smem);
   T *sQ = sP + S * G::LD;
   T *sR = sQ + S * G::LD;
-  double *red = reinterpret_cast<double *>(sR + S * G::LD);
+  double *red = reinterpret_cast<double *>(smem);   // reused after the tile loop
   const Unit u = units[blockIdx.x];
   if (!state[u.chip].active) return;
   const ChipDev ch = chips[u.chip];
@@ -227,9 +263,14 @@ spmm_gram_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chi
   const int j0 = (t % G::TPR) * V, cl0 = (t / G::TPR) * 4;
   const int grp = t / G::NT, w = t % G::NT;
   const int i0 = (w / G::NB) * 4, k0 = (w % G::NB) * 4;
-  T aq[16], ar[16];
+  // With two or more Gram groups, the first half of the groups accumulates
+  // P^T Q and the second half P^T R, each over twice the cells (one 4x4
+  // block of accumulators per thread); with one group a thread holds both.
+  constexpr bool SPLIT = G::NG >= 2;
+  constexpr int NA = SPLIT ? 16 : 32;
+  T acc[NA];
 #pragma unroll
-  for (int e = 0; e < 16; ++e) { aq[e] = T(0); ar[e] = T(0); }
+  for (int e = 0; e < NA; ++e) acc[e] = T(0);
   for (long long base = u.begin; base < u.end; base += G::TC) {
     T pc[4][V], qv[4][V], rv[4][V];
     load_block<T, S>(pc, P, base + cl0, u.end, j0);
@@ -264,17 +305,27 @@ spmm_gram_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chi
     put_tile<T, G::LD>(sQ, qv, cl0, j0);
     put_tile<T, G::LD>(sR, rv, cl0, j0);
     __syncthreads();
-    gram_tile<T, S>(aq, sP, sQ, i0, k0, grp);
-    gram_tile<T, S>(ar, sP, sR, i0, k0, grp);
+    if constexpr (SPLIT) {
+      constexpr int H = G::NG / 2;
+      const bool second = grp >= H;
+      gram_range<T, S>(acc, sP, second ? sR : sQ, i0, k0, (grp % H) * 2 * G::GC, 2 * G::GC);
+    } else {
+      gram_tile<T, S>(acc, sP, sQ, i0, k0, grp);
+      gram_tile<T, S>(acc + 16, sP, sR, i0, k0, grp);
+    }
     __syncthreads();
   }
-  gram_flush<T, S>(aq, red, gram + (long long)u.chip * S * S);
-  gram_flush<T, S>(ar, red, rho + (long long)u.chip * S * S);
+  if constexpr (SPLIT) {
+    gram_flush_split<T, S>(acc, red, gram + (long long)u.chip * S * S, rho + (long long)u.chip * S * S);
+  } else {
+    gram_flush<T, S>(acc, red, gram + (long long)u.chip * S * S);
+    gram_flush<T, S>(acc + 16, red, rho + (long long)u.chip * S * S);
+  }
 }
 
 // X += P alpha, R -= Q alpha; W += Q^T R_new and rn2 += ||R_new_j||^2.
 template <typename T, int S>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 update_gram_kernel(const Unit *__restrict__ units, const ChipSolveState *__restrict__ state,
                    const T *__restrict__ alpha, const T *__restrict__ P, const T *__restrict__ Q,
                    T *__restrict__ X, T *__restrict__ R, double *__restrict__ wgram,
@@ -286,7 +337,7 @@ update_gram_kernel(const Unit *__restrict__ units, const ChipSolveState *__restr
   T *sQ = sP + S * G::LD;
   T *sR = sQ + S * G::LD;
   T *sA = sR + S * G::LD;
-  double *red = reinterpret_cast<double *>(sA + S * S);
+  double *red = reinterpret_cast<double *>(smem);   // reused after the tile loop
   const Unit u = units[blockIdx.x];
   if (!state[u.chip].active) return;
   const int t = threadIdx.x;
@@ -363,7 +414,7 @@ update_gram_kernel(const Unit *__restrict__ units, const ChipSolveState *__restr
 
 // P = R + P beta (one tile per CTA).
 template <typename T, int S>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 p_update_kernel(const Unit *__restrict__ units, const ChipSolveState *__restrict__ state,
                 const T *__restrict__ beta, const T *__restrict__ R, T *__restrict__ P) {
   using G = BK<T, S>;
@@ -450,17 +501,50 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
 template <int S>
 __host__ __device__ constexpr size_t factor_smem_bytes() { return 2 * sizeof(double) * S * (S + 1); }
 
+// Pivot search over the remaining Schur diagonal (warp 0): largest value,
+// lowest index on ties; positive float64 values order like their bit
+// patterns read as int64.  Lane 0 publishes the pivot, its square root and
+// its reciprocal square root (or S when the largest pivot is <= tol).
+template <int S>
+__device__ __forceinline__ void pivot_search(const double *dg, const int *removed, int skip,
+                                             double tol, int *piv, double *sq, double *inv) {
+  const int lane = threadIdx.x & 31;
+  long long best = LLONG_MIN;
+  int bi = S;
+  for (int i = lane; i < S; i += 32) {
+    const long long v = __double_as_longlong(dg[i]);
+    if (!removed[i] && i != skip && v > best) { best = v; bi = i; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  if (lane == 0) {
+    const double bv = __longlong_as_double(best);
+    const bool ok = bi < S && best > 0 && bv > tol;
+    const double y = ok ? rsqrt_nr(bv) : 0.0;
+    *piv = ok ? bi : S;
+    *inv = y;
+    *sq = bv * y;
+  }
+}
+
+// One CTA per chip.  Step k of the pivoted Cholesky: all threads form
+// column k of L from the published pivot; then warp 0 updates the Schur
+// diagonal and already searches the pivot of step k + 1 (its float64
+// latency chain) while warps 1-7 apply the rank-1 update to the strictly
+// lower part.  Two barriers per step.
 template <int S>
 __global__ void __launch_bounds__(256) factor_kernel(SmallArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  double (*W)[S + 1] = reinterpret_cast<double (*)[S + 1]>(smem);   // scaled Gram, lower triangle
+  double (*W)[S + 1] = reinterpret_cast<double (*)[S + 1]>(smem);   // scaled Gram, strictly lower part used
   double (*Lc)[S + 1] = W + S;                                      // Lc[k][row]: column k of L
-  __shared__ double d[S];
+  __shared__ double d[S], dg[S], rv[S];
   __shared__ int perm[S];
   __shared__ int removed[S];
-  __shared__ double rv[S];
-  __shared__ int s_piv, s_bad;
-  __shared__ double s_sq, s_inv;
+  __shared__ int s_piv[2], s_bad;
+  __shared__ double s_sq[2], s_inv[2];
   const int c = blockIdx.x;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   ChipSolveState &st = A.state[c];
@@ -484,51 +568,37 @@ __global__ void __launch_bounds__(256) factor_kernel(SmallArgs A) {
     const double w = W[t][t];
     d[t] = (w > 1e-290 && isfinite(w)) ? rsqrt_nr(w) : 0.0;
     removed[t] = d[t] == 0.0;
+    dg[t] = w * d[t] * d[t];
   }
   __syncthreads();
   for (int e = t; e < S * S; e += 256) {
     const int a = e / S, b = e % S;
-    if (b <= a) W[a][b] *= d[a] * d[b];
+    if (b < a) W[a][b] *= d[a] * d[b];
   }
+  if (warp == 0) pivot_search<S>(dg, removed, -1, A.tol, &s_piv[0], &s_sq[0], &s_inv[0]);
   __syncthreads();
   int k = 0;
   for (; k < S; ++k) {
-    if (warp == 0) {
-      // largest remaining scaled diagonal, lowest index on ties; positive
-      // float64 values order like their bit patterns read as int64
-      long long best = LLONG_MIN;
-      int bi = S;
-      for (int i = lane; i < S; i += 32) {
-        const long long v = __double_as_longlong(W[i][i]);
-        if (!removed[i] && v > best) { best = v; bi = i; }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-      }
-      if (lane == 0) {
-        s_piv = bi;
-        const double bv = __longlong_as_double(best);
-        const bool ok = bi < S && best > 0 && bv > A.tol;
-        const double y = ok ? rsqrt_nr(bv) : 0.0;
-        s_inv = y;
-        s_sq = bv * y;
-        if (!ok) s_piv = S;
-      }
-    }
-    __syncthreads();
-    const int p = s_piv;
+    const int buf = k & 1;
+    const int p = s_piv[buf];
     if (p >= S) break;
-    const double sq = s_sq, inv = s_inv;
-    if (t < S) Lc[k][t] = removed[t] ? 0.0 : (t == p ? sq : (t > p ? W[t][p] : W[p][t]) * inv);
+    const double sq = s_sq[buf], inv = s_inv[buf];
+    if (t < S)
+      Lc[k][t] = (removed[t] || t == p) ? (t == p ? sq : 0.0) : (t > p ? W[t][p] : W[p][t]) * inv;
     __syncthreads();
     if (t == 0) { removed[p] = 1; perm[k] = p; rv[k] = inv; }
-    // rank-1 update of the remaining rows (row per warp; removed rows skipped)
-    for (int a = warp; a < S; a += 8) {
-      if (removed[a] || a == p) continue;
-      const double la = Lc[k][a];
-      for (int b = lane; b <= a; b += 32) W[a][b] -= la * Lc[k][b];
+    if (warp == 0) {
+      for (int a = lane; a < S; a += 32)
+        if (!removed[a] && a != p) dg[a] -= Lc[k][a] * Lc[k][a];
+      __syncwarp();
+      pivot_search<S>(dg, removed, p, A.tol, &s_piv[buf ^ 1], &s_sq[buf ^ 1], &s_inv[buf ^ 1]);
+    } else {
+      for (int a = warp - 1; a < S; a += 7) {
+        if (removed[a] || a == p) continue;
+        const double la = Lc[k][a];
+        for (int b = lane; b < a; b += 32)
+          if (!removed[b] && b != p) W[a][b] -= la * Lc[k][b];
+      }
     }
     __syncthreads();
   }
@@ -795,9 +865,14 @@ static cudaError_t ws_alloc(SolveWS *ws, P **p, size_t bytes) {
 }
 
 template <typename T, int S>
-constexpr size_t spmm_smem() { return 3 * tile_bytes<T, S>() + kRedBytes; }
+constexpr size_t spmm_smem() {
+  return 3 * tile_bytes<T, S>() > kRedBytes ? 3 * tile_bytes<T, S>() : kRedBytes;
+}
 template <typename T, int S>
-constexpr size_t update_smem() { return 3 * tile_bytes<T, S>() + S * S * sizeof(T) + kRedBytes; }
+constexpr size_t update_smem() {
+  return 3 * tile_bytes<T, S>() + S * S * sizeof(T) > kRedBytes
+             ? 3 * tile_bytes<T, S>() + S * S * sizeof(T) : kRedBytes;
+}
 template <typename T, int S>
 constexpr size_t pupdate_smem() { return tile_bytes<T, S>() + S * S * sizeof(T); }
 

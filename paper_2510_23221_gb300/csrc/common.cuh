@@ -8,16 +8,25 @@
 #include <string>
 #include <vector>
 
-#include "../../include/blockoa.h"
+#include "blockoa.h"
 
 namespace blockoa {
 
 // ---------------------------------------------------------------- chip table
 struct ChipDev {
-  int nx, ny, nz, pad;
+  int nx, ny, nz;
+  int layered;    // 1: conductivity constant within every z-row (layer tables valid)
   long long n;    // cells of the chip
   long long off;  // first cell of the chip in the concatenated numbering
+  long long lz;   // first z-row of the chip in the layer tables
 };
+
+// Layer table of a layered chip, one record per z-row: the +x, +y, +z face
+// conductances of interior faces and the Robin conductance of the 16 edge
+// classes (class = 4 * cx + cy, c = 0 interior, 1 low face, 2 high face,
+// 3 both faces of a one-cell-wide chip).  Values are identical to the
+// per-cell assembly.
+constexpr int kLT = 20;   // gx, gy, gz, unused, cb[16]
 
 // A contiguous range of one chip's cells processed by one CTA.
 struct Unit {
@@ -65,11 +74,15 @@ struct blockoa_operator {
   blockoa::ChipDev *d_chips = nullptr;   // device copy
   double *g64 = nullptr;                 // [n_total][4]: cx, cy, cz, cb (float64)
   float *g32 = nullptr;                  // [n_total][4]: float32 copies
+  double *lt64 = nullptr;                // [sum nz][kLT] layer tables (float64)
+  float *lt32 = nullptr;                 // [sum nz][kLT] float32 copies
   cudaMemPool_t pool = nullptr;          // stream-ordered pool for workspaces
   void *solve_ws = nullptr;              // block-solve workspace (blockcg.cu)
   blockoa::KernelTimes times;            // live per-kernel timing
   void *apply_blocks = nullptr;          // cached launch table of the operator action
   int n_apply_blocks = 0;
+  void *apply_vec_blocks = nullptr;      // same for the vectorised form
+  int n_apply_vec_blocks = 0;
 };
 
 namespace blockoa {

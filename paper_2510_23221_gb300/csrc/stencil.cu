@@ -49,89 +49,387 @@ static std::vector<FieldTile> field_tiles(const blockoa_operator *op) {
   return t;
 }
 
-// q = A T for F consecutive fields of a block of consecutive cells.  One
-// thread owns one cell: its own and its -x/-y/-z neighbours' conductances
-// are loaded once and reused for the F fields; neighbour values come
-// through L1 (x) and L2 (y and z planes), so each value of T is read from
-// HBM about once.  Consecutive threads own consecutive cells of a row, so
-// every load and store of a warp is one 128-byte line.
-constexpr int AP_CELLS = 256;
+// q = A T for F consecutive fields: a 2.5D stencil with an asynchronous
+// plane pipeline.  A CTA of 32 x 8 threads owns a 32 x 8 column tile of one
+// chip and marches z for AF fields.  Each z-plane of the tile, with a halo
+// of one row above and below and four cells left and right (16-byte aligned
+// rows), is copied into a shared-memory ring of planes by cp.async, AD + 1
+// planes ahead of the plane being computed, so every value of T leaves L2
+// once (plus the halo) and the copies overlap the arithmetic.  One barrier
+// per plane.  Positions outside the chip are zero once and never written
+// (their faces have zero conductance).
+constexpr int AX = 32, AY = 8, AF = 8;
+constexpr int AD = 2;               // planes in flight beyond z + 1
+constexpr int RING = AD + 2;        // slots: z, z + 1 and AD planes in flight
+constexpr int RW = AX + 8;          // row of a staged plane: x0-4 .. x0+35
+constexpr int RH = AY + 2;          // rows y0-1 .. y0+8
 
-struct CellBlock {
-  int chip, pad;
-  long long begin;  // first cell (global numbering)
+struct ApplyTile {
+  int chip, x0, y0, pad;
 };
 
-template <typename T, int F>
-__global__ void __launch_bounds__(AP_CELLS)
-apply_fields_kernel(const CellBlock *__restrict__ blocks, const ChipDev *__restrict__ chips,
-                    const T *__restrict__ g, const T *__restrict__ Tin, T *__restrict__ qout,
-                    int M) {
-  const CellBlock blk = blocks[blockIdx.x];
-  const ChipDev ch = chips[blk.chip];
-  const long long a = blk.begin + threadIdx.x;
-  const int m0 = blockIdx.y * F;
-  if (a >= ch.off + ch.n) return;
-  const int loc = (int)(a - ch.off);
-  const int nx = ch.nx, ny = ch.ny, nxny = nx * ny;
-  const int x = loc % nx, y = (loc / nx) % ny, z = loc / nxny;
-  const auto c4 = load_coef<T>(g, a);
-  const T cxm = x > 0 ? load_coef<T>(g, a - 1).x : T(0);
-  const T cym = y > 0 ? load_coef<T>(g, a - nx).y : T(0);
-  const T czm = z > 0 ? load_coef<T>(g, a - nxny).z : T(0);
-  // neighbour offsets, 0 (the cell itself) where the face is a boundary
-  const int oxp = x + 1 < nx ? 1 : 0, oxm = x > 0 ? -1 : 0;
-  const int oyp = y + 1 < ny ? nx : 0, oym = y > 0 ? -nx : 0;
-  const int ozp = z + 1 < ch.nz ? nxny : 0, ozm = z > 0 ? -nxny : 0;
-  const long long fb = ch.off * (long long)M + loc;
-  const int nf = M - m0 < F ? M - m0 : F;
-#pragma unroll
-  for (int f = 0; f < F; ++f) {
-    if (f < nf) {
-      const T *tp = Tin + fb + (long long)(m0 + f) * ch.n;
-      const T c = __ldg(tp);
-      const T vxp = __ldg(tp + oxp), vxm = __ldg(tp + oxm);
-      const T vyp = __ldg(tp + oyp), vym = __ldg(tp + oym);
-      const T vzp = __ldg(tp + ozp), vzm = __ldg(tp + ozm);
-      T r = c4.w * c;
-      r += c4.x * (c - vxp);
-      r += cxm * (c - vxm);
-      r += c4.y * (c - vyp);
-      r += cym * (c - vym);
-      r += c4.z * (c - vzp);
-      r += czm * (c - vzm);
-      qout[fb + (long long)(m0 + f) * ch.n] = r;
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Issue the copies of plane z of the tile for every field into ring slot z % RING.
+template <typename T>
+__device__ __forceinline__ void stage_plane(T *ring, const T *__restrict__ Tin, long long fb,
+                                            long long nstride, int nf, int z, int nx, int ny,
+                                            int x0, int y0, bool vec) {
+  constexpr int VE = 16 / (int)sizeof(T);     // elements per 16-byte chunk
+  constexpr int CPR = RW / VE;                 // chunks per row
+  const int tid = threadIdx.y * AX + threadIdx.x;
+  const long long zo = (long long)z * nx * ny;
+  T *slot = ring + (z % RING) * (AF * RH * RW);
+  const int xs = x0 - 4;
+  if (vec) {
+    for (int i = tid; i < nf * RH * CPR; i += AX * AY) {
+      const int f = i / (RH * CPR), rem = i % (RH * CPR);
+      const int r = rem / CPR, cch = rem % CPR;
+      const int y = y0 - 1 + r, x = xs + cch * VE;
+      if (y < 0 || y >= ny || x < 0 || x + VE > nx) continue;
+      cp_async16(slot + (f * RH + r) * RW + cch * VE, Tin + fb + f * nstride + zo + (long long)y * nx + x);
+    }
+  } else {
+    for (int i = tid; i < nf * RH * RW; i += AX * AY) {
+      const int f = i / (RH * RW), rem = i % (RH * RW);
+      const int r = rem / RW, c = rem % RW;
+      const int y = y0 - 1 + r, x = xs + c;
+      if (y < 0 || y >= ny || x < 0 || x >= nx) continue;
+      if (sizeof(T) == 4) cp_async4(slot + (f * RH + r) * RW + c, Tin + fb + f * nstride + zo + (long long)y * nx + x);
+      else slot[(f * RH + r) * RW + c] = Tin[fb + f * nstride + zo + (long long)y * nx + x];
     }
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(AX *AY)
+apply_fields_kernel(const ApplyTile *__restrict__ tiles, const ChipDev *__restrict__ chips,
+                    const T *__restrict__ g, const T *__restrict__ ltab,
+                    const T *__restrict__ Tin, T *__restrict__ qout, int M) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *ring = reinterpret_cast<T *>(smem_raw);        // [RING][AF][RH][RW]
+  __shared__ T scy[AY + 1][AX];
+  const ApplyTile tile = tiles[blockIdx.x];
+  const ChipDev ch = chips[tile.chip];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * AX + tx;
+  const int x = tile.x0 + tx, y = tile.y0 + ty;
+  const int nx = ch.nx, ny = ch.ny, nz = ch.nz;
+  const int nxny = nx * ny;
+  const bool in = x < nx && y < ny;
+  const int m0 = blockIdx.y * AF;
+  const int nf = M - m0 < AF ? M - m0 : AF;
+  const long long fb = ch.off * (long long)M + (long long)m0 * ch.n;
+  const int loc0 = y * nx + x;
+  // 16-byte copies need 16-byte aligned rows and field strides
+  const bool vec = ((nx * (int)sizeof(T)) % 16 == 0) && ((ch.n * (long long)sizeof(T)) % 16 == 0) &&
+                   (((fb * (long long)sizeof(T)) % 16) == 0);
+  for (int i = tid; i < RING * AF * RH * RW; i += AX * AY) ring[i] = T(0);
+  __syncthreads();
+  for (int zz = 0; zz <= AD; ++zz) {
+    if (zz < nz) stage_plane<T>(ring, Tin, fb, ch.n, nf, zz, nx, ny, tile.x0, tile.y0, vec);
+    cp_async_commit();
+  }
+  const int px = tx + 4, py = ty + 1;    // own position in a staged plane
+  T czm = T(0);
+  T prev[AF];                            // T at z - 1 of the own cell, per field
+#pragma unroll
+  for (int f = 0; f < AF; ++f) prev[f] = T(0);
+  for (int z = 0; z < nz; ++z) {
+    // planes up to z + 1 have landed; the AD - 1 newest copies may be pending
+    cp_async_wait<AD - 1>();
+    const long long a = ch.off + (long long)z * nxny + loc0;
+    typename Coef4<T>::type c4;
+    T cxm, cym_l = T(0);
+    if (ch.layered) {
+      // layered chip: conductances from the z-row's table, no per-cell loads
+      const T *lt = ltab + (ch.lz + z) * kLT;
+      const T gx = __ldg(lt), gy = __ldg(lt + 1);
+      const int cx = (x == 0 ? 1 : 0) | (x == nx - 1 ? 2 : 0);
+      const int cy = (y == 0 ? 1 : 0) | (y == ny - 1 ? 2 : 0);
+      c4.x = x + 1 < nx ? gx : T(0);
+      c4.y = y + 1 < ny ? gy : T(0);
+      c4.z = __ldg(lt + 2);
+      c4.w = __ldg(lt + 4 + 4 * cx + cy);
+      cxm = x > 0 ? gx : T(0);
+      cym_l = y > 0 ? gy : T(0);
+    } else {
+      if (in) c4 = load_coef<T>(g, a);
+      else { c4.x = T(0); c4.y = T(0); c4.z = T(0); c4.w = T(0); }
+      cxm = __shfl_up_sync(0xffffffffu, c4.x, 1);
+      if (tx == 0) cxm = (tile.x0 > 0 && y < ny) ? load_coef<T>(g, a - 1).x : T(0);
+      if (x == 0) cxm = T(0);
+      scy[ty + 1][tx] = c4.y;
+      if (ty == 0) scy[0][tx] = (tile.y0 > 0 && x < nx) ? load_coef<T>(g, a - nx).y : T(0);
+    }
+    __syncthreads();
+    if (z + AD + 1 < nz) stage_plane<T>(ring, Tin, fb, ch.n, nf, z + AD + 1, nx, ny, tile.x0, tile.y0, vec);
+    cp_async_commit();
+    const T cym = ch.layered ? cym_l : (y > 0 ? scy[ty][tx] : T(0));
+    const T *pc = ring + (z % RING) * (AF * RH * RW);
+    const T *pn = ring + ((z + 1) % RING) * (AF * RH * RW);
+#pragma unroll
+    for (int f = 0; f < AF; ++f) {
+      const int o = (f * RH + py) * RW + px;
+      const T c = pc[o];
+      if (in && f < nf) {
+        T r = c4.w * c;
+        r += c4.x * (c - pc[o + 1]);
+        r += cxm * (c - pc[o - 1]);
+        r += c4.y * (c - pc[o + RW]);
+        r += cym * (c - pc[o - RW]);
+        r += c4.z * (c - (z + 1 < nz ? pn[o] : c));
+        r += czm * (c - prev[f]);
+        qout[fb + (long long)f * ch.n + (long long)z * nxny + loc0] = r;
+      }
+      prev[f] = c;
+    }
+    czm = c4.z;
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+}
+
+// four consecutive values from shared memory (16-byte aligned)
+template <typename T, int unused>
+__device__ __forceinline__ void ld4(T *d, const T *p, int, int) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2 *>(p);
+    const double2 b = *reinterpret_cast<const double2 *>(p + 2);
+    d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y;
+  }
+}
+// four consecutive values to global memory (16-byte aligned, streaming)
+template <typename T>
+__device__ __forceinline__ void st4g(T *p, const T *v) {
+  if constexpr (sizeof(T) == 4) {
+    __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+  } else {
+    __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
+    __stcs(reinterpret_cast<double2 *>(p + 2), make_double2(v[2], v[3]));
+  }
+}
+
+// Vectorised form for layered chips whose rows and fields are 16-byte
+// aligned: a thread owns 4 consecutive x-cells (one 16-byte vector per
+// row), a CTA of 32 x 8 threads a 128 x 8 column tile, VF fields, and a ring
+// of three staged planes (z, z + 1 landed, z + 2 in flight).  Each thread's
+// staging chunks are fixed over the march, so their offsets are computed
+// once; per plane a chunk costs one add and one cp.async.
+constexpr int VX = 128, VRW = VX + 8, VRING = 3;
+
+template <typename T, int VF>
+__global__ void __launch_bounds__(256)
+apply_fields_vec_kernel(const ApplyTile *__restrict__ tiles, const ChipDev *__restrict__ chips,
+                        const T *__restrict__ ltab, const T *__restrict__ Tin,
+                        T *__restrict__ qout, int M) {
+  constexpr int VE = 16 / (int)sizeof(T);            // elements per 16-byte chunk
+  constexpr int CPR = VRW / VE;                       // chunks per staged row
+  constexpr int SLOT = VF * RH * VRW;                 // elements per staged plane
+  constexpr int NCH = VF * RH * CPR;                  // chunks per staged plane
+  constexpr int PER = (NCH + 255) / 256;              // chunks per thread
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *ring = reinterpret_cast<T *>(smem_raw);          // [VRING][VF][RH][VRW]
+  const ApplyTile tile = tiles[blockIdx.x];
+  const ChipDev ch = chips[tile.chip];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const int nx = ch.nx, ny = ch.ny, nz = ch.nz, nxny = nx * ny;
+  const int x = tile.x0 + 4 * tx, y = tile.y0 + ty;
+  const bool in = x < nx && y < ny;                   // nx is a multiple of 4
+  const int m0 = blockIdx.y * VF;
+  const int nf = M - m0 < VF ? M - m0 : VF;
+  const T *src = Tin + ch.off * (long long)M + (long long)m0 * ch.n;
+  T *dst = qout + ch.off * (long long)M + (long long)m0 * ch.n;
+  // fixed staging chunks: smem offset within a slot, element offset within a plane
+  int c_sm[PER], c_gl[PER];
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int i = tid + 256 * k;
+    c_sm[k] = -1;
+    c_gl[k] = 0;
+    if (i < NCH) {
+      const int f = i / (RH * CPR), rem = i % (RH * CPR);
+      const int r = rem / CPR, cch = rem % CPR;
+      const int yy = tile.y0 - 1 + r, xx = tile.x0 - 4 + cch * VE;
+      if (f < nf && yy >= 0 && yy < ny && xx >= 0 && xx + VE <= nx) {
+        c_sm[k] = (f * RH + r) * VRW + cch * VE;
+        c_gl[k] = f * (int)ch.n + yy * nx + xx;
+      }
+    }
+  }
+  for (int i = tid; i < VRING * SLOT; i += 256) ring[i] = T(0);
+  __syncthreads();
+  auto stage = [&](int z) {
+    T *slot = ring + (z % VRING) * SLOT;
+    const T *plane = src + (long long)z * nxny;
+#pragma unroll
+    for (int k = 0; k < PER; ++k)
+      if (c_sm[k] >= 0) cp_async16(slot + c_sm[k], plane + c_gl[k]);
+  };
+  stage(0);
+  cp_async_commit();
+  if (nz > 1) stage(1);
+  cp_async_commit();
+  // edge classes of the four cells (layer tables: 4 * cx + cy)
+  const int cyc = (y == 0 ? 1 : 0) | (y == ny - 1 ? 2 : 0);
+  int cls[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) cls[j] = 4 * ((x + j == 0 ? 1 : 0) | (x + j == nx - 1 ? 2 : 0)) + cyc;
+  const int p0 = 4 + 4 * tx, pr = ty + 1;            // own position in a staged row
+  T prev[VF][4];
+#pragma unroll
+  for (int f = 0; f < VF; ++f)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) prev[f][j] = T(0);
+  T czm = T(0);
+  for (int z = 0; z < nz; ++z) {
+    cp_async_wait<0>();
+    __syncthreads();
+    if (z + 2 < nz) stage(z + 2);
+    cp_async_commit();
+    const T *lt = ltab + (ch.lz + z) * kLT;
+    const T gx = __ldg(lt), gy = __ldg(lt + 1), gz = __ldg(lt + 2);
+    const T cyp = y + 1 < ny ? gy : T(0), cym = y > 0 ? gy : T(0);
+    T cb[4], cxp[4], cxm[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      cb[j] = __ldg(lt + 4 + cls[j]);
+      cxp[j] = x + j + 1 < nx ? gx : T(0);
+      cxm[j] = x + j > 0 ? gx : T(0);
+    }
+    const T czp = gz;   // zero on the bottom row by construction
+    const T *pc = ring + (z % VRING) * SLOT;
+    const T *pn = ring + ((z + 1) % VRING) * SLOT;
+#pragma unroll
+    for (int f = 0; f < VF; ++f) {
+      const int o = (f * RH + pr) * VRW + p0;
+      T c[4], up[4], dn[4], zp[4];
+      ld4<T, 1>(c, pc + o, 0, 0);
+      ld4<T, 1>(up, pc + o - VRW, 0, 0);
+      ld4<T, 1>(dn, pc + o + VRW, 0, 0);
+      ld4<T, 1>(zp, pn + o, 0, 0);
+      const T left = pc[o - 1], right = pc[o + 4];
+      if (in && f < nf) {
+        T r[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const T xl = j == 0 ? left : c[j - 1];
+          const T xr = j == 3 ? right : c[j + 1];
+          T v = cb[j] * c[j];
+          v += cxp[j] * (c[j] - xr);
+          v += cxm[j] * (c[j] - xl);
+          v += cyp * (c[j] - dn[j]);
+          v += cym * (c[j] - up[j]);
+          v += czp * (c[j] - (z + 1 < nz ? zp[j] : c[j]));
+          v += czm * (c[j] - prev[f][j]);
+          r[j] = v;
+        }
+        st4g<T>(dst + (long long)f * ch.n + (long long)z * nxny + (long long)y * nx + x, r);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) prev[f][j] = c[j];
+    }
+    czm = czp;
+  }
+  cp_async_wait<0>();
 }
 
 int launch_apply_fields(const blockoa_operator *op, const void *Tin, void *qout, int M, int dtype,
                         cudaStream_t st) {
   blockoa_operator *mop = const_cast<blockoa_operator *>(op);
   if (!mop->apply_blocks) {
-    // launch table: 256-cell blocks of every chip (built once per operator)
-    std::vector<CellBlock> blocks;
-    for (int c = 0; c < op->n_chips; ++c)
-      for (long long b = 0; b < op->chips[c].n; b += AP_CELLS)
-        blocks.push_back({c, 0, op->chips[c].off + b});
+    // launch table: 32 x 8 column tiles of every chip (built once per operator)
+    std::vector<ApplyTile> tiles;
+    for (int c = 0; c < op->n_chips; ++c) {
+      const ChipDev &ch = op->chips[c];
+      for (int y = 0; y < ch.ny; y += AY)
+        for (int x = 0; x < ch.nx; x += AX) tiles.push_back({c, x, y, 0});
+    }
     void *d = nullptr;
-    BLOCKOA_CUDA(cudaMalloc(&d, sizeof(CellBlock) * blocks.size()));
-    cudaError_t e = cudaMemcpy(d, blocks.data(), sizeof(CellBlock) * blocks.size(), cudaMemcpyHostToDevice);
+    BLOCKOA_CUDA(cudaMalloc(&d, sizeof(ApplyTile) * tiles.size()));
+    cudaError_t e = cudaMemcpy(d, tiles.data(), sizeof(ApplyTile) * tiles.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cudaFree(d); return cuda_status(e, "apply table"); }
     mop->apply_blocks = d;
-    mop->n_apply_blocks = (int)blocks.size();
+    mop->n_apply_blocks = (int)tiles.size();
   }
-  constexpr int F = 8;
-  dim3 grid((unsigned)op->n_apply_blocks, (unsigned)((M + F - 1) / F));
+  // vectorised kernel when every chip is layered and 16-byte aligned
+  bool vec_ok = true;
+  for (int c = 0; c < op->n_chips; ++c) {
+    const ChipDev &ch = op->chips[c];
+    vec_ok = vec_ok && ch.layered && ch.nx % 4 == 0 && ch.n % 4 == 0 && ch.off % 4 == 0;
+  }
+  constexpr int VF32 = 4, VF64 = 2;
+  const size_t smv32 = sizeof(float) * VRING * VF32 * RH * VRW;
+  const size_t smv64 = sizeof(double) * VRING * VF64 * RH * VRW;
+  const size_t sm32 = sizeof(float) * RING * AF * RH * RW, sm64 = sizeof(double) * RING * AF * RH * RW;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(apply_fields_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm32);
+    cudaFuncSetAttribute(apply_fields_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm64);
+    cudaFuncSetAttribute(apply_fields_vec_kernel<float, VF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv32);
+    cudaFuncSetAttribute(apply_fields_vec_kernel<double, VF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv64);
+    attr = true;
+  }
+  if (vec_ok && !mop->apply_vec_blocks) {
+    std::vector<ApplyTile> tiles;
+    for (int c = 0; c < op->n_chips; ++c) {
+      const ChipDev &ch = op->chips[c];
+      for (int y = 0; y < ch.ny; y += AY)
+        for (int x = 0; x < ch.nx; x += VX) tiles.push_back({c, x, y, 0});
+    }
+    void *d = nullptr;
+    BLOCKOA_CUDA(cudaMalloc(&d, sizeof(ApplyTile) * tiles.size()));
+    cudaError_t e = cudaMemcpy(d, tiles.data(), sizeof(ApplyTile) * tiles.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(d); return cuda_status(e, "apply table"); }
+    mop->apply_vec_blocks = d;
+    mop->n_apply_vec_blocks = (int)tiles.size();
+  }
   cudaEvent_t ev;
   time_begin(mop, st, &ev);
   g_launches += 1;
-  if (dtype == BLOCKOA_FP64)
-    apply_fields_kernel<double, F><<<grid, AP_CELLS, 0, st>>>(
-        (const CellBlock *)op->apply_blocks, op->d_chips, op->g64, (const double *)Tin, (double *)qout, M);
-  else
-    apply_fields_kernel<float, F><<<grid, AP_CELLS, 0, st>>>(
-        (const CellBlock *)op->apply_blocks, op->d_chips, op->g32, (const float *)Tin, (float *)qout, M);
+  if (vec_ok) {
+    dim3 block(32, AY);
+    if (dtype == BLOCKOA_FP64) {
+      dim3 grid((unsigned)op->n_apply_vec_blocks, (unsigned)((M + VF64 - 1) / VF64));
+      apply_fields_vec_kernel<double, VF64><<<grid, block, smv64, st>>>(
+          (const ApplyTile *)op->apply_vec_blocks, op->d_chips, op->lt64, (const double *)Tin,
+          (double *)qout, M);
+    } else {
+      dim3 grid((unsigned)op->n_apply_vec_blocks, (unsigned)((M + VF32 - 1) / VF32));
+      apply_fields_vec_kernel<float, VF32><<<grid, block, smv32, st>>>(
+          (const ApplyTile *)op->apply_vec_blocks, op->d_chips, op->lt32, (const float *)Tin,
+          (float *)qout, M);
+    }
+  } else {
+    dim3 grid((unsigned)op->n_apply_blocks, (unsigned)((M + AF - 1) / AF));
+    dim3 block(AX, AY);
+    if (dtype == BLOCKOA_FP64)
+      apply_fields_kernel<double><<<grid, block, sm64, st>>>(
+          (const ApplyTile *)op->apply_blocks, op->d_chips, op->g64, op->lt64, (const double *)Tin,
+          (double *)qout, M);
+    else
+      apply_fields_kernel<float><<<grid, block, sm32, st>>>(
+          (const ApplyTile *)op->apply_blocks, op->d_chips, op->g32, op->lt32, (const float *)Tin,
+          (float *)qout, M);
+  }
   cudaError_t e = cudaGetLastError();
   time_end(mop, st, KC_APPLY, ev);
   return cuda_status(e, "apply_fields");

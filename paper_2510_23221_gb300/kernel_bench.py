@@ -1,0 +1,75 @@
+"""Microbenchmark of single C-ABI calls (operator action, combination).
+
+    python -m paper_2510_23221_gb300.kernel_bench --call apply --chip 512x512x16 --M 1000
+    python -m paper_2510_23221_gb300.kernel_bench --call combine --chip 128x128x8 --s 32 --M 5000
+
+Times `--reps` calls with CUDA events after `--warmup` calls and prints one
+JSON line with the mean time and the algorithmic bandwidth (operator action:
+read T + write q; combination: write T + read the bfloat16x3 basis images).
+Inputs are random; no correctness check (the test suite does that).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+
+def main():
+    import torch
+
+    from . import blockoa as bo
+    from . import build, synth
+
+    p = argparse.ArgumentParser()
+    p.add_argument("--call", choices=["apply", "combine"], default="apply")
+    p.add_argument("--chip", default="128x128x8")
+    p.add_argument("--s", type=int, default=32)
+    p.add_argument("--M", type=int, default=1000)
+    p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--reps", type=int, default=10)
+    a = p.parse_args()
+    build.build()
+    nx, ny, nl = (int(v) for v in a.chip.split("x"))
+    w = synth.single_chip_workload(nx, ny, nl, s=a.s, M=a.M, cfg=7)
+    op = bo.assemble(w.chips)
+    n, M, s = op.n_total, a.M, a.s
+    prec = bo.MIXED if a.precision == "mixed" else bo.FP64
+    fdt = torch.float32 if prec == bo.MIXED else torch.float64
+    T = torch.randn(n * M, dtype=fdt, device="cuda")
+    q = torch.empty_like(T)
+    U = torch.randn(n * s, dtype=torch.float64, device="cuda")
+    C = torch.from_numpy(np.ascontiguousarray(w.coeffs[0].ravel())).cuda()
+
+    def call():
+        if a.call == "apply":
+            bo.apply_operator(op, T, q, M, prec)
+        else:
+            bo.combine(op, U, C, T, s, M, prec)
+
+    for _ in range(a.warmup):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        call()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.reps
+    esz = 4 if prec == bo.MIXED else 8
+    if a.call == "apply":
+        nbytes = 2 * esz * n * M
+    else:
+        nbytes = esz * n * M + (6 * ((s + 15) // 16 * 16) * n if prec == bo.MIXED else 8 * n * s)
+    kt = bo.kernel_times(op)
+    print(json.dumps({"call": a.call, "chip": a.chip, "cells": n, "s": s, "M": M,
+                      "precision": a.precision, "ms": round(ms, 4),
+                      "GBps": round(nbytes / ms / 1e6, 1),
+                      "kernels": {k: round(v[0] / v[1], 4) for k, v in kt.items() if v[1]}}))
+
+
+if __name__ == "__main__":
+    main()

@@ -115,6 +115,44 @@ def test_apply_fp32(idx):
     assert np.all(relcols(q.cpu().numpy().astype(np.float64).reshape(M, -1), ref, axis=1) < 2e-6)
 
 
+@pytest.mark.parametrize("precision", [bo.FP64, bo.MIXED])
+@pytest.mark.parametrize("nx,ny", [(37, 21), (36, 20), (260, 9)])
+def test_layered_and_per_cell_forms_agree_bitwise(precision, nx, ny):
+    """A layered chip and the same chip given cell by cell give the same q
+    (aligned layered chips take the vectorised kernel, the rest the scalar one)."""
+    layered = synth.random_small_chip(201, nx, ny, 4, h_top=2e4, h_side=3e3)
+    per_cell = synth.random_small_chip(201, nx, ny, 4, h_top=2e4, h_side=3e3)
+    per_cell.k_cell = layered.cell_k()
+    M = 11
+    dt = torch.float64 if precision == bo.FP64 else torch.float32
+    T = torch.randn(M * layered.n, dtype=dt, device="cuda")
+    q1 = torch.empty_like(T)
+    q2 = torch.empty_like(T)
+    bo.apply_operator(bo.assemble([layered]), T, q1, M, precision)
+    bo.apply_operator(bo.assemble([per_cell]), T, q2, M, precision)
+    assert torch.equal(q1, q2)
+
+
+def test_apply_nonuniform_per_cell_conductivity():
+    chip = synth.random_small_chip(202, 19, 14, 3, h_top=1e4, h_side=2e3)
+    rng = np.random.default_rng(202)
+    chip.k_cell = np.exp(rng.uniform(0, np.log(400), (chip.nz, chip.ny, chip.nx)))
+    op = bo.assemble([chip])
+    got = bo.export_conductances(op, 0)
+    ref = orc.face_conductances(chip)
+    for k in ("gx", "gy", "gz", "gb"):
+        assert np.array_equal(got[k], ref[k])
+    M = 5
+    T = np.random.default_rng(3).standard_normal((M, chip.n))
+    q = torch.empty(M * chip.n, dtype=torch.float64, device="cuda")
+    bo.apply_operator(op, cuda(T.ravel()), q, M, bo.FP64)
+    assert np.all(relcols(q.cpu().numpy().reshape(M, -1), orc.apply_operator(orc.assemble(chip), T), axis=1) < 1e-13)
+    B = np.random.default_rng(4).uniform(0, 1e-2, (chip.n, 4))
+    (X,), (st,) = _solve([chip], [B], 4, bo.MIXED, 1e-11)
+    assert st.status == bo.OK
+    assert np.all(relcols(X, np.linalg.solve(orc.assemble(chip).toarray(), B)) < 1e-8)
+
+
 def test_apply_batched_fields_layout():
     chips = small_chips()
     M = 3
