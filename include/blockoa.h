@@ -82,7 +82,11 @@ typedef struct {
   double deflate_tol;   /* pivot threshold on the scaled Gram (<= 0: 1e-14 FP64, 1e-6 float32 inner) */
   const double *x0;     /* device [n_total][s] initial guess, or NULL for zero */
   int check_every;      /* block iterations between convergence polls by the host (<= 0: 8) */
+  int precond;          /* BLOCKOA_PRECOND_NONE (the paper's unpreconditioned block CG) or
+                           BLOCKOA_PRECOND_JACOBI (diagonal: directions from D^-1 R) */
 } blockoa_solve_opts;
+
+enum { BLOCKOA_PRECOND_NONE = 0, BLOCKOA_PRECOND_JACOBI = 1 };
 
 typedef struct {
   int status;           /* blockoa_status of this chip */
@@ -129,6 +133,8 @@ int blockoa_build_rhs(const blockoa_operator *op, const double *density, double 
  * Each iteration: Q = A P; Gamma = P^T Q; Jacobi-scaled pivoted Cholesky of
  * Gamma with deflation of pivots <= deflate_tol; alpha = Gamma^-1 P^T R;
  * X += P alpha; R -= Q alpha; beta = -Gamma^-1 Q^T R; P = R + P beta.
+ * With BLOCKOA_PRECOND_JACOBI, Z = D^-1 R (D = diag(A)) replaces R in the
+ * new directions: beta = -Gamma^-1 Q^T Z, P = Z + P beta (same solution).
  * MIXED runs that loop in float32 (Gram products accumulated to float64)
  * inside float64 iterative refinement on the true residual B - A X.
  * Stops when every column meets ||B_j - A X_j|| <= rtol ||B_j||.

@@ -183,6 +183,29 @@ __global__ void assemble_kernel(const Unit *__restrict__ units, const ChipDev *_
   }
 }
 
+// 1 / diag(A) per cell: the sum of the cell's face conductances and its
+// Robin conductance (float64, then rounded to float32).
+__global__ void inv_diag_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chips,
+                                const double *__restrict__ g64, double *__restrict__ d64,
+                                float *__restrict__ d32) {
+  const Unit u = units[blockIdx.x];
+  const ChipDev ch = chips[u.chip];
+  const long long nxny = (long long)ch.nx * ch.ny;
+  const double4 *g = reinterpret_cast<const double4 *>(g64);
+  for (long long a = u.begin + threadIdx.x; a < u.end; a += blockDim.x) {
+    const long long loc = a - ch.off;
+    const int x = (int)(loc % ch.nx), y = (int)((loc / ch.nx) % ch.ny), z = (int)(loc / nxny);
+    const double4 c = g[a];
+    double d = c.x + c.y + c.z + c.w;
+    if (x > 0) d += g[a - 1].x;
+    if (y > 0) d += g[a - ch.nx].y;
+    if (z > 0) d += g[a - nxny].z;
+    const double inv = d > 0.0 ? 1.0 / d : 0.0;
+    d64[a] = inv;
+    d32[a] = (float)inv;
+  }
+}
+
 // One thread per z-row of a layered chip: the row's interior face
 // conductances and the Robin conductance of every edge class, with the same
 // float64 operations (and order) as assemble_kernel.
@@ -346,6 +369,10 @@ extern "C" int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips,
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc g64"));
   e = cudaMalloc((void **)&op->g32, sizeof(float) * 4 * op->n_total);
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc g32"));
+  e = cudaMalloc((void **)&op->dinv64, sizeof(double) * op->n_total);
+  if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc dinv64"));
+  e = cudaMalloc((void **)&op->dinv32, sizeof(float) * op->n_total);
+  if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc dinv32"));
   e = cudaMalloc((void **)&op->lt64, sizeof(double) * kLT * zk.size());
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc lt64"));
   e = cudaMalloc((void **)&op->lt32, sizeof(float) * kLT * zk.size());
@@ -371,7 +398,9 @@ extern "C" int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips,
       (const double *)d_zdz, (const double *)d_kc, op->g64, op->g32);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(cuda_status(e, "assemble_kernel"));
-  g_launches += 1;
+  g_launches += 2;
+  inv_diag_kernel<<<(unsigned)units.size(), 256, 0, st>>>((const Unit *)d_units, op->d_chips, op->g64,
+                                                          op->dinv64, op->dinv32);
   layer_table_kernel<<<(unsigned)n_chips, 64, 0, st>>>(op->d_chips, (const ChipPhys *)d_phys,
                                                       (const double *)d_zk, (const double *)d_zdz,
                                                       n_chips, op->lt64, op->lt32);
@@ -468,6 +497,8 @@ extern "C" void blockoa_destroy(blockoa_operator *op) {
   if (op->d_chips) cudaFree(op->d_chips);
   if (op->g64) cudaFree(op->g64);
   if (op->g32) cudaFree(op->g32);
+  if (op->dinv64) cudaFree(op->dinv64);
+  if (op->dinv32) cudaFree(op->dinv32);
   if (op->lt64) cudaFree(op->lt64);
   if (op->lt32) cudaFree(op->lt32);
   cudaGetLastError();

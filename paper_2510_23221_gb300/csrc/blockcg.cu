@@ -324,12 +324,12 @@ spmm_gram_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chi
 }
 
 // X += P alpha, R -= Q alpha; W += Q^T R_new and rn2 += ||R_new_j||^2.
-template <typename T, int S>
+template <typename T, int S, bool PC>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 update_gram_kernel(const Unit *__restrict__ units, const ChipSolveState *__restrict__ state,
                    const T *__restrict__ alpha, const T *__restrict__ P, const T *__restrict__ Q,
                    T *__restrict__ X, T *__restrict__ R, double *__restrict__ wgram,
-                   double *__restrict__ rn2) {
+                   double *__restrict__ rn2, const T *__restrict__ dinv) {
   using G = BK<T, S>;
   constexpr int V = G::V;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -383,6 +383,15 @@ update_gram_kernel(const Unit *__restrict__ units, const ChipSolveState *__restr
     for (int k = 0; k < 4; ++k)
 #pragma unroll
       for (int v = 0; v < V; ++v) rn[v] += rv[k][v] * rv[k][v];  // zero past the end
+    if constexpr (PC) {
+      // Gram with Z = D^-1 R_new (R stays unscaled in memory)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const T di = base + cl0 + k < u.end ? dinv[base + cl0 + k] : T(0);
+#pragma unroll
+        for (int v = 0; v < V; ++v) rv[k][v] *= di;
+      }
+    }
     put_tile<T, G::LD>(sR, rv, cl0, j0);
     __syncthreads();
     gram_tile<T, S>(aw, sQ, sR, i0, k0, grp);
@@ -413,10 +422,11 @@ update_gram_kernel(const Unit *__restrict__ units, const ChipSolveState *__restr
 }
 
 // P = R + P beta (one tile per CTA).
-template <typename T, int S>
+template <typename T, int S, bool PC>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 p_update_kernel(const Unit *__restrict__ units, const ChipSolveState *__restrict__ state,
-                const T *__restrict__ beta, const T *__restrict__ R, T *__restrict__ P) {
+                const T *__restrict__ beta, const T *__restrict__ R, T *__restrict__ P,
+                const T *__restrict__ dinv) {
   using G = BK<T, S>;
   constexpr int V = G::V;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -436,6 +446,14 @@ p_update_kernel(const Unit *__restrict__ units, const ChipSolveState *__restrict
     }
     T rv[4][V];
     load_block<T, S>(rv, R, base + cl0, u.end, j0);
+    if constexpr (PC) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const T di = base + cl0 + k < u.end ? dinv[base + cl0 + k] : T(0);
+#pragma unroll
+        for (int v = 0; v < V; ++v) rv[k][v] *= di;
+      }
+    }
     __syncthreads();
 #pragma unroll 4
     for (int i = 0; i < S; ++i) {
@@ -777,17 +795,18 @@ __global__ void col_norms_kernel(const Unit *__restrict__ units, const double *_
 }
 
 // Start an inner solve on A D = R64: R = R64 / sigma_j, P = R, D = 0.
-template <typename T, int S>
+template <typename T, int S, bool PC>
 __global__ void inner_init_kernel(const Unit *__restrict__ units, const int *__restrict__ outer_active,
                                   const double *__restrict__ R64, const double *__restrict__ inv_sigma,
-                                  T *__restrict__ R, T *__restrict__ P, T *__restrict__ D) {
+                                  T *__restrict__ R, T *__restrict__ P, T *__restrict__ D,
+                                  const T *__restrict__ dinv) {
   const Unit u = units[blockIdx.x];
   if (!outer_active[u.chip]) return;
   const double *is = inv_sigma + (long long)u.chip * S;
   for (long long i = u.begin * S + threadIdx.x; i < u.end * S; i += blockDim.x) {
     const T v = (T)(R64[i] * is[i % S]);
     R[i] = v;
-    P[i] = v;
+    P[i] = PC ? v * dinv[i / S] : v;
     D[i] = T(0);
   }
 }
@@ -833,7 +852,7 @@ struct SolveWS {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t tev[7] = {};      // recorded around the kernels of each chunk's first iteration
-  int graph_iters = 0, graph_maxiter = -1, graph_s = -1;
+  int graph_iters = 0, graph_maxiter = -1, graph_s = -1, graph_pc = -1;
   double graph_tol = -1.0;
   std::vector<void *> allocs;
 };
@@ -876,16 +895,16 @@ constexpr size_t update_smem() {
 template <typename T, int S>
 constexpr size_t pupdate_smem() { return tile_bytes<T, S>() + S * S * sizeof(T); }
 
-template <typename T, int S>
+template <typename T, int S, bool PC>
 static void set_smem_limits() {
   static bool done = false;
   if (done) return;
   done = true;
   cudaFuncSetAttribute(spmm_gram_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)spmm_smem<T, S>());
-  cudaFuncSetAttribute(update_gram_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(update_gram_kernel<T, S, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)update_smem<T, S>());
-  cudaFuncSetAttribute(p_update_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(p_update_kernel<T, S, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pupdate_smem<T, S>());
   cudaFuncSetAttribute(factor_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)factor_smem_bytes<S>());
@@ -893,10 +912,11 @@ static void set_smem_limits() {
 
 // One block-CG iteration for every active chip; with `ev`, an event is
 // recorded before each kernel and after the last (for live timing).
-template <typename T, int S>
+template <typename T, int S, bool PC>
 static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const SmallArgs &sa,
                              cudaStream_t st, cudaEvent_t *ev) {
   const T *g = sizeof(T) == 4 ? (const T *)op->g32 : (const T *)op->g64;
+  const T *dinv = sizeof(T) == 4 ? (const T *)op->dinv32 : (const T *)op->dinv64;
   const unsigned nsolve = (unsigned)(ws->n_chips * S);
   // external record nodes: the events carry timestamps when the graph runs
   auto mark = [&](int i) {
@@ -911,14 +931,14 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
   mark(2);
   trsolve_kernel<T, S, true><<<nsolve, 32, 0, st>>>(sa);
   mark(3);
-  update_gram_kernel<T, S><<<ws->n_units, 256, update_smem<T, S>(), st>>>(
+  update_gram_kernel<T, S, PC><<<ws->n_units, 256, update_smem<T, S>(), st>>>(
       ws->units, ws->state, (const T *)ws->alpha, (const T *)ws->P, (const T *)ws->Q,
-      (T *)ws->D, (T *)ws->R, ws->wg, ws->rn2);
+      (T *)ws->D, (T *)ws->R, ws->wg, ws->rn2, dinv);
   mark(4);
   trsolve_kernel<T, S, false><<<nsolve, 32, 0, st>>>(sa);
   mark(5);
-  p_update_kernel<T, S><<<ws->n_units_tile, 256, pupdate_smem<T, S>(), st>>>(
-      ws->units_tile, ws->state, (const T *)ws->beta, (const T *)ws->R, (T *)ws->P);
+  p_update_kernel<T, S, PC><<<ws->n_units_tile, 256, pupdate_smem<T, S>(), st>>>(
+      ws->units_tile, ws->state, (const T *)ws->beta, (const T *)ws->R, (T *)ws->P, dinv);
   mark(6);
 }
 
@@ -990,7 +1010,8 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     BLOCKOA_CUDA(cudaMemset(ws->lfac, 0, sm));
     BLOCKOA_CUDA(cudaMemset(ws->rank, 0, sizeof(int) * (size_t)nc));
     BLOCKOA_CUDA(cudaMemset(ws->perm, 0, sizeof(int) * (size_t)nc * S));
-    set_smem_limits<T, S>();
+    set_smem_limits<T, S, false>();
+    set_smem_limits<T, S, true>();
   }
 
   const double rtol = o->rtol;
@@ -999,6 +1020,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
   const int max_refine = o->max_refine > 0 ? o->max_refine : 12;
   const double tol = o->deflate_tol > 0 ? o->deflate_tol : (prec == BLOCKOA_MIXED ? 1e-6 : 1e-14);
   const int check_every = o->check_every > 0 ? o->check_every : 8;
+  const int pc = o->precond == BLOCKOA_PRECOND_JACOBI ? 1 : 0;
 
   SmallArgs sa;
   sa.state = ws->state; sa.gram = ws->gram; sa.rho = ws->rho; sa.wg = ws->wg; sa.rn2 = ws->rn2;
@@ -1008,14 +1030,15 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
 
   // Build (or reuse) the graph of `check_every` iterations.
   if (!ws->graph || ws->graph_iters != check_every || ws->graph_maxiter != maxiter ||
-      ws->graph_s != s || ws->graph_tol != tol) {
+      ws->graph_s != s || ws->graph_tol != tol || ws->graph_pc != pc) {
     if (ws->graph) { cudaGraphExecDestroy(ws->graph); ws->graph = nullptr; }
     cudaGraph_t graph = nullptr;
     for (int i = 0; i < 7; ++i)
       if (!ws->tev[i]) BLOCKOA_CUDA(cudaEventCreate(&ws->tev[i]));
     BLOCKOA_CUDA(cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < check_every; ++k)
-      launch_iteration<T, S>(op, ws, sa, ws->cap, k == 0 ? ws->tev : nullptr);
+      if (pc) launch_iteration<T, S, true>(op, ws, sa, ws->cap, k == 0 ? ws->tev : nullptr);
+      else launch_iteration<T, S, false>(op, ws, sa, ws->cap, k == 0 ? ws->tev : nullptr);
     cudaError_t e = cudaStreamEndCapture(ws->cap, &graph);
     if (e != cudaSuccess) return cuda_status(e, "capture block-CG iterations");
     e = cudaGraphInstantiate(&ws->graph, graph, 0);
@@ -1025,6 +1048,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     ws->graph_maxiter = maxiter;
     ws->graph_s = s;
     ws->graph_tol = tol;
+    ws->graph_pc = pc;
   }
 
   // Inputs: padded B and X0, ||B_j||^2.
@@ -1109,8 +1133,17 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       BLOCKOA_CUDA(cudaMemsetAsync(ws->rn2, 0, sv, st));
     }
     g_launches += 2;
-    inner_init_kernel<T, S><<<ws->n_units_small, 256, 0, st>>>(
-        ws->units_small, ws->outer_active, ws->R64, ws->inv_sigma, (T *)ws->R, (T *)ws->P, (T *)ws->D);
+    {
+      const T *dinv = sizeof(T) == 4 ? (const T *)op->dinv32 : (const T *)op->dinv64;
+      if (pc)
+        inner_init_kernel<T, S, true><<<ws->n_units_small, 256, 0, st>>>(
+            ws->units_small, ws->outer_active, ws->R64, ws->inv_sigma, (T *)ws->R, (T *)ws->P,
+            (T *)ws->D, dinv);
+      else
+        inner_init_kernel<T, S, false><<<ws->n_units_small, 256, 0, st>>>(
+            ws->units_small, ws->outer_active, ws->R64, ws->inv_sigma, (T *)ws->R, (T *)ws->P,
+            (T *)ws->D, dinv);
+    }
     BLOCKOA_CUDA(cudaGetLastError());
     // Inner block-CG iterations, polled every `check_every` iterations.
     for (;;) {
@@ -1174,6 +1207,7 @@ extern "C" int blockoa_block_solve(blockoa_operator *op, const double *B, double
   }
   if (!(opts->rtol > 0.0) || opts->maxiter < 0) return BLOCKOA_ERR_INVALID;
   if (opts->precision != BLOCKOA_FP64 && opts->precision != BLOCKOA_MIXED) return BLOCKOA_ERR_INVALID;
+  if (opts->precond != BLOCKOA_PRECOND_NONE && opts->precond != BLOCKOA_PRECOND_JACOBI) return BLOCKOA_ERR_INVALID;
   if (s == 0) {
     for (int c = 0; c < op->n_chips; ++c) stats[c].status = BLOCKOA_OK;
     return BLOCKOA_OK;

@@ -266,6 +266,27 @@ def test_block_solve_batched_uneven():
             assert np.all(relcols(Xs[c], ref) < 1e-9)
 
 
+@pytest.mark.parametrize("precision", [bo.FP64, bo.MIXED])
+def test_jacobi_preconditioned_solve(precision):
+    """Diagonal preconditioning changes the iteration, not the solution."""
+    w = synth.small_fp64_workload()
+    chip = w.chips[0]
+    A = orc.assemble(chip)
+    B = orc.rhs(chip, w.density[0])
+    U_or, info = orc.block_cg(A, B, rtol=1e-12)
+    (X,), (st,) = _solve([chip], [B], 8, precision, 1e-12, precond=bo.PRECOND_JACOBI)
+    assert st.status == bo.OK and st.relres_max <= 1e-12
+    assert np.all(relcols(X, U_or) < 1e-9)
+    chips = small_chips()
+    rng = np.random.default_rng(78)
+    Bs = [rng.uniform(0, 1e-2, (c.n, 4)) for c in chips]
+    Xs, stats = _solve(chips, Bs, 4, precision, 1e-11, precond=bo.PRECOND_JACOBI)
+    for c, chip in enumerate(chips):
+        assert stats[c].status == bo.OK
+        ref = np.linalg.solve(orc.assemble(chip).toarray(), Bs[c])
+        assert np.all(relcols(Xs[c], ref) < 1e-8)
+
+
 def test_deflation_duplicate_and_zero_columns():
     chip = synth.random_small_chip(81, 12, 10, 3)
     B = np.random.default_rng(81).uniform(0, 1e-2, (chip.n, 6))
@@ -304,6 +325,9 @@ def test_invalid_calls_return_invalid():
     assert e.value.code == bo.ERR_INVALID
     with pytest.raises(bo.BlockoaError) as e:
         bo.block_solve(op, B, B.clone(), 4, rtol=0.0)
+    assert e.value.code == bo.ERR_INVALID
+    with pytest.raises(bo.BlockoaError) as e:
+        bo.block_solve(op, B, B.clone(), 4, precond=7)
     assert e.value.code == bo.ERR_INVALID
     T = torch.zeros(chip.n, dtype=torch.float64, device="cuda")
     with pytest.raises(bo.BlockoaError):
