@@ -4,16 +4,17 @@
 // space.  One iteration, per chip:
 //   Q = A P,   Gamma = P^T Q,   rho = P^T R                 (spmm_gram)
 //   factor D Gamma D (D = diag(Gamma)^-1/2) by diagonal-pivoted Cholesky,
-//   deflate pivots <= tol, alpha = Gamma^-1 rho             (small_solve, alpha)
-//   X += P alpha,  R -= Q alpha,  W = Q^T R,  ||R_j||^2     (update_gram)
-//   beta = -Gamma^-1 W, per-column convergence test         (small_solve, beta)
-//   P = R + P beta                                          (p_update)
-// Deflated columns get zero rows in alpha and beta.
+//   deflate pivots <= tol, alpha = Gamma^-1 rho             (alpha_solve)
+//   X += P alpha,  R -= Q alpha,  W = Q^T Z,  ||R_j||^2     (update_gram)
+//   beta = -Gamma^-1 W, per-column convergence test         (beta_solve)
+//   P = Z + P beta                                          (p_update)
+// with Z = R, or Z = diag(A)^-1 R under Jacobi preconditioning.  Deflated
+// columns get zero rows in alpha and beta (smallsolve.cuh).
 //
 // Precision.  FP64 runs the loop in float64.  MIXED runs it in float32 with
 // the Gram products folded into compensated float32 sums and reduced in
-// float64, the s x s factorisation and solves in float64, inside float64
-// iterative refinement on the true residual B - A X.
+// float64, the s x s factorisation and solves in double-float, inside
+// float64 iterative refinement on the true residual B - A X.
 //
 // Layout.  Block vectors are [n_total][S] with S in {8, 16, 32, 64} (the
 // caller's s columns zero-padded).  A CTA processes one unit: a contiguous
@@ -28,6 +29,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "smallsolve.cuh"
 
 namespace blockoa {
 
@@ -470,285 +472,6 @@ p_update_kernel(const Unit *__restrict__ units, const ChipSolveState *__restrict
   }
 }
 
-// ---------------------------------------------------------------- small s x s solves
-// Per chip, in float64: Jacobi-scaled, diagonal-pivoted Cholesky of the
-// Gram matrix with deflation (factor kernel, one CTA per chip), then
-// alpha = Gamma^-1 rho and beta = -Gamma^-1 W by substitution (solve
-// kernels, S/4 CTAs per chip, one warp per right-hand-side column).  One
-// thread evaluates each pivot's square root and reciprocal; substitutions
-// multiply by the stored reciprocals.  Accumulators are cleared by the
-// kernel that runs after their last reader: the factor kernel clears W and
-// ||R||^2 (read by the previous beta solve), the beta solve clears Gamma and
-// rho (read by the factor kernel and the alpha solve).
-struct SmallArgs {
-  ChipSolveState *state;
-  double *gram;     // [chip][S][S] Gamma accumulator
-  double *rho;      // [chip][S][S] rho = P^T R accumulator
-  double *wg;       // [chip][S][S] W = Q^T R accumulator
-  double *rn2;      // [chip][S] ||R_j||^2 accumulator
-  const double *target2;  // [chip][S] squared per-column targets
-  double *lfac;     // [chip][S][S] pivot-ordered lower-triangular factor L[i][k]
-  double *rinv;     // [chip][S] 1 / L[i][i]
-  int *perm;        // [chip][S] kept columns in pivot order
-  double *dsc;      // [chip][S] scaling diagonal
-  int *rank;        // [chip]
-  void *alpha;      // [chip][S][S] in the loop's precision
-  void *beta;       // [chip][S][S]
-  int s;            // caller's columns (for deflation counts)
-  int maxiter;      // limit on total iterations per chip
-  double tol;       // deflation threshold on scaled pivots
-};
-
-// 2^e as a float64 for -1022 <= e <= 1023.
-__device__ __forceinline__ double pow2(int e) {
-  return __longlong_as_double((long long)(e + 1023) << 52);
-}
-// 1/sqrt(x) in float64 for normal x > 0.  x = m 4^h with m in [1, 4) (exact
-// power-of-two scaling), float seed for m (about 2^-23 relative error), then
-// one Newton step y <- y (3 - m y^2) / 2, which squares the relative error
-// (about 2^-45).  Each float64 instruction holds this part's float64 pipe for
-// a whole warp's worth of cycles, so the pivot path keeps them few.
-__device__ __forceinline__ double rsqrt_nr(double x) {
-  const int ex = (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
-  const int h = ex >> 1;
-  const double m = x * pow2(-2 * h);
-  const double y = (double)rsqrtf((float)m);
-  return (y * fma(-0.5 * m, y * y, 1.5)) * pow2(-h);
-}
-
-template <int S>
-__host__ __device__ constexpr size_t factor_smem_bytes() { return 2 * sizeof(double) * S * (S + 1); }
-
-// Pivot search over the remaining Schur diagonal (warp 0): largest value,
-// lowest index on ties; positive float64 values order like their bit
-// patterns read as int64.  Lane 0 publishes the pivot, its square root and
-// its reciprocal square root (or S when the largest pivot is <= tol).
-template <int S>
-__device__ __forceinline__ void pivot_search(const double *dg, const int *removed, int skip,
-                                             double tol, int *piv, double *sq, double *inv) {
-  const int lane = threadIdx.x & 31;
-  long long best = LLONG_MIN;
-  int bi = S;
-  for (int i = lane; i < S; i += 32) {
-    const long long v = __double_as_longlong(dg[i]);
-    if (!removed[i] && i != skip && v > best) { best = v; bi = i; }
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-  }
-  if (lane == 0) {
-    const double bv = __longlong_as_double(best);
-    const bool ok = bi < S && best > 0 && bv > tol;
-    const double y = ok ? rsqrt_nr(bv) : 0.0;
-    *piv = ok ? bi : S;
-    *inv = y;
-    *sq = bv * y;
-  }
-}
-
-// One CTA per chip.  Step k of the pivoted Cholesky: all threads form
-// column k of L from the published pivot; then warp 0 updates the Schur
-// diagonal and already searches the pivot of step k + 1 (its float64
-// latency chain) while warps 1-7 apply the rank-1 update to the strictly
-// lower part.  Two barriers per step.
-template <int S>
-__global__ void __launch_bounds__(256) factor_kernel(SmallArgs A) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  double (*W)[S + 1] = reinterpret_cast<double (*)[S + 1]>(smem);   // scaled Gram, strictly lower part used
-  double (*Lc)[S + 1] = W + S;                                      // Lc[k][row]: column k of L
-  __shared__ double d[S], dg[S], rv[S];
-  __shared__ int perm[S];
-  __shared__ int removed[S];
-  __shared__ int s_piv[2], s_bad;
-  __shared__ double s_sq[2], s_inv[2];
-  const int c = blockIdx.x;
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  ChipSolveState &st = A.state[c];
-  if (!st.active) return;
-  if (t == 0) s_bad = 0;
-  __syncthreads();
-  const double *gacc = A.gram + (long long)c * S * S;
-  for (int e = t; e < S * S; e += 256) {
-    const int a = e / S, b = e % S;
-    if (b <= a) {
-      const double v = 0.5 * (gacc[a * S + b] + gacc[b * S + a]);
-      if (!isfinite(v)) s_bad = 1;
-      W[a][b] = v;
-    }
-  }
-  // W and ||R||^2 of the previous iteration were consumed by its beta solve
-  for (int e = t; e < S * S; e += 256) A.wg[(long long)c * S * S + e] = 0.0;
-  if (t < S) A.rn2[(long long)c * S + t] = 0.0;
-  __syncthreads();
-  if (t < S) {
-    const double w = W[t][t];
-    d[t] = (w > 1e-290 && isfinite(w)) ? rsqrt_nr(w) : 0.0;
-    removed[t] = d[t] == 0.0;
-    dg[t] = w * d[t] * d[t];
-  }
-  __syncthreads();
-  for (int e = t; e < S * S; e += 256) {
-    const int a = e / S, b = e % S;
-    if (b < a) W[a][b] *= d[a] * d[b];
-  }
-  if (warp == 0) pivot_search<S>(dg, removed, -1, A.tol, &s_piv[0], &s_sq[0], &s_inv[0]);
-  __syncthreads();
-  int k = 0;
-  for (; k < S; ++k) {
-    const int buf = k & 1;
-    const int p = s_piv[buf];
-    if (p >= S) break;
-    const double sq = s_sq[buf], inv = s_inv[buf];
-    if (t < S)
-      Lc[k][t] = (removed[t] || t == p) ? (t == p ? sq : 0.0) : (t > p ? W[t][p] : W[p][t]) * inv;
-    __syncthreads();
-    if (t == 0) { removed[p] = 1; perm[k] = p; rv[k] = inv; }
-    if (warp == 0) {
-      for (int a = lane; a < S; a += 32)
-        if (!removed[a] && a != p) dg[a] -= Lc[k][a] * Lc[k][a];
-      __syncwarp();
-      pivot_search<S>(dg, removed, p, A.tol, &s_piv[buf ^ 1], &s_sq[buf ^ 1], &s_inv[buf ^ 1]);
-    } else {
-      for (int a = warp - 1; a < S; a += 7) {
-        if (removed[a] || a == p) continue;
-        const double la = Lc[k][a];
-        for (int b = lane; b < a; b += 32)
-          if (!removed[b] && b != p) W[a][b] -= la * Lc[k][b];
-      }
-    }
-    __syncthreads();
-  }
-  const int r = k;
-  // Substitution factors, pivot order, scaled by the reciprocal pivots so a
-  // substitution step is one fused multiply-add:
-  //   F[i][k] = L[i][k] / L[k][k]  (i > k, forward),
-  //   F[i][k] = L[k][i] / L[k][k]  (i < k, backward),  F[i][i] = 0.
-  double *L = A.lfac + (long long)c * S * S;
-  for (int e = t; e < S * S; e += 256) {
-    const int i = e / S, kk = e % S;
-    double v = 0.0;
-    if (i < r && kk < r && i > kk) v = Lc[kk][perm[i]] * rv[kk];
-    else if (i < r && kk < r && i < kk) v = Lc[i][perm[kk]] * rv[kk];
-    L[e] = v;
-  }
-  if (t < S) {
-    A.dsc[(long long)c * S + t] = d[t];
-    A.perm[(long long)c * S + t] = t < r ? perm[t] : -1;
-    A.rinv[(long long)c * S + t] = t < r ? rv[t] : 0.0;
-  }
-  if (t == 0) {
-    A.rank[c] = r;
-    st.rank = r;
-    st.deflated += (A.s - r) > 0 ? (A.s - r) : 0;
-    if (s_bad || r == 0) {
-      st.status = BLOCKOA_ERR_BREAKDOWN;
-      st.active = 0;
-    }
-  }
-}
-
-// Gamma_KK Z = RHS_K for four columns per CTA (one warp each); deflated rows
-// of the result are zero.  The beta solve's CTA 0 also clears Gamma and rho
-// and runs the per-column convergence test of the updated residual.
-template <typename T, int S, bool ALPHA>
-__global__ void __launch_bounds__(32) trsolve_kernel(SmallArgs A) {
-  constexpr int NSPLIT = S;
-  constexpr int RL = (S + 31) / 32;  // rows per lane
-  __shared__ double L[S][S + 1];
-  __shared__ double rinv[S], d[S];  // rinv is 0 past the rank
-  __shared__ int perm[S];
-  const int c = blockIdx.x / NSPLIT;
-  const int split = blockIdx.x % NSPLIT;
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  ChipSolveState &st = A.state[c];
-  if (!st.active) return;
-  const int r = A.rank[c];
-  const double *Lg = A.lfac + (long long)c * S * S;
-  for (int e = t; e < S * S; e += 32) L[e / S][e % S] = Lg[e];
-  for (int i = t; i < S; i += 32) {
-    rinv[i] = A.rinv[(long long)c * S + i];
-    d[i] = A.dsc[(long long)c * S + i];
-    perm[i] = A.perm[(long long)c * S + i];
-  }
-  __syncthreads();
-  const double *rhs = (ALPHA ? A.rho : A.wg) + (long long)c * S * S;
-  T *out = reinterpret_cast<T *>(ALPHA ? A.alpha : A.beta) + (long long)c * S * S;
-  const int j = split;
-  (void)warp;
-  double y[RL];
-  int pr[RL];
-#pragma unroll
-  for (int q = 0; q < RL; ++q) {
-    const int i = lane + 32 * q;
-    pr[q] = (i < r) ? perm[i] : -1;
-    y[q] = (i < r) ? d[pr[q]] * rhs[(long long)pr[q] * S + j] : 0.0;
-  }
-  // L z = y: y_i -= (L_ik / L_kk) y_k, then z = y / diag(L)
-  for (int k = 0; k < r; ++k) {
-    const double yk = __shfl_sync(0xffffffffu, y[k >> 5], k & 31);
-#pragma unroll
-    for (int q = 0; q < RL; ++q) {
-      const int i = lane + 32 * q;
-      const double f = (i > k && i < S) ? L[i < S ? i : 0][k] : 0.0;
-      y[q] -= f * yk;
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < RL; ++q) y[q] *= rinv[min(lane + 32 * q, S - 1)];
-  // L^T x = z: z_i -= (L_ki / L_kk) z_k, then x = z / diag(L)
-  for (int k = r - 1; k >= 0; --k) {
-    const double yk = __shfl_sync(0xffffffffu, y[k >> 5], k & 31);
-#pragma unroll
-    for (int q = 0; q < RL; ++q) {
-      const int i = lane + 32 * q;
-      const double f = (i < k) ? L[i][k] : 0.0;
-      y[q] -= f * yk;
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < RL; ++q) y[q] *= rinv[min(lane + 32 * q, S - 1)];
-#pragma unroll
-  for (int q = 0; q < RL; ++q) {
-    const int i = lane + 32 * q;
-    if (i < S) out[(long long)i * S + j] = T(0);
-  }
-  __syncwarp();
-#pragma unroll
-  for (int q = 0; q < RL; ++q) {
-    const int i = lane + 32 * q;
-    if (i < r) out[(long long)pr[q] * S + j] = (T)((ALPHA ? 1.0 : -1.0) * d[pr[q]] * y[q]);
-  }
-  if (ALPHA || split != 0) return;
-  for (int e = t; e < S * S; e += 32) {
-    A.gram[(long long)c * S * S + e] = 0.0;
-    A.rho[(long long)c * S * S + e] = 0.0;
-  }
-  __shared__ int s_conv, s_bad;
-  if (t == 0) { s_conv = 1; s_bad = 0; }
-  __syncthreads();
-  for (int i = t; i < S; i += 32) {
-    const double v = A.rn2[(long long)c * S + i];
-    if (!isfinite(v)) s_bad = 1;
-    if (!(v <= A.target2[(long long)c * S + i])) s_conv = 0;
-  }
-  __syncthreads();
-  if (t == 0) {
-    st.iters += 1;
-    if (s_bad) {
-      st.status = BLOCKOA_ERR_BREAKDOWN;
-      st.active = 0;
-    } else if (s_conv) {
-      st.status = BLOCKOA_OK;
-      st.active = 0;
-    } else if (st.iters >= A.maxiter) {
-      st.status = BLOCKOA_ERR_NOT_CONVERGED;
-      st.active = 0;
-    }
-  }
-}
-
 // ---------------------------------------------------------------- glue kernels
 // dst[a][j] = src[a][j] for j < s, 0 for s <= j < S (float64).
 __global__ void pad_cols_kernel(const double *__restrict__ src, double *__restrict__ dst,
@@ -824,6 +547,8 @@ __global__ void accumulate_kernel(const Unit *__restrict__ units, const int *__r
 }
 
 // ---------------------------------------------------------------- workspace
+constexpr int kLoopKernels = 5;   // launches per block-CG iteration
+
 struct SolveWS {
   int S = 0, prec = -1;
   long long n = 0;
@@ -851,7 +576,7 @@ struct SolveWS {
   int *h_active = nullptr;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t graph = nullptr;
-  cudaEvent_t tev[7] = {};      // recorded around the kernels of each chunk's first iteration
+  cudaEvent_t tev[kLoopKernels + 1] = {};   // recorded around the kernels of each chunk's first iteration
   int graph_iters = 0, graph_maxiter = -1, graph_s = -1, graph_pc = -1;
   double graph_tol = -1.0;
   std::vector<void *> allocs;
@@ -906,8 +631,8 @@ static void set_smem_limits() {
                        (int)update_smem<T, S>());
   cudaFuncSetAttribute(p_update_kernel<T, S, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pupdate_smem<T, S>());
-  cudaFuncSetAttribute(factor_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)factor_smem_bytes<S>());
+  cudaFuncSetAttribute(alpha_solve_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)factor_smem_bytes<SmallT<T>, S>());
 }
 
 // One block-CG iteration for every active chip; with `ev`, an event is
@@ -927,19 +652,17 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
       ws->units, op->d_chips, ws->state, g, (const T *)ws->P, (const T *)ws->R, (T *)ws->Q,
       ws->gram, ws->rho);
   mark(1);
-  factor_kernel<S><<<ws->n_chips, 256, factor_smem_bytes<S>(), st>>>(sa);
+  alpha_solve_kernel<T, S><<<nsolve, 256, factor_smem_bytes<SmallT<T>, S>(), st>>>(sa);
   mark(2);
-  trsolve_kernel<T, S, true><<<nsolve, 32, 0, st>>>(sa);
-  mark(3);
   update_gram_kernel<T, S, PC><<<ws->n_units, 256, update_smem<T, S>(), st>>>(
       ws->units, ws->state, (const T *)ws->alpha, (const T *)ws->P, (const T *)ws->Q,
       (T *)ws->D, (T *)ws->R, ws->wg, ws->rn2, dinv);
+  mark(3);
+  beta_solve_kernel<T, S><<<nsolve, 32, 0, st>>>(sa);
   mark(4);
-  trsolve_kernel<T, S, false><<<nsolve, 32, 0, st>>>(sa);
-  mark(5);
   p_update_kernel<T, S, PC><<<ws->n_units_tile, 256, pupdate_smem<T, S>(), st>>>(
       ws->units_tile, ws->state, (const T *)ws->beta, (const T *)ws->R, (T *)ws->P, dinv);
-  mark(6);
+  mark(5);
 }
 
 template <typename T, int S>
@@ -1033,7 +756,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       ws->graph_s != s || ws->graph_tol != tol || ws->graph_pc != pc) {
     if (ws->graph) { cudaGraphExecDestroy(ws->graph); ws->graph = nullptr; }
     cudaGraph_t graph = nullptr;
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i <= kLoopKernels; ++i)
       if (!ws->tev[i]) BLOCKOA_CUDA(cudaEventCreate(&ws->tev[i]));
     BLOCKOA_CUDA(cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < check_every; ++k)
@@ -1147,12 +870,12 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     BLOCKOA_CUDA(cudaGetLastError());
     // Inner block-CG iterations, polled every `check_every` iterations.
     for (;;) {
-      g_launches += 6LL * check_every;
-      for (int i = 0; i < 6; ++i) add_launches(op, KC_SPMM_GRAM + i, check_every);
+      g_launches += (long long)kLoopKernels * check_every;
+      for (int i = 0; i < kLoopKernels; ++i) add_launches(op, KC_SPMM_GRAM + i, check_every);
       BLOCKOA_CUDA(cudaGraphLaunch(ws->graph, st));
       BLOCKOA_CUDA(cudaMemcpyAsync(ws->h_state, ws->state, sizeof(ChipSolveState) * nc, cudaMemcpyDeviceToHost, st));
       BLOCKOA_CUDA(cudaStreamSynchronize(st));
-      for (int i = 0; i < 6; ++i) {   // live timing of this chunk's first iteration
+      for (int i = 0; i < kLoopKernels; ++i) {   // live timing of this chunk's first iteration
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, ws->tev[i], ws->tev[i + 1]) == cudaSuccess)
           add_time(op, KC_SPMM_GRAM + i, ms);

@@ -46,7 +46,7 @@ struct ChipSolveState {
 
 // Kernel classes with live event timing.
 enum KernelClass {
-  KC_SPMM_GRAM = 0, KC_FACTOR, KC_TRSOLVE_ALPHA, KC_UPDATE_GRAM, KC_TRSOLVE_BETA, KC_P_UPDATE,
+  KC_SPMM_GRAM = 0, KC_ALPHA_SOLVE, KC_UPDATE_GRAM, KC_BETA_SOLVE, KC_P_UPDATE,
   KC_RESIDUAL64, KC_COMBINE_TC, KC_SPLIT, KC_APPLY, KC_COMBINE_FP64, KC_COUNT
 };
 
