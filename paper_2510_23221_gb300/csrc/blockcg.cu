@@ -3,18 +3,21 @@
 // All s right-hand sides of a chip share its operator A and one Krylov
 // space.  One iteration, per chip:
 //   Q = A P,   Gamma = P^T Q,   rho = P^T R                 (spmm_gram)
-//   factor D Gamma D (D = diag(Gamma)^-1/2) by diagonal-pivoted Cholesky,
-//   deflate pivots <= tol, alpha = Gamma^-1 rho             (alpha_solve)
+//   deflating solve of the s x s system, alpha = Gamma^-1 rho
 //   X += P alpha,  R -= Q alpha,  W = Q^T Z,  ||R_j||^2     (update_gram)
-//   beta = -Gamma^-1 W, per-column convergence test         (beta_solve)
+//   beta = -Gamma^-1 W, per-column convergence test
 //   P = Z + P beta                                          (p_update)
 // with Z = R, or Z = diag(A)^-1 R under Jacobi preconditioning.  Deflated
-// columns get zero rows in alpha and beta (smallsolve.cuh).
+// columns get zero rows in alpha and beta.  The mixed form forms alpha and
+// beta in the last CTA per chip of spmm_gram and update_gram by sweeping
+// Gamma in double-float (smallsolve.cuh); the float64 form factors Gamma by
+// pivoted Cholesky and substitutes in kernels of their own
+// (smallsolve_chol.cuh).
 //
 // Precision.  FP64 runs the loop in float64.  MIXED runs it in float32 with
 // the Gram products folded into compensated float32 sums and reduced in
-// float64, the s x s factorisation and solves in double-float, inside
-// float64 iterative refinement on the true residual B - A X.
+// float64, the s x s solves in double-float, inside float64 iterative
+// refinement on the true residual B - A X.
 //
 // Layout.  Block vectors are [n_total][S] with S in {8, 16, 32, 64} (the
 // caller's s columns zero-padded).  A CTA processes one unit: a contiguous
@@ -30,6 +33,7 @@
 
 #include "common.cuh"
 #include "smallsolve.cuh"
+#include "smallsolve_chol.cuh"
 
 namespace blockoa {
 
@@ -247,9 +251,8 @@ constexpr size_t kRedBytes = 256 * 16 * sizeof(double);
 template <typename T, int S>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
 spmm_gram_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chips,
-                 const ChipSolveState *__restrict__ state, const T *__restrict__ g,
-                 const T *__restrict__ P, const T *__restrict__ R, T *__restrict__ Q,
-                 double *__restrict__ gram, double *__restrict__ rho) {
+                 const T *__restrict__ g, const T *__restrict__ P, const T *__restrict__ R,
+                 T *__restrict__ Q, const SmallArgs A) {
   using G = BK<T, S>;
   constexpr int V = G::V;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -258,7 +261,7 @@ spmm_gram_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chi
   T *sR = sQ + S * G::LD;
   double *red = reinterpret_cast<double *>(smem);   // reused after the tile loop
   const Unit u = units[blockIdx.x];
-  if (!state[u.chip].active) return;
+  if (!A.state[u.chip].active) return;
   const ChipDev ch = chips[u.chip];
   const int nx = ch.nx, ny = ch.ny, nz = ch.nz, nxny = nx * ny;
   const int t = threadIdx.x;
@@ -318,20 +321,22 @@ spmm_gram_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chi
     __syncthreads();
   }
   if constexpr (SPLIT) {
-    gram_flush_split<T, S>(acc, red, gram + (long long)u.chip * S * S, rho + (long long)u.chip * S * S);
+    gram_flush_split<T, S>(acc, red, A.gram + (long long)u.chip * S * S, A.rho + (long long)u.chip * S * S);
   } else {
-    gram_flush<T, S>(acc, red, gram + (long long)u.chip * S * S);
-    gram_flush<T, S>(acc + 16, red, rho + (long long)u.chip * S * S);
+    gram_flush<T, S>(acc, red, A.gram + (long long)u.chip * S * S);
+    gram_flush<T, S>(acc + 16, red, A.rho + (long long)u.chip * S * S);
+  }
+  // mixed form: the chip's last CTA sweeps Gamma and forms alpha
+  if constexpr (sizeof(T) == 4) {
+    if (last_cta_of_chip(A.ticket + u.chip, A.unit_count[u.chip])) chip_alpha<T, S>(A, u.chip);
   }
 }
 
 // X += P alpha, R -= Q alpha; W += Q^T R_new and rn2 += ||R_new_j||^2.
 template <typename T, int S, bool PC>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
-update_gram_kernel(const Unit *__restrict__ units, const ChipSolveState *__restrict__ state,
-                   const T *__restrict__ alpha, const T *__restrict__ P, const T *__restrict__ Q,
-                   T *__restrict__ X, T *__restrict__ R, double *__restrict__ wgram,
-                   double *__restrict__ rn2, const T *__restrict__ dinv) {
+update_gram_kernel(const Unit *__restrict__ units, const T *__restrict__ P, const T *__restrict__ Q,
+                   T *__restrict__ X, T *__restrict__ R, const T *__restrict__ dinv, const SmallArgs A) {
   using G = BK<T, S>;
   constexpr int V = G::V;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -341,9 +346,9 @@ update_gram_kernel(const Unit *__restrict__ units, const ChipSolveState *__restr
   T *sA = sR + S * G::LD;
   double *red = reinterpret_cast<double *>(smem);   // reused after the tile loop
   const Unit u = units[blockIdx.x];
-  if (!state[u.chip].active) return;
+  if (!A.state[u.chip].active) return;
   const int t = threadIdx.x;
-  const T *al = alpha + (long long)u.chip * S * S;
+  const T *al = reinterpret_cast<const T *>(A.alpha) + (long long)u.chip * S * S;
   for (int e = t; e < S * S; e += 256) sA[e] = al[e];
   const int j0 = (t % G::TPR) * V, cl0 = (t / G::TPR) * 4;
   const int grp = t / G::NT, w = t % G::NT;
@@ -399,7 +404,7 @@ update_gram_kernel(const Unit *__restrict__ units, const ChipSolveState *__restr
     gram_tile<T, S>(aw, sQ, sR, i0, k0, grp);
     __syncthreads();
   }
-  gram_flush<T, S>(aw, red, wgram + (long long)u.chip * S * S);
+  gram_flush<T, S>(aw, red, A.wg + (long long)u.chip * S * S);
   // column norms: threads with equal (t % TPR) own the same columns
   T *rt = reinterpret_cast<T *>(red);
 #pragma unroll
@@ -418,8 +423,12 @@ update_gram_kernel(const Unit *__restrict__ units, const ChipSolveState *__restr
         hi = s2;
       }
       sum = (double)hi + (double)lo;
-      atomicAdd(rn2 + (long long)u.chip * S + t * V + v, sum);
+      atomicAdd(A.rn2 + (long long)u.chip * S + t * V + v, sum);
     }
+  }
+  // mixed form: the chip's last CTA forms beta and tests convergence
+  if constexpr (sizeof(T) == 4) {
+    if (last_cta_of_chip(A.ticket + A.n_chips + u.chip, A.unit_count[u.chip])) chip_beta<T, S>(A, u.chip);
   }
 }
 
@@ -547,7 +556,18 @@ __global__ void accumulate_kernel(const Unit *__restrict__ units, const int *__r
 }
 
 // ---------------------------------------------------------------- workspace
-constexpr int kLoopKernels = 5;   // launches per block-CG iteration
+// Launches per block-CG iteration and their timing classes: the mixed form
+// runs the small solves in the tails of the Gram kernels, the float64 form
+// in kernels of their own.
+constexpr int kMaxLoopKernels = 5;
+template <typename T>
+constexpr int loop_kernels() { return sizeof(T) == 4 ? 3 : 5; }
+template <typename T>
+constexpr int loop_class(int i) {
+  return sizeof(T) == 4 ? (i == 0 ? KC_SPMM_GRAM : i == 1 ? KC_UPDATE_GRAM : KC_P_UPDATE)
+                        : (i == 0 ? KC_SPMM_GRAM : i == 1 ? KC_ALPHA_SOLVE : i == 2 ? KC_UPDATE_GRAM
+                                                  : i == 3 ? KC_BETA_SOLVE : KC_P_UPDATE);
+}
 
 struct SolveWS {
   int S = 0, prec = -1;
@@ -560,8 +580,10 @@ struct SolveWS {
   // per-chip small buffers
   double *gram = nullptr, *rho = nullptr, *wg = nullptr, *rn2 = nullptr, *rn64 = nullptr,
          *bn2 = nullptr, *target2 = nullptr, *sigma = nullptr, *inv_sigma = nullptr,
-         *lfac = nullptr, *dsc = nullptr, *rinv = nullptr;
+         *ginv = nullptr, *dsc = nullptr,   // small-solve arithmetic type (8 bytes)
+         *rinv = nullptr;
   int *perm = nullptr, *rank = nullptr, *outer_active = nullptr;
+  int *ticket = nullptr, *unit_count = nullptr;
   void *alpha = nullptr, *beta = nullptr;
   ChipSolveState *state = nullptr;
   Unit *units = nullptr;        // loop units
@@ -576,7 +598,7 @@ struct SolveWS {
   int *h_active = nullptr;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t graph = nullptr;
-  cudaEvent_t tev[kLoopKernels + 1] = {};   // recorded around the kernels of each chunk's first iteration
+  cudaEvent_t tev[kMaxLoopKernels + 1] = {};   // recorded around the kernels of each chunk's first iteration
   int graph_iters = 0, graph_maxiter = -1, graph_s = -1, graph_pc = -1;
   double graph_tol = -1.0;
   std::vector<void *> allocs;
@@ -608,14 +630,16 @@ static cudaError_t ws_alloc(SolveWS *ws, P **p, size_t bytes) {
   return e;
 }
 
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+template <typename T, int S>
+constexpr size_t tail_smem() { return sizeof(T) == 4 ? small_smem_bytes<dfl, S>() : 0; }
 template <typename T, int S>
 constexpr size_t spmm_smem() {
-  return 3 * tile_bytes<T, S>() > kRedBytes ? 3 * tile_bytes<T, S>() : kRedBytes;
+  return cmax(cmax(3 * tile_bytes<T, S>(), kRedBytes), tail_smem<T, S>());
 }
 template <typename T, int S>
 constexpr size_t update_smem() {
-  return 3 * tile_bytes<T, S>() + S * S * sizeof(T) > kRedBytes
-             ? 3 * tile_bytes<T, S>() + S * S * sizeof(T) : kRedBytes;
+  return cmax(cmax(3 * tile_bytes<T, S>() + S * S * sizeof(T), kRedBytes), tail_smem<T, S>());
 }
 template <typename T, int S>
 constexpr size_t pupdate_smem() { return tile_bytes<T, S>() + S * S * sizeof(T); }
@@ -631,8 +655,9 @@ static void set_smem_limits() {
                        (int)update_smem<T, S>());
   cudaFuncSetAttribute(p_update_kernel<T, S, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pupdate_smem<T, S>());
-  cudaFuncSetAttribute(alpha_solve_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)factor_smem_bytes<SmallT<T>, S>());
+  if constexpr (sizeof(T) == 8)
+    cudaFuncSetAttribute(chol_alpha_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)chol_smem_bytes<S>());
 }
 
 // One block-CG iteration for every active chip; with `ev`, an event is
@@ -642,27 +667,29 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
                              cudaStream_t st, cudaEvent_t *ev) {
   const T *g = sizeof(T) == 4 ? (const T *)op->g32 : (const T *)op->g64;
   const T *dinv = sizeof(T) == 4 ? (const T *)op->dinv32 : (const T *)op->dinv64;
-  const unsigned nsolve = (unsigned)(ws->n_chips * S);
   // external record nodes: the events carry timestamps when the graph runs
   auto mark = [&](int i) {
     if (ev) cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal);
   };
-  mark(0);
+  int m = 0;
+  mark(m++);
   spmm_gram_kernel<T, S><<<ws->n_units, 256, spmm_smem<T, S>(), st>>>(
-      ws->units, op->d_chips, ws->state, g, (const T *)ws->P, (const T *)ws->R, (T *)ws->Q,
-      ws->gram, ws->rho);
-  mark(1);
-  alpha_solve_kernel<T, S><<<nsolve, 256, factor_smem_bytes<SmallT<T>, S>(), st>>>(sa);
-  mark(2);
+      ws->units, op->d_chips, g, (const T *)ws->P, (const T *)ws->R, (T *)ws->Q, sa);
+  if constexpr (sizeof(T) == 8) {
+    mark(m++);
+    chol_alpha_kernel<S><<<ws->n_chips * S, 256, chol_smem_bytes<S>(), st>>>(sa);
+  }
+  mark(m++);
   update_gram_kernel<T, S, PC><<<ws->n_units, 256, update_smem<T, S>(), st>>>(
-      ws->units, ws->state, (const T *)ws->alpha, (const T *)ws->P, (const T *)ws->Q,
-      (T *)ws->D, (T *)ws->R, ws->wg, ws->rn2, dinv);
-  mark(3);
-  beta_solve_kernel<T, S><<<nsolve, 32, 0, st>>>(sa);
-  mark(4);
+      ws->units, (const T *)ws->P, (const T *)ws->Q, (T *)ws->D, (T *)ws->R, dinv, sa);
+  if constexpr (sizeof(T) == 8) {
+    mark(m++);
+    chol_beta_kernel<S><<<ws->n_chips * S, 32, 0, st>>>(sa);
+  }
+  mark(m++);
   p_update_kernel<T, S, PC><<<ws->n_units_tile, 256, pupdate_smem<T, S>(), st>>>(
       ws->units_tile, ws->state, (const T *)ws->beta, (const T *)ws->R, (T *)ws->P, dinv);
-  mark(5);
+  mark(m++);
 }
 
 template <typename T, int S>
@@ -690,7 +717,9 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     BLOCKOA_CUDA(ws_alloc(ws, &ws->gram, sm));
     BLOCKOA_CUDA(ws_alloc(ws, &ws->rho, sm));
     BLOCKOA_CUDA(ws_alloc(ws, &ws->wg, sm));
-    BLOCKOA_CUDA(ws_alloc(ws, &ws->lfac, sm));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->ginv, sm));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->rinv, sv));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->perm, sizeof(int) * (size_t)nc * S));
     BLOCKOA_CUDA(ws_alloc(ws, &ws->alpha, sizeof(T) * (size_t)nc * S * S));
     BLOCKOA_CUDA(ws_alloc(ws, &ws->beta, sizeof(T) * (size_t)nc * S * S));
     BLOCKOA_CUDA(ws_alloc(ws, &ws->rn2, sv));
@@ -700,8 +729,6 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     BLOCKOA_CUDA(ws_alloc(ws, &ws->sigma, sv));
     BLOCKOA_CUDA(ws_alloc(ws, &ws->inv_sigma, sv));
     BLOCKOA_CUDA(ws_alloc(ws, &ws->dsc, sv));
-    BLOCKOA_CUDA(ws_alloc(ws, &ws->rinv, sv));
-    BLOCKOA_CUDA(ws_alloc(ws, &ws->perm, sizeof(int) * (size_t)nc * S));
     BLOCKOA_CUDA(ws_alloc(ws, &ws->rank, sizeof(int) * (size_t)nc));
     BLOCKOA_CUDA(ws_alloc(ws, &ws->outer_active, sizeof(int) * (size_t)nc));
     BLOCKOA_CUDA(ws_alloc(ws, &ws->state, sizeof(ChipSolveState) * (size_t)nc));
@@ -712,6 +739,14 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     long long cells = pick_unit_cells(op, G::TC, 2 * G::TC, 3 * nsm);
     std::vector<Unit> units = make_units(op, cells);
     ws->n_units = (int)units.size();
+    {
+      std::vector<int> cnt(nc, 0);
+      for (const Unit &uu : units) cnt[uu.chip] += 1;
+      BLOCKOA_CUDA(ws_alloc(ws, &ws->unit_count, sizeof(int) * (size_t)nc));
+      BLOCKOA_CUDA(cudaMemcpy(ws->unit_count, cnt.data(), sizeof(int) * (size_t)nc, cudaMemcpyHostToDevice));
+      BLOCKOA_CUDA(ws_alloc(ws, &ws->ticket, sizeof(int) * 2 * (size_t)nc));
+      BLOCKOA_CUDA(cudaMemset(ws->ticket, 0, sizeof(int) * 2 * (size_t)nc));
+    }
     BLOCKOA_CUDA(ws_alloc(ws, &ws->units, sizeof(Unit) * units.size()));
     BLOCKOA_CUDA(cudaMemcpy(ws->units, units.data(), sizeof(Unit) * units.size(), cudaMemcpyHostToDevice));
     std::vector<Unit> ut = make_units(op, G::TC);
@@ -730,9 +765,8 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     BLOCKOA_CUDA(cudaMemset(ws->rho, 0, sm));
     BLOCKOA_CUDA(cudaMemset(ws->wg, 0, sm));
     BLOCKOA_CUDA(cudaMemset(ws->rn2, 0, sv));
-    BLOCKOA_CUDA(cudaMemset(ws->lfac, 0, sm));
+    BLOCKOA_CUDA(cudaMemset(ws->ginv, 0, sm));
     BLOCKOA_CUDA(cudaMemset(ws->rank, 0, sizeof(int) * (size_t)nc));
-    BLOCKOA_CUDA(cudaMemset(ws->perm, 0, sizeof(int) * (size_t)nc * S));
     set_smem_limits<T, S, false>();
     set_smem_limits<T, S, true>();
   }
@@ -747,8 +781,10 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
 
   SmallArgs sa;
   sa.state = ws->state; sa.gram = ws->gram; sa.rho = ws->rho; sa.wg = ws->wg; sa.rn2 = ws->rn2;
-  sa.target2 = ws->target2; sa.lfac = ws->lfac; sa.rinv = ws->rinv; sa.perm = ws->perm;
-  sa.dsc = ws->dsc; sa.rank = ws->rank; sa.alpha = ws->alpha; sa.beta = ws->beta;
+  sa.target2 = ws->target2; sa.ginv = ws->ginv; sa.dsc = ws->dsc; sa.rank = ws->rank;
+  sa.rinv = ws->rinv; sa.perm = ws->perm;
+  sa.alpha = ws->alpha; sa.beta = ws->beta;
+  sa.ticket = ws->ticket; sa.unit_count = ws->unit_count; sa.n_chips = nc;
   sa.s = s; sa.maxiter = maxiter; sa.tol = tol;
 
   // Build (or reuse) the graph of `check_every` iterations.
@@ -756,7 +792,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       ws->graph_s != s || ws->graph_tol != tol || ws->graph_pc != pc) {
     if (ws->graph) { cudaGraphExecDestroy(ws->graph); ws->graph = nullptr; }
     cudaGraph_t graph = nullptr;
-    for (int i = 0; i <= kLoopKernels; ++i)
+    for (int i = 0; i <= kMaxLoopKernels; ++i)
       if (!ws->tev[i]) BLOCKOA_CUDA(cudaEventCreate(&ws->tev[i]));
     BLOCKOA_CUDA(cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < check_every; ++k)
@@ -854,6 +890,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       BLOCKOA_CUDA(cudaMemsetAsync(ws->rho, 0, sm, st));
       BLOCKOA_CUDA(cudaMemsetAsync(ws->wg, 0, sm, st));
       BLOCKOA_CUDA(cudaMemsetAsync(ws->rn2, 0, sv, st));
+      BLOCKOA_CUDA(cudaMemsetAsync(ws->ticket, 0, sizeof(int) * 2 * (size_t)nc, st));
     }
     g_launches += 2;
     {
@@ -870,15 +907,15 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     BLOCKOA_CUDA(cudaGetLastError());
     // Inner block-CG iterations, polled every `check_every` iterations.
     for (;;) {
-      g_launches += (long long)kLoopKernels * check_every;
-      for (int i = 0; i < kLoopKernels; ++i) add_launches(op, KC_SPMM_GRAM + i, check_every);
+      g_launches += (long long)loop_kernels<T>() * check_every;
+      for (int i = 0; i < loop_kernels<T>(); ++i) add_launches(op, loop_class<T>(i), check_every);
       BLOCKOA_CUDA(cudaGraphLaunch(ws->graph, st));
       BLOCKOA_CUDA(cudaMemcpyAsync(ws->h_state, ws->state, sizeof(ChipSolveState) * nc, cudaMemcpyDeviceToHost, st));
       BLOCKOA_CUDA(cudaStreamSynchronize(st));
-      for (int i = 0; i < kLoopKernels; ++i) {   // live timing of this chunk's first iteration
+      for (int i = 0; i < loop_kernels<T>(); ++i) {   // live timing of this chunk's first iteration
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, ws->tev[i], ws->tev[i + 1]) == cudaSuccess)
-          add_time(op, KC_SPMM_GRAM + i, ms);
+          add_time(op, loop_class<T>(i), ms);
         else
           cudaGetLastError();
       }

@@ -1,30 +1,37 @@
 // Small s x s solves of the block-CG iteration (Eq. 4, Sec. III-A).
 //
-// Per chip and iteration, with D = diag(Gamma)^-1/2 (Jacobi scaling):
-//   D Gamma D = L L^T by diagonal-pivoted Cholesky, stopping at the first
-//   pivot <= tol (deflation: the remaining directions are numerically
-//   dependent on the kept ones);
-//   alpha = Gamma^+ rho and beta = -Gamma^+ W on the kept columns, by
-//   forward and backward substitution; deflated rows are zero.
+// Per chip and iteration, with D = diag(Gamma)^-1/2 (Jacobi scaling) and
+// G = D Gamma D (unit diagonal):
+//   the symmetric sweep operator (Gauss-Jordan elimination with diagonal
+//   pivoting) is applied to G pivot by pivot, always on the largest
+//   remaining Schur-complement diagonal, and stops at the first one <= tol
+//   (deflation: the remaining directions are numerically dependent on the
+//   kept set K).  The pivots and the deflation test are those of a
+//   diagonal-pivoted Cholesky factorisation; after sweeping K the kept
+//   block holds -(G_KK)^-1, so
+//   alpha = D G_KK^-1 D rho  and  beta = -D G_KK^-1 D W
+//   are plain s x s products (zero rows outside K), with no triangular
+//   substitutions and their serial chains.
+//
+// Where they run.  Each loop kernel's CTAs add their Gram partials to the
+// chip's float64 accumulators and then take a ticket; the CTA that takes a
+// chip's last ticket has every partial of that chip and solves in place: at
+// the end of the Q = A P kernel it sweeps Gamma and forms alpha
+// (chip_alpha), at the end of the update kernel it forms beta and tests
+// convergence (chip_beta).  No separate launches.  Each tail clears the
+// accumulators it consumed.
 //
 // Arithmetic.  The float64 form runs this in float64.  The mixed form runs
 // it in double-float: a value is the unevaluated sum hi + lo of two float32
-// words (about 48 significant bits), built on the error-free transforms
-// TwoSum and TwoProd.  float64 instructions issue at 1/64 of the float32
-// rate on this part, and the factorisation and substitutions are long
-// chains of dependent scalar steps, so double-float shortens them several
-// times while staying about 2^-44 accurate, far below what the float32 loop
-// resolves.
-//
-// Structure.  alpha_solve_kernel runs one CTA per (chip, column j): every
-// CTA of a chip factors the same matrix with the same instruction sequence
-// (bitwise the same factor), then solves its column of alpha.  CTA j = 0
-// publishes the substitution factors for beta_solve_kernel, which solves
-// one column of beta per single-warp CTA.
-//
-// Accumulators are cleared by the kernel that runs after their last reader:
-// alpha_solve (CTA 0) clears W and ||R||^2, read by the previous beta solve;
-// beta_solve (CTA 0) clears Gamma and rho, read by the alpha solve.
+// words (about 48 significant bits).  float64 instructions issue at 1/64 of
+// the float32 rate on this part, and a sweep is a chain of s dependent
+// steps whose latency, not its flops, sets the time.  Sums of products are
+// carried as lazy compensated accumulators (s, c): the loop-carried
+// dependency of one term is a single float32 add on s, while the rounding
+// error (TwoSum) and the low-order product terms (TwoProd by fma) collect
+// in c, as in the compensated dot product of Ogita, Rump and Oishi (SIAM J.
+// Sci. Comput. 26(6), 2005); a value is normalised only where it is
+// consumed.
 #pragma once
 
 #include <climits>
@@ -38,16 +45,20 @@ struct SmallArgs {
   ChipSolveState *state;
   double *gram;     // [chip][S][S] Gamma accumulator
   double *rho;      // [chip][S][S] rho = P^T R accumulator
-  double *wg;       // [chip][S][S] W = Q^T R accumulator
+  double *wg;       // [chip][S][S] W = Q^T Z accumulator
   double *rn2;      // [chip][S] ||R_j||^2 accumulator
   const double *target2;  // [chip][S] squared per-column targets
-  void *lfac;       // [chip][S][S] substitution factors F (small-solve arithmetic type)
-  void *rinv;       // [chip][S] 1 / L[k][k] (small-solve arithmetic type)
-  int *perm;        // [chip][S] kept columns in pivot order
-  double *dsc;      // [chip][S] scaling diagonal D
-  int *rank;        // [chip]
+  void *ginv;       // [chip][S][S] (G_KK)^-1, zero outside K (small-solve arithmetic type);
+                    //   float64 form: substitution factors F
+  void *dsc;        // [chip][S] scaling diagonal D (small-solve arithmetic type)
+  int *rank;        // [chip] |K|
+  double *rinv;     // [chip][S] float64 form: 1 / L[k][k] in pivot order
+  int *perm;        // [chip][S] float64 form: kept columns in pivot order
   void *alpha;      // [chip][S][S] in the loop's precision
   void *beta;       // [chip][S][S]
+  int *ticket;      // [2][chip] CTA completion counters of the two Gram kernels (zero between launches)
+  const int *unit_count;  // [chip] CTAs per chip of the Gram kernels
+  int n_chips;
   int s;            // caller's columns (for deflation counts)
   int maxiter;      // limit on total iterations per chip
   double tol;       // deflation threshold on scaled pivots
@@ -70,11 +81,10 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
 }
 
 // ---------------------------------------------------------------- double-float
-// A double-word value hi + lo with |lo| <= ulp(hi) / 2.  The sum and
-// product are the double-word algorithms of Joldes, Muller and Popescu
-// (ACM TOMS 44(2), 2017): the sum has relative error <= 3u^2 and the
-// product <= 5u^2, u = 2^-24.  Every operation uses the _rn intrinsics, so
-// the compiler neither contracts nor reorders them.
+// A double-word value hi + lo with |lo| <= ulp(hi) / 2.  The product is the
+// double-word product of Joldes, Muller and Popescu (ACM TOMS 44(2), 2017),
+// relative error <= 5u^2, u = 2^-24.  Every operation uses the _rn
+// intrinsics, so the compiler neither contracts nor reorders them.
 struct dfl {
   float h, l;
 };
@@ -91,12 +101,6 @@ __device__ __forceinline__ dfl fast_two_sum(float a, float b) {
   const float s = __fadd_rn(a, b);
   return {s, __fsub_rn(b, __fsub_rn(s, a))};
 }
-__device__ __forceinline__ dfl dw_add(dfl x, dfl y) {
-  const dfl s = two_sum(x.h, y.h);
-  const dfl t = two_sum(x.l, y.l);
-  const dfl v = fast_two_sum(s.h, __fadd_rn(s.l, t.h));
-  return fast_two_sum(v.h, __fadd_rn(t.l, v.l));
-}
 __device__ __forceinline__ dfl dw_mul(dfl x, dfl y) {
   const float ch = __fmul_rn(x.h, y.h);
   const float cl1 = __fmaf_rn(x.h, y.h, -ch);   // exact error of ch
@@ -104,33 +108,41 @@ __device__ __forceinline__ dfl dw_mul(dfl x, dfl y) {
   return fast_two_sum(ch, __fadd_rn(cl1, cl2));
 }
 
+// Lazy compensated accumulator: the value is s + c.
+struct acc2 {
+  float s, c;
+};
+
 // The small-solve arithmetic: native float64, or double-float.
 template <typename R>
 struct SmallMath;
 
 template <>
 struct SmallMath<double> {
+  using Acc = double;
   static __device__ __forceinline__ double zero() { return 0.0; }
   static __device__ __forceinline__ double from64(double x) { return x; }
   static __device__ __forceinline__ double to64(double x) { return x; }
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-  // acc - a b
-  static __device__ __forceinline__ double fms(double acc, double a, double b) {
-    return __fma_rn(-a, b, acc);
-  }
   static __device__ __forceinline__ double rsqrt(double x) { return rsqrt_nr(x); }
-  static __device__ __forceinline__ bool positive(double x) { return x > 0.0; }
+  static __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+  static __device__ __forceinline__ double neg(double x) { return -x; }
   static __device__ __forceinline__ bool greater(double x, double y) { return x > y; }
   // Order-preserving bits of a positive value (sign, exponent, 20 mantissa bits).
   static __device__ __forceinline__ unsigned order_bits(double x) { return (unsigned)__double2hiint(x); }
   static __device__ __forceinline__ double shfl(double x, int src) {
     return __shfl_sync(0xffffffffu, x, src);
   }
+  static __device__ __forceinline__ Acc acc(double v) { return v; }
+  static __device__ __forceinline__ double value(Acc x) { return x; }
+  // x -= a b
+  static __device__ __forceinline__ void fms(Acc &x, double a, double b) { x = __fma_rn(-a, b, x); }
   static constexpr bool kScaled = false;   // no range normalisation needed
 };
 
 template <>
 struct SmallMath<dfl> {
+  using Acc = acc2;
   static __device__ __forceinline__ dfl zero() { return {0.f, 0.f}; }
   static __device__ __forceinline__ dfl from64(double x) {
     const float h = __double2float_rn(x);
@@ -138,27 +150,48 @@ struct SmallMath<dfl> {
   }
   static __device__ __forceinline__ double to64(dfl x) { return (double)x.h + (double)x.l; }
   static __device__ __forceinline__ dfl mul(dfl a, dfl b) { return dw_mul(a, b); }
-  static __device__ __forceinline__ dfl fms(dfl acc, dfl a, dfl b) {
-    const dfl p = dw_mul(a, b);
-    return dw_add(acc, dfl{-p.h, -p.l});
-  }
-  // Newton step on a float32 seed: y1 = y0 + y0 (1 - x y0^2) / 2 with the
-  // residual 1 - x y0^2 in double-word (y0^2 is exact as a TwoProd), so the
-  // seed's ~2^-23 error becomes ~2^-44.
+  // Newton step on a float32 seed y0: y1 = y0 + y0 e / 2 with the residual
+  // e = 1 - x y0^2 formed to double-word accuracy: x.h y0 = p + pe exactly
+  // (TwoProd), so e = (1 - p y0) - (pe + x.l y0) y0, where the first fma is
+  // exact up to its final rounding (p y0 is near 1).  The seed's ~2^-23
+  // error becomes ~2^-44.
   static __device__ __forceinline__ dfl rsqrt(dfl x) {
     const float y0 = rsqrtf(x.h);
-    const float q = __fmul_rn(y0, y0);
-    const dfl xq = dw_mul(x, dfl{q, __fmaf_rn(y0, y0, -q)});
-    const dfl e = dw_add(dfl{1.f, 0.f}, dfl{-xq.h, -xq.l});
-    return fast_two_sum(y0, __fmul_rn(__fmul_rn(0.5f, y0), e.h));
+    const float p = __fmul_rn(x.h, y0);
+    const float pe = __fmaf_rn(x.h, y0, -p);
+    const float lo = __fmaf_rn(x.l, y0, pe);
+    const float e = __fmaf_rn(-lo, y0, __fmaf_rn(-p, y0, 1.f));
+    return fast_two_sum(y0, __fmul_rn(__fmul_rn(0.5f, y0), e));
   }
-  static __device__ __forceinline__ bool positive(dfl x) { return x.h > 0.f; }
+  // Newton step on the float32 reciprocal y0: y1 = y0 + y0 e with
+  // e = 1 - x y0 = (1 - p) - (pe + x.l y0), x.h y0 = p + pe exactly; 1 - p
+  // is exact (p is near 1).  About 2^-46 relative error.
+  static __device__ __forceinline__ dfl rcp(dfl x) {
+    const float y0 = __frcp_rn(x.h);
+    const float p = __fmul_rn(x.h, y0);
+    const float pe = __fmaf_rn(x.h, y0, -p);
+    const float e = __fsub_rn(__fsub_rn(1.f, p), __fmaf_rn(x.l, y0, pe));
+    return fast_two_sum(y0, __fmul_rn(y0, e));
+  }
+  static __device__ __forceinline__ dfl neg(dfl x) { return {-x.h, -x.l}; }
   static __device__ __forceinline__ bool greater(dfl x, dfl y) {
     return x.h > y.h || (x.h == y.h && x.l > y.l);
   }
   static __device__ __forceinline__ unsigned order_bits(dfl x) { return __float_as_uint(x.h); }
   static __device__ __forceinline__ dfl shfl(dfl x, int src) {
     return {__shfl_sync(0xffffffffu, x.h, src), __shfl_sync(0xffffffffu, x.l, src)};
+  }
+  static __device__ __forceinline__ Acc acc(dfl v) { return {v.h, v.l}; }
+  static __device__ __forceinline__ dfl value(Acc x) { return two_sum(x.s, x.c); }
+  // x -= a b: the high product joins s through TwoSum, its exact error and
+  // the cross terms join c.
+  static __device__ __forceinline__ void fms(Acc &x, dfl a, dfl b) {
+    const float ph = __fmul_rn(a.h, b.h);
+    const float pe = __fmaf_rn(a.h, b.h, -ph);
+    const float pl = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, pe));
+    const dfl t = two_sum(x.s, -ph);
+    x.s = t.h;
+    x.c = __fadd_rn(x.c, __fsub_rn(t.l, pl));
   }
   static constexpr bool kScaled = true;    // float32 exponent range: normalise columns
 };
@@ -168,330 +201,324 @@ template <typename T>
 using SmallT = typename std::conditional<sizeof(T) == 4, dfl, double>::type;
 
 template <typename R, int S>
-struct FactorSmem {
-  R W[S][S + 1];   // scaled Gram (strict lower part); then F in pivot order
-  R Lc[S][S];      // Lc[k][a]: column k of L, rows in the original order
-  R rv[S];         // 1 / L[k][k], pivot order
-  R sq[2], inv[2]; // published pivot: square root and reciprocal square root
-  double d[S];     // D
-  int perm[S];     // pivot order
-  int removed[S];
-  int piv[2];
+struct SweepSmem {
+  R Gi[S][S + 1];   // (G_KK)^-1 on K x K, zero elsewhere
+  R B[S][S + 1];    // right-hand sides, scaled: D rhs 2^-ex
+  R C[2][S];        // published pivot column, by step parity
+  R dR[S];          // D
+  int ex[S];        // per-column exponent of the right-hand sides
+  int sw[S];        // swept (kept) flags
   int bad;
+  int rank;
 };
 template <typename R, int S>
-constexpr size_t factor_smem_bytes() { return sizeof(FactorSmem<R, S>); }
+constexpr size_t small_smem_bytes() { return sizeof(SweepSmem<R, S>); }
 
-// Pivot search over the Schur diagonal held by warp 0 (rows lane + 32 q):
-// the largest value, as a 32-bit key of its order-preserving high bits with
-// the low 6 bits replaced by 63 - index, reduced in one instruction.  The
-// choice is exact up to a relative 2^-14 (float64) or 2^-17 (double-float)
-// among near-equal pivots, lower index first; any such choice keeps the
-// pivoted factorisation stable.  Lane 0 publishes the pivot or S when the
-// largest value is <= tol.
+// True in the CTA that finishes last among the `count` CTAs of a chip.  Every
+// thread fences its own accumulator updates, then one thread takes a ticket;
+// the last CTA resets the counter for the next launch and fences again
+// before it reads the accumulators.
+__device__ __forceinline__ bool last_cta_of_chip(int *ticket, int count) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int prev = atomicAdd(ticket, 1);
+    s_last = prev == count - 1;
+    if (s_last) *ticket = 0;
+  }
+  __syncthreads();
+  const bool last = s_last != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+// Unbiased exponent of a nonzero float64 (subnormals report -1023).
+__device__ __forceinline__ int exponent64(double v) {
+  return (int)((__double_as_longlong(v) >> 52) & 0x7ff) - 1023;
+}
+
+// x 2^ex in the loop's precision.
+template <typename T, typename R>
+__device__ __forceinline__ T scaled_out(R x, int ex);
+template <>
+__device__ __forceinline__ float scaled_out<float, dfl>(dfl x, int ex) {
+  return ldexpf(__fadd_rn(x.h, x.l), ex);
+}
+template <>
+__device__ __forceinline__ double scaled_out<double, double>(double x, int ex) {
+  return ex == 0 ? x : x * pow2(ex);
+}
+
+// out = sign D (G_KK)^-1 D rhs for one chip (all S columns), with
+// sh.Gi and sh.dR in place.  256 threads: thread t forms the entries
+// (i, j = t % S) for rows i = t / S + (256 / S) m, each an S-term lazy
+// compensated dot product.  The right-hand side (float64) is first
+// normalised per column by an exact power of two, since double-float has
+// float32's exponent range.
+template <typename T, typename R, int S>
+__device__ __forceinline__ void gram_apply(SweepSmem<R, S> &sh, const double *rhs, bool negate, T *out) {
+  using M = SmallMath<R>;
+  using Acc = typename M::Acc;
+  constexpr int RS = 256 / S < S ? 256 / S : S;            // row stride
+  constexpr int OPT = (S + RS - 1) / RS;                   // outputs per thread
+  const int t = threadIdx.x;
+  if (t < S) sh.ex[t] = M::kScaled ? INT_MIN : 0;
+  __syncthreads();
+  if (M::kScaled) {
+    for (int e = t; e < S * S; e += 256) {
+      const double v = __ldcg(rhs + e);
+      if (v != 0.0) atomicMax(&sh.ex[e % S], exponent64(v));
+    }
+    __syncthreads();
+    if (t < S) {
+      const int x = sh.ex[t];
+      sh.ex[t] = x == INT_MIN ? 0 : (x < -1000 ? -1000 : (x > 1000 ? 1000 : x));
+    }
+    __syncthreads();
+  }
+  for (int e = t; e < S * S; e += 256) {
+    const int k = e / S, j = e % S;
+    const double v = __ldcg(rhs + e) * (M::kScaled ? pow2(-sh.ex[j]) : 1.0);
+    sh.B[k][j] = M::mul(sh.dR[k], M::from64(v));
+  }
+  __syncthreads();
+  const int j = t % S, i0 = t / S;
+  if (i0 >= RS) return;
+  Acc acc[OPT];
+#pragma unroll
+  for (int m = 0; m < OPT; ++m) acc[m] = M::acc(M::zero());
+  // i0 < RS and RS * OPT == S for S in {8, 16, 32, 64}: every row below is
+  // in range, so the chains carry no guards and interleave freely
+  static_assert(RS * OPT == S, "row split");
+  for (int k = 0; k < S; ++k) {
+    const R b = sh.B[k][j];
+#pragma unroll
+    for (int m = 0; m < OPT; ++m) M::fms(acc[m], sh.Gi[i0 + RS * m][k], b);   // accumulates -sum
+  }
+#pragma unroll
+  for (int m = 0; m < OPT; ++m) {
+    const int i = i0 + RS * m;
+    R x = M::mul(sh.dR[i], M::value(acc[m]));
+    if (!negate) x = M::neg(x);
+    out[(long long)i * S + j] = scaled_out<T, R>(x, sh.ex[j]);
+  }
+}
+
+// Pivot search over the Schur-complement diagonal (rows lane + 32 q of the
+// calling warp).  Every lane first evaluates the reciprocal of its own
+// candidates, off the serial path; then the largest candidate above tol
+// wins a single 32-bit max-reduction over keys made of its
+// order-preserving high bits with the low 6 bits replaced by 63 - index
+// (exact up to a relative 2^-14 in float64, 2^-17 in double-float among
+// near-equal pivots, lower index first -- any such choice keeps the
+// pivoted elimination stable).  Returns the pivot (S: none), its value and
+// its reciprocal in every lane.  Warps holding bitwise equal diagonals get
+// bitwise equal results.
 template <typename R, int S>
-__device__ __forceinline__ void find_pivot(const R *dg, const int *gone, R tol, FactorSmem<R, S> &sh,
-                                           int slot) {
+__device__ __forceinline__ int find_pivot(const typename SmallMath<R>::Acc *dg, const int *alive, R tol,
+                                          R &a, R &inva) {
   using M = SmallMath<R>;
   constexpr int RL = (S + 31) / 32;
   const int lane = threadIdx.x & 31;
   unsigned key = 0;
+  R cv[RL], ci[RL];
 #pragma unroll
   for (int q = 0; q < RL; ++q) {
-    const int a = lane + 32 * q;
-    if (a < S && !gone[q] && M::positive(dg[q])) {
-      const unsigned kq = (M::order_bits(dg[q]) & ~63u) | (unsigned)(63 - a);
-      key = kq > key ? kq : key;
-    }
+    const int i = lane + 32 * q;
+    cv[q] = M::value(dg[q]);
+    const bool ok = alive[q] && M::greater(cv[q], tol);
+    const R rc = M::rcp(cv[q]);   // evaluated unconditionally: selects, not branches
+    ci[q] = ok ? rc : M::zero();
+    const unsigned kq = (M::order_bits(cv[q]) & ~63u) | (unsigned)(63 - i);
+    key = (ok && kq > key) ? kq : key;
   }
   key = __reduce_max_sync(0xffffffffu, key);
   const int p = key ? 63 - (int)(key & 63u) : S;
-  R v = M::zero();
-  if (p < S) {
-    R mine = dg[0];
+  R mv = cv[0], mi = ci[0];
 #pragma unroll
-    for (int q = 1; q < RL; ++q)
-      if ((p >> 5) == q) mine = dg[q];
-    v = M::shfl(mine, p & 31);
-  }
-  if (lane == 0) {
-    const bool ok = p < S && M::greater(v, tol);
-    const R y = ok ? M::rsqrt(v) : M::zero();
-    sh.piv[slot] = ok ? p : S;
-    sh.inv[slot] = y;
-    sh.sq[slot] = ok ? M::mul(v, y) : M::zero();
-  }
+  for (int q = 1; q < RL; ++q)
+    if ((p >> 5) == q) { mv = cv[q]; mi = ci[q]; }
+  a = M::shfl(mv, p & 31);
+  inva = M::shfl(mi, p & 31);
+  return p;
 }
 
-// Solve column j of Gamma_KK x = rhs_K (kept set K) with the pivot-order
-// substitution factors F (F[i][k] = L[i][k] / L[k][k] below the diagonal,
-// L[k][i] / L[k][k] above, zero on it) and write sign * D x into column j of
-// out (zero rows for deflated columns).  One warp; lane i holds rows i + 32 q.
-template <typename T, typename R, int S, int LDF>
-__device__ __forceinline__ void solve_column(const R *F, const R *rv, const double *d, const int *perm,
-                                             int r, const double *rhs, int j, double sign, T *out) {
-  using M = SmallMath<R>;
-  constexpr int RL = (S + 31) / 32;
-  const int lane = threadIdx.x & 31;
-  double y64[RL];
-  int pr[RL];
-  int ex = INT_MIN;
-#pragma unroll
-  for (int q = 0; q < RL; ++q) {
-    const int i = lane + 32 * q;
-    pr[q] = i < r ? perm[i] : -1;
-    y64[q] = i < r ? d[pr[q]] * rhs[(long long)pr[q] * S + j] : 0.0;
-    if (y64[q] != 0.0) {
-      const int e = (int)((__double_as_longlong(y64[q]) >> 52) & 0x7ff) - 1023;
-      ex = e > ex ? e : ex;
-    }
-  }
-  // double-float has float32's exponent range: bring the column's largest
-  // entry to [1, 2) by an exact power of two, undone at the end
-  if (M::kScaled) {
-    ex = __reduce_max_sync(0xffffffffu, ex);
-    ex = ex == INT_MIN ? 0 : (ex < -1000 ? -1000 : (ex > 1000 ? 1000 : ex));
-  } else {
-    ex = 0;
-  }
-  const double up = pow2(ex), down = pow2(-ex);
-  R y[RL];
-#pragma unroll
-  for (int q = 0; q < RL; ++q) y[q] = M::from64(y64[q] * down);
-  // L z = y: y_i -= F[i][k] y_k (i > k), then z_i = y_i / L[i][i]
-  for (int k = 0; k < r; ++k) {
-    R mine = y[0];
-#pragma unroll
-    for (int q = 1; q < RL; ++q)
-      if ((k >> 5) == q) mine = y[q];
-    const R yk = M::shfl(mine, k & 31);
-#pragma unroll
-    for (int q = 0; q < RL; ++q) {
-      const int i = lane + 32 * q;
-      if (i > k && i < r) y[q] = M::fms(y[q], F[i * LDF + k], yk);
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < RL; ++q) {
-    const int i = lane + 32 * q;
-    if (i < r) y[q] = M::mul(y[q], rv[i]);
-  }
-  // L^T x = z: z_i -= F[i][k] z_k (i < k), then x_i = z_i / L[i][i]
-  for (int k = r - 1; k >= 0; --k) {
-    R mine = y[0];
-#pragma unroll
-    for (int q = 1; q < RL; ++q)
-      if ((k >> 5) == q) mine = y[q];
-    const R yk = M::shfl(mine, k & 31);
-#pragma unroll
-    for (int q = 0; q < RL; ++q) {
-      const int i = lane + 32 * q;
-      if (i < k) y[q] = M::fms(y[q], F[i * LDF + k], yk);
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < RL; ++q) {
-    const int i = lane + 32 * q;
-    if (i < r) y[q] = M::mul(y[q], rv[i]);
-  }
-#pragma unroll
-  for (int q = 0; q < RL; ++q) {
-    const int i = lane + 32 * q;
-    if (i < S) out[(long long)i * S + j] = T(0);
-  }
-  __syncwarp();
-#pragma unroll
-  for (int q = 0; q < RL; ++q) {
-    const int i = lane + 32 * q;
-    if (i < r) out[(long long)pr[q] * S + j] = (T)(sign * d[pr[q]] * (M::to64(y[q]) * up));
-  }
-}
-
-// alpha = Gamma^+ rho, column j = blockIdx.x % S of chip blockIdx.x / S.
-// Step k of the factorisation: threads a < S form column k of L from the
-// published pivot; then warp 0 updates the Schur diagonal and searches the
-// next pivot while warps 1-7 apply the rank-1 update to the strict lower
-// part (fixed entries per thread; rows and columns already pivoted receive
-// zero updates, the pivot's own row is never read again).  Two barriers
-// per step.
+// Sweep Gamma of chip c and form alpha.  256 threads; the kernel's dynamic
+// shared memory holds SweepSmem.  Warp w keeps the column slab
+// j in [w NC, w NC + NC) of G in registers (lane = row, lazy accumulators),
+// and every warp keeps its own bitwise-identical copy of the diagonal, so
+// all warps find the same pivot without communication.  Step k, pivot p,
+// a = G[p][p], c = column p before the step:
+//   G[i][j] -= c_i c_j / a (i, j != p),  G[i][p] = c_i / a,  G[p][j] = c_j / a,
+//   G[p][p] = -1 / a.
+// The warp owning column p publishes c; one barrier per step; then every
+// warp updates its slab and diagonal copy and searches the next pivot.
 template <typename T, int S>
-__global__ void __launch_bounds__(256) alpha_solve_kernel(SmallArgs A) {
+__device__ __noinline__ void chip_alpha(const SmallArgs &A, int c) {
   using R = SmallT<T>;
   using M = SmallMath<R>;
-  constexpr int RL = (S + 31) / 32;
-  constexpr int NE = S * (S - 1) / 2;          // strict lower entries
-  constexpr int NEPT = (NE + 223) / 224;       // per thread of warps 1-7
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  FactorSmem<R, S> &sh = *reinterpret_cast<FactorSmem<R, S> *>(smem_raw);
-  const int c = blockIdx.x / S, j = blockIdx.x % S;
+  using Acc = typename M::Acc;
+  constexpr int RL = (S + 31) / 32;            // rows per lane
+  constexpr int NC = S / 8;                    // slab columns per warp
+  extern __shared__ __align__(16) unsigned char small_smem[];
+  SweepSmem<R, S> &sh = *reinterpret_cast<SweepSmem<R, S> *>(small_smem);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   ChipSolveState &st = A.state[c];
-  if (!st.active) return;
-  const double *g = A.gram + (long long)c * S * S;
+  double *g = A.gram + (long long)c * S * S;
   if (t == 0) sh.bad = 0;
   if (t < S) {
-    const double w = g[t * S + t];
-    const double dd = (w > 1e-290 && isfinite(w)) ? rsqrt_nr(w) : 0.0;
-    sh.d[t] = dd;
-    sh.removed[t] = dd == 0.0;
-  }
-  if (j == 0) {   // W and ||R||^2 of the previous iteration were read by its beta solve
-    for (int e = t; e < S * S; e += 256) A.wg[(long long)c * S * S + e] = 0.0;
-    if (t < S) A.rn2[(long long)c * S + t] = 0.0;
+    const double w = __ldcg(g + t * S + t);
+    sh.dR[t] = (w > 1e-290 && isfinite(w)) ? M::rsqrt(M::from64(w)) : M::zero();
+    sh.sw[t] = 0;
   }
   __syncthreads();
-  for (int e = t; e < S * S; e += 256) {
-    const int a = e / S, b = e % S;
-    if (b <= a) {
-      const double v = 0.5 * (g[a * S + b] + g[b * S + a]);
-      if (!isfinite(v)) sh.bad = 1;
-      if (b < a) sh.W[a][b] = M::from64(v * sh.d[a] * sh.d[b]);
+  // the lower triangle defines the (exactly symmetric) matrix
+  Acc W[RL][NC], dg[RL];
+  int alive[RL];
+  int bad = 0;
+#pragma unroll
+  for (int q = 0; q < RL; ++q) {
+    const int i = lane + 32 * q;
+    const int ic = i < S ? i : 0;
+    const R di = sh.dR[ic];
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) {
+      const int j = warp * NC + cc;
+      double v = 0.0;
+      if (i < S) {
+        v = __ldcg(g + (i > j ? i : j) * S + (i > j ? j : i));
+        bad |= !isfinite(v);
+      }
+      W[q][cc] = M::acc(M::mul(M::mul(M::from64(v), di), sh.dR[j]));
     }
+    const double vd = i < S ? __ldcg(g + i * S + i) : 0.0;
+    dg[q] = M::acc(M::mul(M::mul(M::from64(vd), di), di));   // bitwise equal to W[i][i]
+    alive[q] = i < S && M::greater(di, M::zero());
   }
-  // warp 0: the Schur diagonal; warps 1-7: their fixed strict-lower entries
-  R dg[RL];
-  int gone[RL];
+  if (bad) sh.bad = 1;
+  __syncthreads();
+  for (int e = t; e < S * S; e += 256) g[e] = 0.0;   // Gamma is consumed
   const R tolR = M::from64(A.tol);
-  if (warp == 0) {
-#pragma unroll
-    for (int q = 0; q < RL; ++q) {
-      const int a = lane + 32 * q;
-      gone[q] = a >= S || sh.removed[a];
-      const double da = a < S ? sh.d[a] : 0.0;
-      dg[q] = gone[q] ? M::zero() : M::from64(g[a * S + a] * da * da);
-    }
-  }
-  int ea[NEPT], eb[NEPT];
-#pragma unroll
-  for (int m = 0; m < NEPT; ++m) {
-    const int e = (t - 32) + 224 * m;
-    int a = 0, b = 0;
-    if (warp > 0 && e < NE) {
-      a = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)e)) * 0.5f);
-      while (a * (a - 1) / 2 > e) --a;
-      while ((a + 1) * a / 2 <= e) ++a;
-      b = e - a * (a - 1) / 2;
-    }
-    ea[m] = (warp > 0 && e < NE) ? a : -1;
-    eb[m] = b;
-  }
-  __syncthreads();
-  if (warp == 0) find_pivot<R, S>(dg, gone, tolR, sh, 0);
-  __syncthreads();
+  R a, inva;
+  int p = sh.bad ? S : find_pivot<R, S>(dg, alive, tolR, a, inva);
   int k = 0;
-  for (; k < S; ++k) {
-    const int p = sh.piv[k & 1];
-    if (p >= S || sh.bad) break;
-    if (t < S) {
-      R l = M::zero();
-      if (t == p) l = sh.sq[k & 1];
-      else if (!sh.removed[t]) l = M::mul(t > p ? sh.W[t][p] : sh.W[p][t], sh.inv[k & 1]);
-      sh.Lc[k][t] = l;
-    }
-    __syncthreads();
-    if (warp == 0) {
+  for (; k < S && p < S; ++k) {
+    const int buf = k & 1;
+    if (warp == p / NC) {   // owner of column p publishes it
+      const int co = p % NC;
 #pragma unroll
       for (int q = 0; q < RL; ++q) {
-        const int a = lane + 32 * q;
-        if (a == p) gone[q] = 1;
-        else if (!gone[q]) dg[q] = M::fms(dg[q], sh.Lc[k][a], sh.Lc[k][a]);
-      }
-      if (lane == 0) {
-        sh.removed[p] = 1;
-        sh.perm[k] = p;
-        sh.rv[k] = sh.inv[k & 1];
-      }
-      find_pivot<R, S>(dg, gone, tolR, sh, (k + 1) & 1);
-    } else {
+        const int i = lane + 32 * q;
+        if (S < 32 && i >= S) continue;
+        Acc wv = W[q][0];
 #pragma unroll
-      for (int m = 0; m < NEPT; ++m)
-        if (ea[m] >= 0) sh.W[ea[m]][eb[m]] = M::fms(sh.W[ea[m]][eb[m]], sh.Lc[k][ea[m]], sh.Lc[k][eb[m]]);
+        for (int cc = 1; cc < NC; ++cc)
+          if (cc == co) wv = W[q][cc];
+        sh.C[buf][i] = M::value(wv);
+      }
+      if (lane == 0) sh.sw[p] = 1;
     }
     __syncthreads();
-  }
-  const int r = sh.bad ? 0 : k;
-  // substitution factors in pivot order, over W (dead after the loop)
-  for (int e = t; e < S * S; e += 256) {
-    const int i = e / S, kk = e % S;
-    R v = M::zero();
-    if (i < r && kk < r) {
-      if (i > kk) v = M::mul(sh.Lc[kk][sh.perm[i]], sh.rv[kk]);
-      else if (i < kk) v = M::mul(sh.Lc[i][sh.perm[kk]], sh.rv[kk]);
+    R cjs[NC];
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) cjs[cc] = M::mul(sh.C[buf][warp * NC + cc], inva);
+#pragma unroll
+    for (int q = 0; q < RL; ++q) {
+      const int i = lane + 32 * q;
+      if (S < 32 && i >= S) continue;   // compile-time for S >= 32
+      const R ci = sh.C[buf][i];
+      const R cis = M::mul(ci, inva);
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc) {
+        const int j = warp * NC + cc;
+        Acc u = W[q][cc];
+        M::fms(u, ci, cjs[cc]);
+        const R spec = j == p ? (i == p ? M::neg(inva) : cis) : cjs[cc];
+        W[q][cc] = (i == p || j == p) ? M::acc(spec) : u;
+      }
+      Acc nd = dg[q];
+      M::fms(nd, ci, cis);
+      const bool keep = alive[q] && i != p;
+      dg[q] = keep ? nd : dg[q];
+      alive[q] = keep;
     }
-    sh.W[i][kk] = v;
+    p = find_pivot<R, S>(dg, alive, tolR, a, inva);
   }
   __syncthreads();
-  if (j == 0) {   // publish the factor for the beta solve, update the chip state
-    R *F = reinterpret_cast<R *>(A.lfac) + (long long)c * S * S;
-    for (int e = t; e < S * S; e += 256) F[e] = sh.W[e / S][e % S];
-    if (t < S) {
-      reinterpret_cast<R *>(A.rinv)[(long long)c * S + t] = t < r ? sh.rv[t] : M::zero();
-      A.dsc[(long long)c * S + t] = sh.d[t];
-      A.perm[(long long)c * S + t] = t < r ? sh.perm[t] : -1;
-    }
-    if (t == 0) {
-      A.rank[c] = r;
-      st.rank = r;
-      st.deflated += (A.s - r) > 0 ? (A.s - r) : 0;
-      if (r == 0) {
-        st.status = BLOCKOA_ERR_BREAKDOWN;
-        st.active = 0;
-      }
+  const int r = sh.bad ? 0 : k;
+  // (G_KK)^-1 = -(swept block), zero outside K x K
+#pragma unroll
+  for (int q = 0; q < RL; ++q) {
+    const int i = lane + 32 * q;
+    if (S < 32 && i >= S) continue;
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) {
+      const int j = warp * NC + cc;
+      sh.Gi[i][j] = (r > 0 && sh.sw[i] && sh.sw[j]) ? M::neg(M::value(W[q][cc])) : M::zero();
     }
   }
-  if (r == 0 || warp != 0) return;
-  solve_column<T, R, S, S + 1>(&sh.W[0][0], sh.rv, sh.d, sh.perm, r, A.rho + (long long)c * S * S, j, 1.0,
-                               reinterpret_cast<T *>(A.alpha) + (long long)c * S * S);
-}
-
-// beta = -Gamma^+ W, column j; CTA 0 of each chip also clears Gamma and rho
-// and runs the per-column convergence test of the updated residual.
-template <typename T, int S>
-__global__ void __launch_bounds__(32) beta_solve_kernel(SmallArgs A) {
-  using R = SmallT<T>;
-  __shared__ R F[S][S + 1];
-  __shared__ R rv[S];
-  __shared__ double d[S];
-  __shared__ int perm[S];
-  const int c = blockIdx.x / S, j = blockIdx.x % S;
-  const int t = threadIdx.x;
-  ChipSolveState &st = A.state[c];
-  if (!st.active) return;
-  const int r = A.rank[c];
-  const R *Fg = reinterpret_cast<const R *>(A.lfac) + (long long)c * S * S;
-  for (int e = t; e < S * S; e += 32) F[e / S][e % S] = Fg[e];
-  for (int i = t; i < S; i += 32) {
-    rv[i] = reinterpret_cast<const R *>(A.rinv)[(long long)c * S + i];
-    d[i] = A.dsc[(long long)c * S + i];
-    perm[i] = A.perm[(long long)c * S + i];
-  }
-  __syncwarp();
-  solve_column<T, R, S, S + 1>(&F[0][0], rv, d, perm, r, A.wg + (long long)c * S * S, j, -1.0,
-                               reinterpret_cast<T *>(A.beta) + (long long)c * S * S);
-  if (j != 0) return;
-  for (int e = t; e < S * S; e += 32) {
-    A.gram[(long long)c * S * S + e] = 0.0;
-    A.rho[(long long)c * S * S + e] = 0.0;
-  }
-  int conv = 1, bad = 0;
-  for (int i = t; i < S; i += 32) {
-    const double v = A.rn2[(long long)c * S + i];
-    if (!isfinite(v)) bad = 1;
-    if (!(v <= A.target2[(long long)c * S + i])) conv = 0;
-  }
-  conv = __all_sync(0xffffffffu, conv);
-  bad = __any_sync(0xffffffffu, bad);
+  __syncthreads();
+  // publish (G_KK)^-1 and D for the beta solve, update the chip state
+  R *Gg = reinterpret_cast<R *>(A.ginv) + (long long)c * S * S;
+  for (int e = t; e < S * S; e += 256) Gg[e] = sh.Gi[e / S][e % S];
+  if (t < S) reinterpret_cast<R *>(A.dsc)[(long long)c * S + t] = sh.dR[t];
   if (t == 0) {
-    st.iters += 1;
-    if (bad) {
+    A.rank[c] = r;
+    st.rank = r;
+    st.deflated += (A.s - r) > 0 ? (A.s - r) : 0;
+    if (r == 0) {
       st.status = BLOCKOA_ERR_BREAKDOWN;
       st.active = 0;
-    } else if (conv) {
-      st.status = BLOCKOA_OK;
-      st.active = 0;
-    } else if (st.iters >= A.maxiter) {
-      st.status = BLOCKOA_ERR_NOT_CONVERGED;
-      st.active = 0;
+    }
+  }
+  double *rho = A.rho + (long long)c * S * S;
+  if (r > 0) gram_apply<T, R, S>(sh, rho, false, reinterpret_cast<T *>(A.alpha) + (long long)c * S * S);
+  __syncthreads();
+  for (int e = t; e < S * S; e += 256) rho[e] = 0.0;   // rho is consumed
+}
+
+// Form beta = -D (G_KK)^-1 D W for chip c from the published inverse, test
+// per-column convergence of the updated residual, and clear W and ||R||^2.
+// 256 threads; the kernel's dynamic shared memory holds SweepSmem.
+template <typename T, int S>
+__device__ __noinline__ void chip_beta(const SmallArgs &A, int c) {
+  using R = SmallT<T>;
+  extern __shared__ __align__(16) unsigned char small_smem[];
+  SweepSmem<R, S> &sh = *reinterpret_cast<SweepSmem<R, S> *>(small_smem);
+  const int t = threadIdx.x, warp = t >> 5;
+  ChipSolveState &st = A.state[c];
+  const R *Gg = reinterpret_cast<const R *>(A.ginv) + (long long)c * S * S;
+  for (int e = t; e < S * S; e += 256) sh.Gi[e / S][e % S] = Gg[e];
+  if (t < S) sh.dR[t] = reinterpret_cast<const R *>(A.dsc)[(long long)c * S + t];
+  if (t == 0) sh.rank = A.rank[c];
+  __syncthreads();
+  double *wg = A.wg + (long long)c * S * S;
+  if (sh.rank > 0) gram_apply<T, R, S>(sh, wg, true, reinterpret_cast<T *>(A.beta) + (long long)c * S * S);
+  __syncthreads();
+  for (int e = t; e < S * S; e += 256) wg[e] = 0.0;   // W is consumed
+  if (warp == 0) {
+    int conv = 1, bad = 0;
+    for (int i = t; i < S; i += 32) {
+      const double v = __ldcg(A.rn2 + (long long)c * S + i);
+      if (!isfinite(v)) bad = 1;
+      if (!(v <= A.target2[(long long)c * S + i])) conv = 0;
+    }
+    conv = __all_sync(0xffffffffu, conv);
+    bad = __any_sync(0xffffffffu, bad);
+    for (int i = t; i < S; i += 32) A.rn2[(long long)c * S + i] = 0.0;   // consumed
+    if (t == 0) {
+      st.iters += 1;
+      if (bad) {
+        st.status = BLOCKOA_ERR_BREAKDOWN;
+        st.active = 0;
+      } else if (conv) {
+        st.status = BLOCKOA_OK;
+        st.active = 0;
+      } else if (st.iters >= A.maxiter) {
+        st.status = BLOCKOA_ERR_NOT_CONVERGED;
+        st.active = 0;
+      }
     }
   }
 }
