@@ -84,9 +84,23 @@ typedef struct {
   int check_every;      /* block iterations between convergence polls by the host (<= 0: 8) */
   int precond;          /* BLOCKOA_PRECOND_NONE (the paper's unpreconditioned block CG) or
                            BLOCKOA_PRECOND_JACOBI (diagonal: directions from D^-1 R) */
+  int small_solve;      /* BLOCKOA_SMALL_AUTO or BLOCKOA_SMALL_FP64_CHOLESKY (below) */
 } blockoa_solve_opts;
 
 enum { BLOCKOA_PRECOND_NONE = 0, BLOCKOA_PRECOND_JACOBI = 1 };
+
+/*
+ * How the s x s systems Gamma alpha = rho and Gamma beta = -W are solved:
+ *  BLOCKOA_SMALL_AUTO: FP64 form: float64 diagonal-pivoted Cholesky and
+ *    substitution in kernels of their own.  MIXED form: in the last CTA per
+ *    chip of the Gram kernels, by the symmetric sweep operator (Gauss-Jordan
+ *    with the pivots and deflation test of the pivoted Cholesky) in
+ *    double-float arithmetic (~48-bit significand, ~2^-44 relative), which
+ *    leaves G_KK^-1 so that alpha and beta are plain s x s products.
+ *  BLOCKOA_SMALL_FP64_CHOLESKY: float64 pivoted Cholesky and substitution
+ *    in kernels of their own for both forms.
+ */
+enum { BLOCKOA_SMALL_AUTO = 0, BLOCKOA_SMALL_FP64_CHOLESKY = 1 };
 
 typedef struct {
   int status;           /* blockoa_status of this chip */

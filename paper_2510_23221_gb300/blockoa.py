@@ -28,6 +28,8 @@ FP64 = 0
 MIXED = 1
 PRECOND_NONE = 0
 PRECOND_JACOBI = 1
+SMALL_AUTO = 0
+SMALL_FP64_CHOLESKY = 1
 
 EXPORTED = (
     "blockoa_assemble", "blockoa_operator_size", "blockoa_operator_total", "blockoa_build_rhs",
@@ -50,7 +52,8 @@ class SolveOpts(ct.Structure):
     _fields_ = [("rtol", ct.c_double), ("maxiter", ct.c_int), ("precision", ct.c_int),
                 ("inner_rtol", ct.c_double), ("max_refine", ct.c_int),
                 ("deflate_tol", ct.c_double), ("x0", ct.c_void_p), ("check_every", ct.c_int),
-                ("precond", ct.c_int)]
+                ("precond", ct.c_int),
+                ("small_solve", ct.c_int)]
 
 
 class SolveStats(ct.Structure):
@@ -220,11 +223,13 @@ class Stats:
 def block_solve(op: Operator, B, X, s: int, rtol: float = 1e-12, maxiter: int = 100000,
                 precision: int = FP64, inner_rtol: float = 0.0, max_refine: int = 0,
                 deflate_tol: float = 0.0, x0=None, check_every: int = 0, precond: int = PRECOND_NONE,
+                small_solve: int = SMALL_AUTO,
                 stream=None, raise_on_error: bool = True) -> List[Stats]:
     import torch
     o = SolveOpts(rtol=rtol, maxiter=maxiter, precision=precision, inner_rtol=inner_rtol,
                   max_refine=max_refine, deflate_tol=deflate_tol,
-                  x0=_ptr(x0, torch.float64, "x0"), check_every=check_every, precond=precond)
+                  x0=_ptr(x0, torch.float64, "x0"), check_every=check_every, precond=precond,
+                  small_solve=small_solve)
     st = (SolveStats * op.n_chips)()
     code = _lib().blockoa_block_solve(op.handle, _ptr(B, torch.float64, "B"),
                                       _ptr(X, torch.float64, "X"), s, ct.byref(o), st,

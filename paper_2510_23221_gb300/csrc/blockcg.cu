@@ -328,7 +328,7 @@ spmm_gram_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chi
   }
   // mixed form: the chip's last CTA sweeps Gamma and forms alpha
   if constexpr (sizeof(T) == 4) {
-    if (last_cta_of_chip(A.ticket + u.chip, A.unit_count[u.chip])) chip_alpha<T, S>(A, u.chip);
+    if (A.tail && last_cta_of_chip(A.ticket + u.chip, A.unit_count[u.chip])) chip_alpha<T, S>(A, u.chip);
   }
 }
 
@@ -428,7 +428,8 @@ update_gram_kernel(const Unit *__restrict__ units, const T *__restrict__ P, cons
   }
   // mixed form: the chip's last CTA forms beta and tests convergence
   if constexpr (sizeof(T) == 4) {
-    if (last_cta_of_chip(A.ticket + A.n_chips + u.chip, A.unit_count[u.chip])) chip_beta<T, S>(A, u.chip);
+    if (A.tail && last_cta_of_chip(A.ticket + A.n_chips + u.chip, A.unit_count[u.chip]))
+      chip_beta<T, S>(A, u.chip);
   }
 }
 
@@ -556,17 +557,15 @@ __global__ void accumulate_kernel(const Unit *__restrict__ units, const int *__r
 }
 
 // ---------------------------------------------------------------- workspace
-// Launches per block-CG iteration and their timing classes: the mixed form
-// runs the small solves in the tails of the Gram kernels, the float64 form
-// in kernels of their own.
+// Launches per block-CG iteration and their timing classes: with the small
+// solves in the tails of the Gram kernels (CH = false) three, with the
+// Cholesky kernels (CH = true) five.
 constexpr int kMaxLoopKernels = 5;
-template <typename T>
-constexpr int loop_kernels() { return sizeof(T) == 4 ? 3 : 5; }
-template <typename T>
-constexpr int loop_class(int i) {
-  return sizeof(T) == 4 ? (i == 0 ? KC_SPMM_GRAM : i == 1 ? KC_UPDATE_GRAM : KC_P_UPDATE)
-                        : (i == 0 ? KC_SPMM_GRAM : i == 1 ? KC_ALPHA_SOLVE : i == 2 ? KC_UPDATE_GRAM
-                                                  : i == 3 ? KC_BETA_SOLVE : KC_P_UPDATE);
+constexpr int loop_kernels(bool ch) { return ch ? 5 : 3; }
+constexpr int loop_class(bool ch, int i) {
+  return !ch ? (i == 0 ? KC_SPMM_GRAM : i == 1 ? KC_UPDATE_GRAM : KC_P_UPDATE)
+             : (i == 0 ? KC_SPMM_GRAM : i == 1 ? KC_ALPHA_SOLVE : i == 2 ? KC_UPDATE_GRAM
+                                       : i == 3 ? KC_BETA_SOLVE : KC_P_UPDATE);
 }
 
 struct SolveWS {
@@ -599,7 +598,7 @@ struct SolveWS {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t tev[kMaxLoopKernels + 1] = {};   // recorded around the kernels of each chunk's first iteration
-  int graph_iters = 0, graph_maxiter = -1, graph_s = -1, graph_pc = -1;
+  int graph_iters = 0, graph_maxiter = -1, graph_s = -1, graph_pc = -1, graph_ch = -1;
   double graph_tol = -1.0;
   std::vector<void *> allocs;
 };
@@ -655,14 +654,13 @@ static void set_smem_limits() {
                        (int)update_smem<T, S>());
   cudaFuncSetAttribute(p_update_kernel<T, S, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pupdate_smem<T, S>());
-  if constexpr (sizeof(T) == 8)
-    cudaFuncSetAttribute(chol_alpha_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)chol_smem_bytes<S>());
+  cudaFuncSetAttribute(chol_alpha_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)chol_smem_bytes<S>());
 }
 
 // One block-CG iteration for every active chip; with `ev`, an event is
 // recorded before each kernel and after the last (for live timing).
-template <typename T, int S, bool PC>
+template <typename T, int S, bool PC, bool CH>
 static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const SmallArgs &sa,
                              cudaStream_t st, cudaEvent_t *ev) {
   const T *g = sizeof(T) == 4 ? (const T *)op->g32 : (const T *)op->g64;
@@ -675,16 +673,16 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
   mark(m++);
   spmm_gram_kernel<T, S><<<ws->n_units, 256, spmm_smem<T, S>(), st>>>(
       ws->units, op->d_chips, g, (const T *)ws->P, (const T *)ws->R, (T *)ws->Q, sa);
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (CH) {
     mark(m++);
-    chol_alpha_kernel<S><<<ws->n_chips * S, 256, chol_smem_bytes<S>(), st>>>(sa);
+    chol_alpha_kernel<T, S><<<ws->n_chips * S, 256, chol_smem_bytes<S>(), st>>>(sa);
   }
   mark(m++);
   update_gram_kernel<T, S, PC><<<ws->n_units, 256, update_smem<T, S>(), st>>>(
       ws->units, (const T *)ws->P, (const T *)ws->Q, (T *)ws->D, (T *)ws->R, dinv, sa);
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (CH) {
     mark(m++);
-    chol_beta_kernel<S><<<ws->n_chips * S, 32, 0, st>>>(sa);
+    chol_beta_kernel<T, S><<<ws->n_chips * S, 32, 0, st>>>(sa);
   }
   mark(m++);
   p_update_kernel<T, S, PC><<<ws->n_units_tile, 256, pupdate_smem<T, S>(), st>>>(
@@ -778,26 +776,35 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
   const double tol = o->deflate_tol > 0 ? o->deflate_tol : (prec == BLOCKOA_MIXED ? 1e-6 : 1e-14);
   const int check_every = o->check_every > 0 ? o->check_every : 8;
   const int pc = o->precond == BLOCKOA_PRECOND_JACOBI ? 1 : 0;
+  // the float64 form always factors by Cholesky in kernels of their own
+  const bool ch = prec == BLOCKOA_FP64 || o->small_solve == BLOCKOA_SMALL_FP64_CHOLESKY;
 
   SmallArgs sa;
   sa.state = ws->state; sa.gram = ws->gram; sa.rho = ws->rho; sa.wg = ws->wg; sa.rn2 = ws->rn2;
   sa.target2 = ws->target2; sa.ginv = ws->ginv; sa.dsc = ws->dsc; sa.rank = ws->rank;
   sa.rinv = ws->rinv; sa.perm = ws->perm;
   sa.alpha = ws->alpha; sa.beta = ws->beta;
-  sa.ticket = ws->ticket; sa.unit_count = ws->unit_count; sa.n_chips = nc;
+  sa.ticket = ws->ticket; sa.unit_count = ws->unit_count; sa.n_chips = nc; sa.tail = ch ? 0 : 1;
   sa.s = s; sa.maxiter = maxiter; sa.tol = tol;
 
   // Build (or reuse) the graph of `check_every` iterations.
   if (!ws->graph || ws->graph_iters != check_every || ws->graph_maxiter != maxiter ||
-      ws->graph_s != s || ws->graph_tol != tol || ws->graph_pc != pc) {
+      ws->graph_s != s || ws->graph_tol != tol || ws->graph_pc != pc || ws->graph_ch != (int)ch) {
     if (ws->graph) { cudaGraphExecDestroy(ws->graph); ws->graph = nullptr; }
     cudaGraph_t graph = nullptr;
     for (int i = 0; i <= kMaxLoopKernels; ++i)
       if (!ws->tev[i]) BLOCKOA_CUDA(cudaEventCreate(&ws->tev[i]));
     BLOCKOA_CUDA(cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < check_every; ++k)
-      if (pc) launch_iteration<T, S, true>(op, ws, sa, ws->cap, k == 0 ? ws->tev : nullptr);
-      else launch_iteration<T, S, false>(op, ws, sa, ws->cap, k == 0 ? ws->tev : nullptr);
+    for (int k = 0; k < check_every; ++k) {
+      cudaEvent_t *ev = k == 0 ? ws->tev : nullptr;
+      if (ch) {
+        if (pc) launch_iteration<T, S, true, true>(op, ws, sa, ws->cap, ev);
+        else launch_iteration<T, S, false, true>(op, ws, sa, ws->cap, ev);
+      } else if constexpr (sizeof(T) == 4) {
+        if (pc) launch_iteration<T, S, true, false>(op, ws, sa, ws->cap, ev);
+        else launch_iteration<T, S, false, false>(op, ws, sa, ws->cap, ev);
+      }
+    }
     cudaError_t e = cudaStreamEndCapture(ws->cap, &graph);
     if (e != cudaSuccess) return cuda_status(e, "capture block-CG iterations");
     e = cudaGraphInstantiate(&ws->graph, graph, 0);
@@ -808,6 +815,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     ws->graph_s = s;
     ws->graph_tol = tol;
     ws->graph_pc = pc;
+    ws->graph_ch = (int)ch;
   }
 
   // Inputs: padded B and X0, ||B_j||^2.
@@ -907,15 +915,15 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     BLOCKOA_CUDA(cudaGetLastError());
     // Inner block-CG iterations, polled every `check_every` iterations.
     for (;;) {
-      g_launches += (long long)loop_kernels<T>() * check_every;
-      for (int i = 0; i < loop_kernels<T>(); ++i) add_launches(op, loop_class<T>(i), check_every);
+      g_launches += (long long)loop_kernels(ch) * check_every;
+      for (int i = 0; i < loop_kernels(ch); ++i) add_launches(op, loop_class(ch, i), check_every);
       BLOCKOA_CUDA(cudaGraphLaunch(ws->graph, st));
       BLOCKOA_CUDA(cudaMemcpyAsync(ws->h_state, ws->state, sizeof(ChipSolveState) * nc, cudaMemcpyDeviceToHost, st));
       BLOCKOA_CUDA(cudaStreamSynchronize(st));
-      for (int i = 0; i < loop_kernels<T>(); ++i) {   // live timing of this chunk's first iteration
+      for (int i = 0; i < loop_kernels(ch); ++i) {   // live timing of this chunk's first iteration
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, ws->tev[i], ws->tev[i + 1]) == cudaSuccess)
-          add_time(op, loop_class<T>(i), ms);
+          add_time(op, loop_class(ch, i), ms);
         else
           cudaGetLastError();
       }
@@ -968,6 +976,8 @@ extern "C" int blockoa_block_solve(blockoa_operator *op, const double *B, double
   if (!(opts->rtol > 0.0) || opts->maxiter < 0) return BLOCKOA_ERR_INVALID;
   if (opts->precision != BLOCKOA_FP64 && opts->precision != BLOCKOA_MIXED) return BLOCKOA_ERR_INVALID;
   if (opts->precond != BLOCKOA_PRECOND_NONE && opts->precond != BLOCKOA_PRECOND_JACOBI) return BLOCKOA_ERR_INVALID;
+  if (opts->small_solve != BLOCKOA_SMALL_AUTO && opts->small_solve != BLOCKOA_SMALL_FP64_CHOLESKY)
+    return BLOCKOA_ERR_INVALID;
   if (s == 0) {
     for (int c = 0; c < op->n_chips; ++c) stats[c].status = BLOCKOA_OK;
     return BLOCKOA_OK;

@@ -59,6 +59,7 @@ struct SmallArgs {
   int *ticket;      // [2][chip] CTA completion counters of the two Gram kernels (zero between launches)
   const int *unit_count;  // [chip] CTAs per chip of the Gram kernels
   int n_chips;
+  int tail;         // 1: the Gram kernels' last CTAs solve (mixed form, sweep)
   int s;            // caller's columns (for deflation counts)
   int maxiter;      // limit on total iterations per chip
   double tol;       // deflation threshold on scaled pivots

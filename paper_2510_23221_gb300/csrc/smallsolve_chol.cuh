@@ -1,6 +1,8 @@
-// Small s x s solves of the float64 block-CG form (Eq. 4, Sec. III-A), by
-// diagonal-pivoted Cholesky and substitution, as the float64 reference
-// computes them.
+// Small s x s solves by float64 diagonal-pivoted Cholesky and substitution
+// (Eq. 4, Sec. III-A), as the float64 reference computes them: always for
+// the float64 form, and for the mixed form on request
+// (BLOCKOA_SMALL_FP64_CHOLESKY); alpha and beta are written in the loop's
+// precision.
 //
 // Per chip and iteration, with D = diag(Gamma)^-1/2:
 //   D Gamma D = L L^T by diagonal-pivoted Cholesky, stopping at the first
@@ -84,10 +86,10 @@ __device__ __forceinline__ void chol_find_pivot(const double *dg, const int *gon
 // factors F (F[i][k] = L[i][k] / L[k][k] below the diagonal, L[k][i] / L[k][k]
 // above, zero on it) and write sign * D x into column j of out (zero rows
 // for deflated columns).  One warp; lane i holds rows i + 32 q.
-template <int S, int LDF>
+template <typename T, int S, int LDF>
 __device__ __forceinline__ void chol_solve_column(const double *F, const double *rv, const double *d,
                                                   const int *perm, int r, const double *rhs, int j,
-                                                  double sign, double *out) {
+                                                  double sign, T *out) {
   constexpr int RL = (S + 31) / 32;
   const int lane = threadIdx.x & 31;
   double y[RL];
@@ -137,13 +139,13 @@ __device__ __forceinline__ void chol_solve_column(const double *F, const double 
 #pragma unroll
   for (int q = 0; q < RL; ++q) {
     const int i = lane + 32 * q;
-    if (i < S) out[(long long)i * S + j] = 0.0;
+    if (i < S) out[(long long)i * S + j] = T(0);
   }
   __syncwarp();
 #pragma unroll
   for (int q = 0; q < RL; ++q) {
     const int i = lane + 32 * q;
-    if (i < r) out[(long long)pr[q] * S + j] = sign * d[pr[q]] * y[q];
+    if (i < r) out[(long long)pr[q] * S + j] = (T)(sign * d[pr[q]] * y[q]);
   }
 }
 
@@ -153,7 +155,7 @@ __device__ __forceinline__ void chol_solve_column(const double *F, const double 
 // 1-7 apply the rank-1 update to the strict lower part (fixed entries per
 // thread; rows and columns already pivoted receive zero updates, the
 // pivot's own row is never read again).  Two barriers per step.
-template <int S>
+template <typename T, int S>
 __global__ void __launch_bounds__(256) chol_alpha_kernel(SmallArgs A) {
   constexpr int RL = (S + 31) / 32;
   constexpr int NE = S * (S - 1) / 2;          // strict lower entries
@@ -276,13 +278,13 @@ __global__ void __launch_bounds__(256) chol_alpha_kernel(SmallArgs A) {
     }
   }
   if (r == 0 || warp != 0) return;
-  chol_solve_column<S, S + 1>(&sh.W[0][0], sh.rv, sh.d, sh.perm, r, A.rho + (long long)c * S * S, j, 1.0,
-                              reinterpret_cast<double *>(A.alpha) + (long long)c * S * S);
+  chol_solve_column<T, S, S + 1>(&sh.W[0][0], sh.rv, sh.d, sh.perm, r, A.rho + (long long)c * S * S, j, 1.0,
+                                 reinterpret_cast<T *>(A.alpha) + (long long)c * S * S);
 }
 
 // beta = -Gamma^+ W, column j; CTA 0 of each chip also clears Gamma and rho
 // and runs the per-column convergence test of the updated residual.
-template <int S>
+template <typename T, int S>
 __global__ void __launch_bounds__(32) chol_beta_kernel(SmallArgs A) {
   __shared__ double F[S][S + 1];
   __shared__ double rv[S], d[S];
@@ -300,8 +302,8 @@ __global__ void __launch_bounds__(32) chol_beta_kernel(SmallArgs A) {
     perm[i] = A.perm[(long long)c * S + i];
   }
   __syncwarp();
-  chol_solve_column<S, S + 1>(&F[0][0], rv, d, perm, r, A.wg + (long long)c * S * S, j, -1.0,
-                              reinterpret_cast<double *>(A.beta) + (long long)c * S * S);
+  chol_solve_column<T, S, S + 1>(&F[0][0], rv, d, perm, r, A.wg + (long long)c * S * S, j, -1.0,
+                                 reinterpret_cast<T *>(A.beta) + (long long)c * S * S);
   if (j != 0) return;
   for (int e = t; e < S * S; e += 32) {
     A.gram[(long long)c * S * S + e] = 0.0;

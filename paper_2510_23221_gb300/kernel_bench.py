@@ -34,6 +34,7 @@ def main():
     p.add_argument("--M", type=int, default=1000)
     p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     p.add_argument("--precond", choices=["none", "jacobi"], default="jacobi")
+    p.add_argument("--small", choices=["auto", "fp64-cholesky"], default="auto")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--reps", type=int, default=10)
     a = p.parse_args()
@@ -58,7 +59,8 @@ def main():
 
     def call():
         if a.call == "solve":
-            stats[:] = bo.block_solve(op, B, U, s, rtol=1e-6, precision=prec, precond=pc)
+            stats[:] = bo.block_solve(op, B, U, s, rtol=1e-6, precision=prec, precond=pc,
+                                      small_solve=bo.SMALL_AUTO if a.small == "auto" else bo.SMALL_FP64_CHOLESKY)
         elif a.call == "apply":
             bo.apply_operator(op, T, q, M, prec)
         else:
@@ -82,7 +84,7 @@ def main():
     else:
         nbytes = esz * n * M + (6 * ((s + 15) // 16 * 16) * n if prec == bo.MIXED else 8 * n * s)
     kt = bo.kernel_times(op)
-    print(json.dumps({"call": a.call, "chip": a.chip, "cells": n, "s": s, "M": M,
+    print(json.dumps({"call": a.call, "chip": a.chip, "cells": n, "s": s, "M": M, "small": a.small,
                       "precision": a.precision, "ms": round(ms, 4),
                       "GBps": round(nbytes / ms / 1e6, 1),
                       "solver": [dataclasses.asdict(st) for st in stats],

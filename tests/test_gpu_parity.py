@@ -287,6 +287,28 @@ def test_jacobi_preconditioned_solve(precision):
         assert np.all(relcols(Xs[c], ref) < 1e-8)
 
 
+@pytest.mark.parametrize("precond", [bo.PRECOND_NONE, bo.PRECOND_JACOBI])
+def test_mixed_with_fp64_cholesky_small_solves(precond):
+    """The mixed loop with float64 Cholesky small solves reaches the same basis."""
+    w = synth.small_fp64_workload()
+    chip = w.chips[0]
+    A = orc.assemble(chip)
+    B = orc.rhs(chip, w.density[0])
+    U_or, _ = orc.block_cg(A, B, rtol=1e-12)
+    (X,), (st,) = _solve([chip], [B], 8, bo.MIXED, 1e-12, precond=precond,
+                         small_solve=bo.SMALL_FP64_CHOLESKY)
+    assert st.status == bo.OK and st.relres_max <= 1e-12
+    assert np.all(relcols(X, U_or) < 1e-9)
+    chips = small_chips()
+    rng = np.random.default_rng(79)
+    Bs = [rng.uniform(0, 1e-2, (c.n, 12)) for c in chips]
+    Xs, stats = _solve(chips, Bs, 12, bo.MIXED, 1e-11, precond=precond, small_solve=bo.SMALL_FP64_CHOLESKY)
+    for c, chip in enumerate(chips):
+        assert stats[c].status == bo.OK
+        ref = np.linalg.solve(orc.assemble(chip).toarray(), Bs[c])
+        assert np.all(relcols(Xs[c], ref) < 1e-8)
+
+
 def test_deflation_duplicate_and_zero_columns():
     chip = synth.random_small_chip(81, 12, 10, 3)
     B = np.random.default_rng(81).uniform(0, 1e-2, (chip.n, 6))
@@ -328,6 +350,9 @@ def test_invalid_calls_return_invalid():
     assert e.value.code == bo.ERR_INVALID
     with pytest.raises(bo.BlockoaError) as e:
         bo.block_solve(op, B, B.clone(), 4, precond=7)
+    assert e.value.code == bo.ERR_INVALID
+    with pytest.raises(bo.BlockoaError) as e:
+        bo.block_solve(op, B, B.clone(), 4, small_solve=5)
     assert e.value.code == bo.ERR_INVALID
     T = torch.zeros(chip.n, dtype=torch.float64, device="cuda")
     with pytest.raises(bo.BlockoaError):
