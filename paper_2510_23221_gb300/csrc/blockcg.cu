@@ -246,24 +246,63 @@ template <typename T, int S>
 constexpr size_t tile_bytes() { return (size_t)S * BK<T, S>::LD * sizeof(T); }
 constexpr size_t kRedBytes = 256 * 16 * sizeof(double);
 
+// ---------------------------------------------------------------- unit scheduling
+// The loop kernels run persistent CTAs (about as many as fit on the GPU at
+// once) that fetch units -- a few tiles of one chip -- from a counter, so
+// SMs finish together whatever the chips' sizes, and units of chips that
+// have converged are skipped in bulk (the chips' units are contiguous).
+struct UnitSched {
+  const Unit *units;
+  int n_units;
+  const int *chip_unit_end;   // [chip] index of the first unit past the chip
+  int *work;                  // [0] next unit, [1] CTAs finished (zero between launches)
+};
+
+// Next unit of the calling CTA (n_units when none is left).
+__device__ __forceinline__ int next_unit(const UnitSched &us, const ChipSolveState *state, int *slot) {
+  __syncthreads();   // every thread has read the previous value
+  if (threadIdx.x == 0) {
+    int ui;
+    for (;;) {
+      ui = atomicAdd(&us.work[0], 1);
+      if (ui >= us.n_units) break;
+      const int chip = us.units[ui].chip;
+      if (state[chip].active) break;
+      atomicMax(&us.work[0], us.chip_unit_end[chip]);   // skip the rest of this chip
+    }
+    *slot = ui;
+  }
+  __syncthreads();
+  return *slot;
+}
+
+// Every CTA calls this once its loop is over; the last one resets the
+// counters for the next launch (no CTA fetches after it has finished).
+__device__ __forceinline__ void sched_finish(const UnitSched &us) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&us.work[1], 1) == (int)gridDim.x - 1) {
+      us.work[0] = 0;
+      us.work[1] = 0;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- kernels
 // Q = A P on the block layout; Gamma += P^T Q and rho += P^T R per chip.
 template <typename T, int S>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
-spmm_gram_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chips,
-                 const T *__restrict__ g, const T *__restrict__ P, const T *__restrict__ R,
-                 T *__restrict__ Q, const SmallArgs A) {
+spmm_gram_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T *__restrict__ g,
+                 const T *__restrict__ P, const T *__restrict__ R, T *__restrict__ Q, const SmallArgs A) {
   using G = BK<T, S>;
   constexpr int V = G::V;
   extern __shared__ __align__(16) unsigned char smem[];
   T *sP = reinterpret_cast<T *>(smem);
   T *sQ = sP + S * G::LD;
   T *sR = sQ + S * G::LD;
-  double *red = reinterpret_cast<double *>(smem);   // reused after the tile loop
-  const Unit u = units[blockIdx.x];
-  if (!A.state[u.chip].active) return;
-  const ChipDev ch = chips[u.chip];
-  const int nx = ch.nx, ny = ch.ny, nz = ch.nz, nxny = nx * ny;
+  double *red = reinterpret_cast<double *>(smem);   // reused between units
+  __shared__ int s_unit;
   const int t = threadIdx.x;
   const int j0 = (t % G::TPR) * V, cl0 = (t / G::TPR) * 4;
   const int grp = t / G::NT, w = t % G::NT;
@@ -276,136 +315,88 @@ spmm_gram_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chi
   T acc[NA];
 #pragma unroll
   for (int e = 0; e < NA; ++e) acc[e] = T(0);
-  for (long long base = u.begin; base < u.end; base += G::TC) {
-    T pc[4][V], qv[4][V], rv[4][V];
-    load_block<T, S>(pc, P, base + cl0, u.end, j0);
-    load_block<T, S>(rv, R, base + cl0, u.end, j0);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const long long a = base + cl0 + k;
-#pragma unroll
-      for (int v = 0; v < V; ++v) qv[k][v] = T(0);
-      if (a < u.end) {
-        const int loc = (int)(a - ch.off);
-        const int x = loc % nx, y = (loc / nx) % ny, z = loc / nxny;
-        const auto c4 = coef_ld(g, a);
-#pragma unroll
-        for (int v = 0; v < V; ++v) qv[k][v] = c4.w * pc[k][v];
-        auto nb = [&](long long b, T gg) {
-          T o[V];
-          vload<T>(o, P + b * S + j0);
-#pragma unroll
-          for (int v = 0; v < V; ++v) qv[k][v] += gg * (pc[k][v] - o[v]);
-        };
-        if (x + 1 < nx) nb(a + 1, c4.x);
-        if (x > 0) nb(a - 1, coef_ld(g, a - 1).x);
-        if (y + 1 < ny) nb(a + nx, c4.y);
-        if (y > 0) nb(a - nx, coef_ld(g, a - nx).y);
-        if (z + 1 < nz) nb(a + nxny, c4.z);
-        if (z > 0) nb(a - nxny, coef_ld(g, a - nxny).z);
+  int cur = -1, run = 0;   // chip of the running accumulation and its units
+  for (;;) {
+    const int ui = next_unit(us, A.state, &s_unit);
+    const int chip = ui < us.n_units ? us.units[ui].chip : -1;
+    if (run > 0 && chip != cur) {   // flush the running chip
+      if constexpr (SPLIT) {
+        gram_flush_split<T, S>(acc, red, A.gram + (long long)cur * S * S, A.rho + (long long)cur * S * S);
+      } else {
+        gram_flush<T, S>(acc, red, A.gram + (long long)cur * S * S);
+        gram_flush<T, S>(acc + 16, red, A.rho + (long long)cur * S * S);
       }
+      // mixed form: the flush that completes the chip sweeps Gamma and forms alpha
+      if constexpr (sizeof(T) == 4) {
+        if (A.tail && last_flush_of_chip(A.ticket + cur, run, A.unit_count[cur])) chip_alpha<T, S>(A, cur);
+      }
+#pragma unroll
+      for (int e = 0; e < NA; ++e) acc[e] = T(0);
+      run = 0;
     }
-    store_block<T, S>(Q, qv, base + cl0, u.end, j0);
-    put_tile<T, G::LD>(sP, pc, cl0, j0);
-    put_tile<T, G::LD>(sQ, qv, cl0, j0);
-    put_tile<T, G::LD>(sR, rv, cl0, j0);
-    __syncthreads();
-    if constexpr (SPLIT) {
-      constexpr int H = G::NG / 2;
-      const bool second = grp >= H;
-      gram_range<T, S>(acc, sP, second ? sR : sQ, i0, k0, (grp % H) * 2 * G::GC, 2 * G::GC);
-    } else {
-      gram_tile<T, S>(acc, sP, sQ, i0, k0, grp);
-      gram_tile<T, S>(acc + 16, sP, sR, i0, k0, grp);
-    }
-    __syncthreads();
-  }
-  if constexpr (SPLIT) {
-    gram_flush_split<T, S>(acc, red, A.gram + (long long)u.chip * S * S, A.rho + (long long)u.chip * S * S);
-  } else {
-    gram_flush<T, S>(acc, red, A.gram + (long long)u.chip * S * S);
-    gram_flush<T, S>(acc + 16, red, A.rho + (long long)u.chip * S * S);
-  }
-  // mixed form: the chip's last CTA sweeps Gamma and forms alpha
-  if constexpr (sizeof(T) == 4) {
-    if (A.tail && last_cta_of_chip(A.ticket + u.chip, A.unit_count[u.chip])) chip_alpha<T, S>(A, u.chip);
-  }
-}
-
-// X += P alpha, R -= Q alpha; W += Q^T R_new and rn2 += ||R_new_j||^2.
-template <typename T, int S, bool PC>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
-update_gram_kernel(const Unit *__restrict__ units, const T *__restrict__ P, const T *__restrict__ Q,
-                   T *__restrict__ X, T *__restrict__ R, const T *__restrict__ dinv, const SmallArgs A) {
-  using G = BK<T, S>;
-  constexpr int V = G::V;
-  extern __shared__ __align__(16) unsigned char smem[];
-  T *sP = reinterpret_cast<T *>(smem);
-  T *sQ = sP + S * G::LD;
-  T *sR = sQ + S * G::LD;
-  T *sA = sR + S * G::LD;
-  double *red = reinterpret_cast<double *>(smem);   // reused after the tile loop
-  const Unit u = units[blockIdx.x];
-  if (!A.state[u.chip].active) return;
-  const int t = threadIdx.x;
-  const T *al = reinterpret_cast<const T *>(A.alpha) + (long long)u.chip * S * S;
-  for (int e = t; e < S * S; e += 256) sA[e] = al[e];
-  const int j0 = (t % G::TPR) * V, cl0 = (t / G::TPR) * 4;
-  const int grp = t / G::NT, w = t % G::NT;
-  const int i0 = (w / G::NB) * 4, k0 = (w % G::NB) * 4;
-  T aw[16], rn[V];
-#pragma unroll
-  for (int e = 0; e < 16; ++e) aw[e] = T(0);
-#pragma unroll
-  for (int v = 0; v < V; ++v) rn[v] = T(0);
-  for (long long base = u.begin; base < u.end; base += G::TC) {
-    {
-      T pv[4][V], qv[4][V];
-      load_block<T, S>(pv, P, base + cl0, u.end, j0);
-      load_block<T, S>(qv, Q, base + cl0, u.end, j0);
-      put_tile<T, G::LD>(sP, pv, cl0, j0);
-      put_tile<T, G::LD>(sQ, qv, cl0, j0);
-    }
-    T xv[4][V], rv[4][V];
-    load_block<T, S>(xv, X, base + cl0, u.end, j0);
-    load_block<T, S>(rv, R, base + cl0, u.end, j0);
-    __syncthreads();
-#pragma unroll 4
-    for (int i = 0; i < S; ++i) {
-      T p4[4], q4[4], av[V];
-      ld4<T, G::LD>(p4, sP, i, cl0);
-      ld4<T, G::LD>(q4, sQ, i, cl0);
-      vload<T>(av, sA + i * S + j0);
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          xv[k][v] += p4[k] * av[v];
-          rv[k][v] -= q4[k] * av[v];
-        }
-    }
-    store_block<T, S>(X, xv, base + cl0, u.end, j0);
-    store_block<T, S>(R, rv, base + cl0, u.end, j0);
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-      for (int v = 0; v < V; ++v) rn[v] += rv[k][v] * rv[k][v];  // zero past the end
-    if constexpr (PC) {
-      // Gram with Z = D^-1 R_new (R stays unscaled in memory)
+    if (ui >= us.n_units) break;
+    const Unit u = us.units[ui];
+    cur = u.chip;
+    ++run;
+    const ChipDev ch = chips[u.chip];
+    const int nx = ch.nx, ny = ch.ny, nz = ch.nz, nxny = nx * ny;
+    for (long long base = u.begin; base < u.end; base += G::TC) {
+      T pc[4][V], qv[4][V], rv[4][V];
+      load_block<T, S>(pc, P, base + cl0, u.end, j0);
+      load_block<T, S>(rv, R, base + cl0, u.end, j0);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const T di = base + cl0 + k < u.end ? dinv[base + cl0 + k] : T(0);
+        const long long a = base + cl0 + k;
 #pragma unroll
-        for (int v = 0; v < V; ++v) rv[k][v] *= di;
+        for (int v = 0; v < V; ++v) qv[k][v] = T(0);
+        if (a < u.end) {
+          const int loc = (int)(a - ch.off);
+          const int x = loc % nx, y = (loc / nx) % ny, z = loc / nxny;
+          const auto c4 = coef_ld(g, a);
+#pragma unroll
+          for (int v = 0; v < V; ++v) qv[k][v] = c4.w * pc[k][v];
+          auto nb = [&](long long b, T gg) {
+            T o[V];
+            vload<T>(o, P + b * S + j0);
+#pragma unroll
+            for (int v = 0; v < V; ++v) qv[k][v] += gg * (pc[k][v] - o[v]);
+          };
+          if (x + 1 < nx) nb(a + 1, c4.x);
+          if (x > 0) nb(a - 1, coef_ld(g, a - 1).x);
+          if (y + 1 < ny) nb(a + nx, c4.y);
+          if (y > 0) nb(a - nx, coef_ld(g, a - nx).y);
+          if (z + 1 < nz) nb(a + nxny, c4.z);
+          if (z > 0) nb(a - nxny, coef_ld(g, a - nxny).z);
+        }
       }
+      store_block<T, S>(Q, qv, base + cl0, u.end, j0);
+      put_tile<T, G::LD>(sP, pc, cl0, j0);
+      put_tile<T, G::LD>(sQ, qv, cl0, j0);
+      put_tile<T, G::LD>(sR, rv, cl0, j0);
+      __syncthreads();
+      if constexpr (SPLIT) {
+        constexpr int H = G::NG / 2;
+        const bool second = grp >= H;
+        gram_range<T, S>(acc, sP, second ? sR : sQ, i0, k0, (grp % H) * 2 * G::GC, 2 * G::GC);
+      } else {
+        gram_tile<T, S>(acc, sP, sQ, i0, k0, grp);
+        gram_tile<T, S>(acc + 16, sP, sR, i0, k0, grp);
+      }
+      __syncthreads();
     }
-    put_tile<T, G::LD>(sR, rv, cl0, j0);
-    __syncthreads();
-    gram_tile<T, S>(aw, sQ, sR, i0, k0, grp);
-    __syncthreads();
   }
-  gram_flush<T, S>(aw, red, A.wg + (long long)u.chip * S * S);
-  // column norms: threads with equal (t % TPR) own the same columns
+  sched_finish(us);
+}
+
+// Flush of the update kernel's running accumulation for chip c: W += Q^T Z
+// (Gram blocks) and rn2 += ||R_new_j||^2 (threads with equal t % TPR own the
+// same columns).
+template <typename T, int S>
+__device__ __forceinline__ void update_flush(const T *aw, const T *rn, double *red, const SmallArgs &A, int c) {
+  using G = BK<T, S>;
+  constexpr int V = G::V;
+  const int t = threadIdx.x;
+  gram_flush<T, S>(aw, red, A.wg + (long long)c * S * S);
   T *rt = reinterpret_cast<T *>(red);
 #pragma unroll
   for (int v = 0; v < V; ++v) rt[t * V + v] = rn[v];
@@ -413,7 +404,6 @@ update_gram_kernel(const Unit *__restrict__ units, const T *__restrict__ P, cons
   if (t < G::TPR) {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      double sum = 0.0;
       T hi = T(0), lo = T(0);
       for (int tt = t; tt < 256; tt += G::TPR) {
         const T x = rt[tt * V + v];
@@ -422,64 +412,165 @@ update_gram_kernel(const Unit *__restrict__ units, const T *__restrict__ P, cons
         lo += (hi - (s2 - bp)) + (x - bp);
         hi = s2;
       }
-      sum = (double)hi + (double)lo;
-      atomicAdd(A.rn2 + (long long)u.chip * S + t * V + v, sum);
+      atomicAdd(A.rn2 + (long long)c * S + t * V + v, (double)hi + (double)lo);
     }
   }
-  // mixed form: the chip's last CTA forms beta and tests convergence
-  if constexpr (sizeof(T) == 4) {
-    if (A.tail && last_cta_of_chip(A.ticket + A.n_chips + u.chip, A.unit_count[u.chip]))
-      chip_beta<T, S>(A, u.chip);
-  }
+  __syncthreads();
 }
 
-// P = R + P beta (one tile per CTA).
+// X += P alpha, R -= Q alpha; W += Q^T Z_new and rn2 += ||R_new_j||^2.
 template <typename T, int S, bool PC>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
-p_update_kernel(const Unit *__restrict__ units, const ChipSolveState *__restrict__ state,
-                const T *__restrict__ beta, const T *__restrict__ R, T *__restrict__ P,
-                const T *__restrict__ dinv) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+update_gram_kernel(const UnitSched us, const T *__restrict__ P, const T *__restrict__ Q,
+                   T *__restrict__ X, T *__restrict__ R, const T *__restrict__ dinv, const SmallArgs A) {
+  using G = BK<T, S>;
+  constexpr int V = G::V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *sP = reinterpret_cast<T *>(smem);
+  T *sQ = sP + S * G::LD;
+  T *sR = sQ + S * G::LD;
+  T *sA = sR + S * G::LD;
+  double *red = reinterpret_cast<double *>(smem);   // reused between units
+  __shared__ int s_unit;
+  const int t = threadIdx.x;
+  const int j0 = (t % G::TPR) * V, cl0 = (t / G::TPR) * 4;
+  const int grp = t / G::NT, w = t % G::NT;
+  const int i0 = (w / G::NB) * 4, k0 = (w % G::NB) * 4;
+  T aw[16], rn[V];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) aw[e] = T(0);
+#pragma unroll
+  for (int v = 0; v < V; ++v) rn[v] = T(0);
+  int cur = -1, run = 0;
+  for (;;) {
+    const int ui = next_unit(us, A.state, &s_unit);
+    const int chip = ui < us.n_units ? us.units[ui].chip : -1;
+    if (run > 0 && chip != cur) {   // flush the running chip
+      update_flush<T, S>(aw, rn, red, A, cur);
+      // mixed form: the flush that completes the chip forms beta and tests convergence
+      if constexpr (sizeof(T) == 4) {
+        if (A.tail && last_flush_of_chip(A.ticket + A.n_chips + cur, run, A.unit_count[cur]))
+          chip_beta<T, S>(A, cur);
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) aw[e] = T(0);
+#pragma unroll
+      for (int v = 0; v < V; ++v) rn[v] = T(0);
+      run = 0;
+    }
+    if (ui >= us.n_units) break;
+    const Unit u = us.units[ui];
+    if (u.chip != cur) {   // alpha of the chip (the tiles below read sA after a barrier)
+      const T *al = reinterpret_cast<const T *>(A.alpha) + (long long)u.chip * S * S;
+      for (int e = t; e < S * S; e += 256) sA[e] = al[e];
+    }
+    cur = u.chip;
+    ++run;
+    for (long long base = u.begin; base < u.end; base += G::TC) {
+      {
+        T pv[4][V], qv[4][V];
+        load_block<T, S>(pv, P, base + cl0, u.end, j0);
+        load_block<T, S>(qv, Q, base + cl0, u.end, j0);
+        put_tile<T, G::LD>(sP, pv, cl0, j0);
+        put_tile<T, G::LD>(sQ, qv, cl0, j0);
+      }
+      T xv[4][V], rv[4][V];
+      load_block<T, S>(xv, X, base + cl0, u.end, j0);
+      load_block<T, S>(rv, R, base + cl0, u.end, j0);
+      __syncthreads();
+#pragma unroll 4
+      for (int i = 0; i < S; ++i) {
+        T p4[4], q4[4], av[V];
+        ld4<T, G::LD>(p4, sP, i, cl0);
+        ld4<T, G::LD>(q4, sQ, i, cl0);
+        vload<T>(av, sA + i * S + j0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            xv[k][v] += p4[k] * av[v];
+            rv[k][v] -= q4[k] * av[v];
+          }
+      }
+      store_block<T, S>(X, xv, base + cl0, u.end, j0);
+      store_block<T, S>(R, rv, base + cl0, u.end, j0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int v = 0; v < V; ++v) rn[v] += rv[k][v] * rv[k][v];  // zero past the end
+      if constexpr (PC) {
+        // Gram with Z = D^-1 R_new (R stays unscaled in memory)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const T di = base + cl0 + k < u.end ? dinv[base + cl0 + k] : T(0);
+#pragma unroll
+          for (int v = 0; v < V; ++v) rv[k][v] *= di;
+        }
+      }
+      put_tile<T, G::LD>(sR, rv, cl0, j0);
+      __syncthreads();
+      gram_tile<T, S>(aw, sQ, sR, i0, k0, grp);
+      __syncthreads();
+    }
+  }
+  sched_finish(us);
+}
+
+// P = Z + P beta, Z = R or D^-1 R.
+template <typename T, int S, bool PC>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+p_update_kernel(const UnitSched us, const ChipSolveState *__restrict__ state, const T *__restrict__ beta,
+                const T *__restrict__ R, T *__restrict__ P, const T *__restrict__ dinv) {
   using G = BK<T, S>;
   constexpr int V = G::V;
   extern __shared__ __align__(16) unsigned char smem[];
   T *sP = reinterpret_cast<T *>(smem);
   T *sB = sP + S * G::LD;
-  const Unit u = units[blockIdx.x];
-  if (!state[u.chip].active) return;
+  __shared__ int s_unit;
   const int t = threadIdx.x;
-  const T *be = beta + (long long)u.chip * S * S;
-  for (int e = t; e < S * S; e += 256) sB[e] = be[e];
   const int j0 = (t % G::TPR) * V, cl0 = (t / G::TPR) * 4;
-  for (long long base = u.begin; base < u.end; base += G::TC) {
-    {
-      T pv[4][V];
-      load_block<T, S>(pv, P, base + cl0, u.end, j0);
-      put_tile<T, G::LD>(sP, pv, cl0, j0);
+  int cur = -1;
+  for (;;) {
+    const int ui = next_unit(us, state, &s_unit);
+    if (ui >= us.n_units) break;
+    const Unit u = us.units[ui];
+    if (u.chip != cur) {   // beta of the chip (read after the tile barrier)
+      const T *be = beta + (long long)u.chip * S * S;
+      for (int e = t; e < S * S; e += 256) sB[e] = be[e];
+      cur = u.chip;
     }
-    T rv[4][V];
-    load_block<T, S>(rv, R, base + cl0, u.end, j0);
-    if constexpr (PC) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const T di = base + cl0 + k < u.end ? dinv[base + cl0 + k] : T(0);
-#pragma unroll
-        for (int v = 0; v < V; ++v) rv[k][v] *= di;
+    for (long long base = u.begin; base < u.end; base += G::TC) {
+      {
+        T pv[4][V];
+        load_block<T, S>(pv, P, base + cl0, u.end, j0);
+        put_tile<T, G::LD>(sP, pv, cl0, j0);
       }
-    }
-    __syncthreads();
+      T rv[4][V];
+      load_block<T, S>(rv, R, base + cl0, u.end, j0);
+      if constexpr (PC) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const T di = base + cl0 + k < u.end ? dinv[base + cl0 + k] : T(0);
+#pragma unroll
+          for (int v = 0; v < V; ++v) rv[k][v] *= di;
+        }
+      }
+      __syncthreads();
 #pragma unroll 4
-    for (int i = 0; i < S; ++i) {
-      T p4[4], bv[V];
-      ld4<T, G::LD>(p4, sP, i, cl0);
-      vload<T>(bv, sB + i * S + j0);
+      for (int i = 0; i < S; ++i) {
+        T p4[4], bv[V];
+        ld4<T, G::LD>(p4, sP, i, cl0);
+        vload<T>(bv, sB + i * S + j0);
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 4; ++k)
 #pragma unroll
-        for (int v = 0; v < V; ++v) rv[k][v] += p4[k] * bv[v];
+          for (int v = 0; v < V; ++v) rv[k][v] += p4[k] * bv[v];
+      }
+      store_block<T, S>(P, rv, base + cl0, u.end, j0);
+      __syncthreads();
     }
-    store_block<T, S>(P, rv, base + cl0, u.end, j0);
-    __syncthreads();
   }
+  sched_finish(us);
 }
 
 // ---------------------------------------------------------------- glue kernels
@@ -582,13 +673,12 @@ struct SolveWS {
          *ginv = nullptr, *dsc = nullptr,   // small-solve arithmetic type (8 bytes)
          *rinv = nullptr;
   int *perm = nullptr, *rank = nullptr, *outer_active = nullptr;
-  int *ticket = nullptr, *unit_count = nullptr;
+  int *ticket = nullptr, *unit_count = nullptr, *chip_unit_end = nullptr, *work = nullptr;
   void *alpha = nullptr, *beta = nullptr;
   ChipSolveState *state = nullptr;
-  Unit *units = nullptr;        // loop units
+  Unit *units = nullptr;        // loop units (contiguous per chip)
   int n_units = 0;
-  Unit *units_tile = nullptr;   // one tile per unit (P update)
-  int n_units_tile = 0;
+  int grid_spmm = 0, grid_update = 0, grid_pupd = 0;   // persistent CTAs per loop kernel
   Unit *units_small = nullptr;  // elementwise units
   int n_units_small = 0;
   // host staging (pinned)
@@ -671,22 +761,25 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
   };
   int m = 0;
   mark(m++);
-  spmm_gram_kernel<T, S><<<ws->n_units, 256, spmm_smem<T, S>(), st>>>(
-      ws->units, op->d_chips, g, (const T *)ws->P, (const T *)ws->R, (T *)ws->Q, sa);
+  const UnitSched us_s{ws->units, ws->n_units, ws->chip_unit_end, ws->work};
+  const UnitSched us_u{ws->units, ws->n_units, ws->chip_unit_end, ws->work + 2};
+  const UnitSched us_p{ws->units, ws->n_units, ws->chip_unit_end, ws->work + 4};
+  spmm_gram_kernel<T, S><<<ws->grid_spmm, 256, spmm_smem<T, S>(), st>>>(
+      us_s, op->d_chips, g, (const T *)ws->P, (const T *)ws->R, (T *)ws->Q, sa);
   if constexpr (CH) {
     mark(m++);
     chol_alpha_kernel<T, S><<<ws->n_chips * S, 256, chol_smem_bytes<S>(), st>>>(sa);
   }
   mark(m++);
-  update_gram_kernel<T, S, PC><<<ws->n_units, 256, update_smem<T, S>(), st>>>(
-      ws->units, (const T *)ws->P, (const T *)ws->Q, (T *)ws->D, (T *)ws->R, dinv, sa);
+  update_gram_kernel<T, S, PC><<<ws->grid_update, 256, update_smem<T, S>(), st>>>(
+      us_u, (const T *)ws->P, (const T *)ws->Q, (T *)ws->D, (T *)ws->R, dinv, sa);
   if constexpr (CH) {
     mark(m++);
     chol_beta_kernel<T, S><<<ws->n_chips * S, 32, 0, st>>>(sa);
   }
   mark(m++);
-  p_update_kernel<T, S, PC><<<ws->n_units_tile, 256, pupdate_smem<T, S>(), st>>>(
-      ws->units_tile, ws->state, (const T *)ws->beta, (const T *)ws->R, (T *)ws->P, dinv);
+  p_update_kernel<T, S, PC><<<ws->grid_pupd, 256, pupdate_smem<T, S>(), st>>>(
+      us_p, ws->state, (const T *)ws->beta, (const T *)ws->R, (T *)ws->P, dinv);
   mark(m++);
 }
 
@@ -730,27 +823,45 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     BLOCKOA_CUDA(ws_alloc(ws, &ws->rank, sizeof(int) * (size_t)nc));
     BLOCKOA_CUDA(ws_alloc(ws, &ws->outer_active, sizeof(int) * (size_t)nc));
     BLOCKOA_CUDA(ws_alloc(ws, &ws->state, sizeof(ChipSolveState) * (size_t)nc));
-    // loop units: about two CTAs per SM over all chips, whole tiles
+    // loop units: 1-8 whole tiles of one chip, about 16 per persistent CTA
     using G = BK<T, S>;
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, op->device);
-    long long cells = pick_unit_cells(op, G::TC, 2 * G::TC, 3 * nsm);
-    std::vector<Unit> units = make_units(op, cells);
+    set_smem_limits<T, S, false>();
+    set_smem_limits<T, S, true>();
+    int occ_s = 1, occ_u = 1, occ_p = 1;
+    BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, spmm_gram_kernel<T, S>, 256,
+                                                               spmm_smem<T, S>()));
+    BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, update_gram_kernel<T, S, true>, 256,
+                                                               update_smem<T, S>()));
+    BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, p_update_kernel<T, S, true>, 256,
+                                                               pupdate_smem<T, S>()));
+    long long tiles = 0;
+    for (const ChipDev &cd : op->chips) tiles += (cd.n + G::TC - 1) / G::TC;
+    long long tpu = tiles / (16LL * std::max(occ_s, 1) * nsm);
+    tpu = std::min<long long>(std::max<long long>(tpu, 1), 8);
+    std::vector<Unit> units = make_units(op, tpu * G::TC);
     ws->n_units = (int)units.size();
     {
-      std::vector<int> cnt(nc, 0);
-      for (const Unit &uu : units) cnt[uu.chip] += 1;
+      std::vector<int> cnt(nc, 0), uend(nc, 0);
+      for (size_t i = 0; i < units.size(); ++i) {
+        cnt[units[i].chip] += 1;
+        uend[units[i].chip] = (int)i + 1;
+      }
       BLOCKOA_CUDA(ws_alloc(ws, &ws->unit_count, sizeof(int) * (size_t)nc));
       BLOCKOA_CUDA(cudaMemcpy(ws->unit_count, cnt.data(), sizeof(int) * (size_t)nc, cudaMemcpyHostToDevice));
+      BLOCKOA_CUDA(ws_alloc(ws, &ws->chip_unit_end, sizeof(int) * (size_t)nc));
+      BLOCKOA_CUDA(cudaMemcpy(ws->chip_unit_end, uend.data(), sizeof(int) * (size_t)nc, cudaMemcpyHostToDevice));
       BLOCKOA_CUDA(ws_alloc(ws, &ws->ticket, sizeof(int) * 2 * (size_t)nc));
       BLOCKOA_CUDA(cudaMemset(ws->ticket, 0, sizeof(int) * 2 * (size_t)nc));
+      BLOCKOA_CUDA(ws_alloc(ws, &ws->work, sizeof(int) * 6));
+      BLOCKOA_CUDA(cudaMemset(ws->work, 0, sizeof(int) * 6));
     }
     BLOCKOA_CUDA(ws_alloc(ws, &ws->units, sizeof(Unit) * units.size()));
     BLOCKOA_CUDA(cudaMemcpy(ws->units, units.data(), sizeof(Unit) * units.size(), cudaMemcpyHostToDevice));
-    std::vector<Unit> ut = make_units(op, G::TC);
-    ws->n_units_tile = (int)ut.size();
-    BLOCKOA_CUDA(ws_alloc(ws, &ws->units_tile, sizeof(Unit) * ut.size()));
-    BLOCKOA_CUDA(cudaMemcpy(ws->units_tile, ut.data(), sizeof(Unit) * ut.size(), cudaMemcpyHostToDevice));
+    ws->grid_spmm = (int)std::min<long long>(ws->n_units, (long long)std::max(occ_s, 1) * nsm);
+    ws->grid_update = (int)std::min<long long>(ws->n_units, (long long)std::max(occ_u, 1) * nsm);
+    ws->grid_pupd = (int)std::min<long long>(ws->n_units, (long long)std::max(occ_p, 1) * nsm);
     std::vector<Unit> us = make_units(op, 2048);
     ws->n_units_small = (int)us.size();
     BLOCKOA_CUDA(ws_alloc(ws, &ws->units_small, sizeof(Unit) * us.size()));
@@ -899,6 +1010,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       BLOCKOA_CUDA(cudaMemsetAsync(ws->wg, 0, sm, st));
       BLOCKOA_CUDA(cudaMemsetAsync(ws->rn2, 0, sv, st));
       BLOCKOA_CUDA(cudaMemsetAsync(ws->ticket, 0, sizeof(int) * 2 * (size_t)nc, st));
+      BLOCKOA_CUDA(cudaMemsetAsync(ws->work, 0, sizeof(int) * 6, st));
     }
     g_launches += 2;
     {

@@ -56,8 +56,8 @@ struct SmallArgs {
   int *perm;        // [chip][S] float64 form: kept columns in pivot order
   void *alpha;      // [chip][S][S] in the loop's precision
   void *beta;       // [chip][S][S]
-  int *ticket;      // [2][chip] CTA completion counters of the two Gram kernels (zero between launches)
-  const int *unit_count;  // [chip] CTAs per chip of the Gram kernels
+  int *ticket;      // [2][chip] flushed-unit counters of the two Gram kernels (zero between launches)
+  const int *unit_count;  // [chip] units per chip of the loop kernels
   int n_chips;
   int tail;         // 1: the Gram kernels' last CTAs solve (mixed form, sweep)
   int s;            // caller's columns (for deflation counts)
@@ -215,17 +215,18 @@ struct SweepSmem {
 template <typename R, int S>
 constexpr size_t small_smem_bytes() { return sizeof(SweepSmem<R, S>); }
 
-// True in the CTA that finishes last among the `count` CTAs of a chip.  Every
-// thread fences its own accumulator updates, then one thread takes a ticket;
-// the last CTA resets the counter for the next launch and fences again
-// before it reads the accumulators.
-__device__ __forceinline__ bool last_cta_of_chip(int *ticket, int count) {
+// True in the CTA whose flush completes a chip: each flush covers `done`
+// of the chip's `count` units.  Every thread fences its own accumulator
+// updates, then one thread adds the flush's units to the chip's ticket; the
+// flush that reaches `count` resets the ticket for the next launch and
+// fences again before its CTA reads the accumulators.
+__device__ __forceinline__ bool last_flush_of_chip(int *ticket, int done, int count) {
   __shared__ int s_last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int prev = atomicAdd(ticket, 1);
-    s_last = prev == count - 1;
+    const int prev = atomicAdd(ticket, done);
+    s_last = prev + done == count;
     if (s_last) *ticket = 0;
   }
   __syncthreads();
