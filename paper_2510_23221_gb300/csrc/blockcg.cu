@@ -419,8 +419,10 @@ __device__ __forceinline__ void update_flush(const T *aw, const T *rn, double *r
 }
 
 // X += P alpha, R -= Q alpha; W += Q^T Z_new and rn2 += ||R_new_j||^2.
+// Two CTAs per SM: the persistent loop keeps the Gram and norm partials of
+// the running chip live across units, which does not fit 80 registers.
 template <typename T, int S, bool PC>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(256, 2)
 update_gram_kernel(const UnitSched us, const T *__restrict__ P, const T *__restrict__ Q,
                    T *__restrict__ X, T *__restrict__ R, const T *__restrict__ dinv, const SmallArgs A) {
   using G = BK<T, S>;
@@ -518,7 +520,7 @@ update_gram_kernel(const UnitSched us, const T *__restrict__ P, const T *__restr
 
 // P = Z + P beta, Z = R or D^-1 R.
 template <typename T, int S, bool PC>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 p_update_kernel(const UnitSched us, const ChipSolveState *__restrict__ state, const T *__restrict__ beta,
                 const T *__restrict__ R, T *__restrict__ P, const T *__restrict__ dinv) {
   using G = BK<T, S>;
