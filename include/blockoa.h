@@ -252,6 +252,80 @@ const char *blockoa_status_string(int status);
 /* Text of the last CUDA error seen by the calling thread ("" if none). */
 const char *blockoa_last_error(void);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start: a 3-D Fourier neural operator that maps per-cell
+ * inputs of one chip shape (e.g. normalised log k, power density and cell
+ * coordinates) to a predicted basis solution, used as the initial guess of
+ * block CG (blockoa_solve_opts.x0).  The paper trains neural operators on
+ * data the method generates (Sec. IV); the network follows the FNO
+ * literature:
+ *   v0 = P x + bP;  u_l = K_l(v_l) + W_l v_l + b_l,  v_{l+1} = gelu(u_l)
+ *   (no gelu after the last layer);  y = Q2 gelu(Q1 v_L + c1) + c2,
+ * K_l the spectral convolution over the retained modes kx in [-mx/2, mx/2),
+ * ky in [-my/2, my/2), kz in [0, mz) with complex per-mode channel mixing:
+ *   Yh_m = Xh_m R_m,  K(v) = 1/(nx ny nz) sum_m w_m Re(Yh_m e^{+i theta_m}),
+ *   w_m = 1 for kz = 0 and 2 otherwise.
+ * Weight matrices are used as bfloat16 copies of float32 masters; all
+ * arithmetic is float32.
+ *
+ * Parameters are one float32 array in this order:
+ *   P [width][c_in], bP [width], W [layers][width][width], b [layers][width],
+ *   Rr, Ri [layers][mz*my*mx][width][width] (R[mode][in][out]; mode = (kz, ky, kx)
+ *   row-major with kx fastest), Q1 [hidden][width], c1 [hidden], Q2 [hidden], c2 [1].
+ * Gradients use the same layout.
+ * ------------------------------------------------------------------------ */
+typedef struct blockoa_fno blockoa_fno;
+
+typedef struct {
+  int nx, ny, nz;          /* grid of every sample */
+  int c_in;                /* input channels per cell, 1..8 */
+  int width;               /* 32 */
+  int hidden;              /* projection width, 128 */
+  int layers;              /* Fourier layers, >= 1 */
+  int mx, my, mz;          /* retained modes (even mx, my; mx <= nx, my <= ny, mz <= nz) */
+  int max_batch;           /* samples per forward / backward call, >= 1 */
+} blockoa_fno_shape;
+
+/* Number of float32 parameters of a shape (host output).  ERR_INVALID for
+ * an unsupported shape (width must be 32; hidden 32..256, a multiple of 32). */
+int blockoa_fno_param_count(const blockoa_fno_shape *shape, int64_t *count);
+
+/* Create a network with the given initial parameters (host float32 array of
+ * blockoa_fno_param_count entries, read before return), zero gradients and
+ * zero Adam moments.  Allocates its activations for max_batch samples. */
+int blockoa_fno_create(const blockoa_fno_shape *shape, const float *params, blockoa_fno **out);
+
+/* y = net(x).  x: device float32 [batch][nz][ny][nx][c_in]; y: device
+ * float32 [batch][nz][ny][nx].  keep = 1 keeps the activations for
+ * blockoa_fno_backward. */
+int blockoa_fno_forward(blockoa_fno *net, const float *x, float *y, int batch, int keep,
+                        blockoa_stream stream);
+
+/* Mean squared error of y against target over batch samples, and its
+ * gradient dy = 2 (y - target) / (batch nx ny nz).  loss: device float32 [1]
+ * (overwritten); dy: device float32 like y. */
+int blockoa_fno_mse(const blockoa_fno *net, const float *y, const float *target, int batch, float *dy,
+                    float *loss, blockoa_stream stream);
+
+/* Accumulate into the gradients the gradient of sum(dy * y) for the last
+ * forward call made with keep = 1 (same batch). */
+int blockoa_fno_backward(blockoa_fno *net, const float *dy, int batch, blockoa_stream stream);
+
+/* Zero the gradients. */
+int blockoa_fno_zero_grad(blockoa_fno *net, blockoa_stream stream);
+
+/* One Adam step (Kingma & Ba, Algorithm 1; t counts from 1) on all
+ * parameters from the accumulated gradients; refreshes the bfloat16 copies. */
+int blockoa_fno_adam_step(blockoa_fno *net, float lr, float beta1, float beta2, float eps, int t,
+                          blockoa_stream stream);
+
+/* Copy the float32 parameters or gradients to a host array.  Synchronous. */
+int blockoa_fno_get_params(const blockoa_fno *net, float *params);
+int blockoa_fno_get_grads(const blockoa_fno *net, float *grads);
+
+/* Free the network (NULL is a no-op).  Synchronises the device. */
+void blockoa_fno_destroy(blockoa_fno *net);
+
 #ifdef __cplusplus
 }
 #endif
