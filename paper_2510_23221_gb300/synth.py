@@ -195,6 +195,19 @@ def batched_workload(n_chips: int = 256, s: int = 16, M: int = 20,
     return Workload(f"batch{n_chips}_s{s}_M{M}", chips, dens, Cs, s=s, M=M, rtol=rtol)
 
 
+FNO_TRAIN_SEED0 = 10_000_000      # training chips of the warm-start network
+FNO_HELDOUT_SEED0 = 20_000_000    # held-out evaluation chips (disjoint seeds)
+
+
+def warm_start_chip(seed: int, nx: int = 128, ny: int = 128, n_layers: int = 8, s: int = 32):
+    """One chip of the benchmark chip's distribution (8 layers, k log-uniform
+    in [1, 400], top h = 1e4, s mixed rectangle/hotspot maps) from its own
+    seed: (chip, density [s][ny][nx])."""
+    rng = np.random.default_rng(seed)
+    chip = _layered_chip(rng, nx, ny, n_layers, 1e4)
+    return chip, power_maps(rng, nx, ny, s, mix=True)
+
+
 def large_chip_workload(M: int = 10000, s: int = 64) -> Workload:
     """512x512x16 chip, 16 log-uniform layers, s=64, M fields."""
     return single_chip_workload(512, 512, 16, s=s, M=M, cfg=5,
