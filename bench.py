@@ -3,7 +3,7 @@
 
 One step = the whole hot path on one synthetic chip (128 x 128 x 8 cells,
 8 layers, s = 32 power maps, M = 5000 fields): assemble, right-hand sides,
-Jacobi-preconditioned mixed-precision block CG to a float64 relative
+z-line-preconditioned mixed-precision block CG to a float64 relative
 residual of 1e-6, bfloat16x3
 tensor-core combination T = U C, operator action q = A T.  Inputs (power
 maps and coefficients) are resident on the device when timing starts; L2 is
@@ -208,7 +208,7 @@ def run_ours(args):
     e_pair = torch.empty(M, dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    CHOSEN_PRECOND = bo.PRECOND_JACOBI
+    CHOSEN_PRECOND = bo.PRECOND_ZLINE
 
     def step(precision, Tb, qb, precond=CHOSEN_PRECOND):
         op = bo.assemble(w.chips)
@@ -348,7 +348,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": w.name, "cells": n, "s": s, "M": M, "precision": "mixed",
-                       "precond": "jacobi", "plain_fp64_precond": "none",
+                       "precond": "zline", "plain_fp64_precond": "none",
                        "rtol": RTOL, "pair_tol": PAIR_TOL,
                        "l2": "flushed between steps (512 MB write, outside timed events)",
                        "parallelism": f"replicas x{world}"},

@@ -82,12 +82,14 @@ typedef struct {
   double deflate_tol;   /* pivot threshold on the scaled Gram (<= 0: 1e-14 FP64, 1e-6 float32 inner) */
   const double *x0;     /* device [n_total][s] initial guess, or NULL for zero */
   int check_every;      /* block iterations between convergence polls by the host (<= 0: 8) */
-  int precond;          /* BLOCKOA_PRECOND_NONE (the paper's unpreconditioned block CG) or
-                           BLOCKOA_PRECOND_JACOBI (diagonal: directions from D^-1 R) */
+  int precond;          /* BLOCKOA_PRECOND_NONE (the paper's unpreconditioned block CG),
+                           BLOCKOA_PRECOND_JACOBI (diagonal: directions from D^-1 R) or
+                           BLOCKOA_PRECOND_ZLINE (z-line: directions from M^-1 R, M the
+                           tridiagonal coupling of each (x, y) cell column) */
   int small_solve;      /* BLOCKOA_SMALL_AUTO or BLOCKOA_SMALL_FP64_CHOLESKY (below) */
 } blockoa_solve_opts;
 
-enum { BLOCKOA_PRECOND_NONE = 0, BLOCKOA_PRECOND_JACOBI = 1 };
+enum { BLOCKOA_PRECOND_NONE = 0, BLOCKOA_PRECOND_JACOBI = 1, BLOCKOA_PRECOND_ZLINE = 2 };
 
 /*
  * How the s x s systems Gamma alpha = rho and Gamma beta = -W are solved:
@@ -148,7 +150,11 @@ int blockoa_build_rhs(const blockoa_operator *op, const double *density, double 
  * Gamma with deflation of pivots <= deflate_tol; alpha = Gamma^-1 P^T R;
  * X += P alpha; R -= Q alpha; beta = -Gamma^-1 Q^T R; P = R + P beta.
  * With BLOCKOA_PRECOND_JACOBI, Z = D^-1 R (D = diag(A)) replaces R in the
- * new directions: beta = -Gamma^-1 Q^T Z, P = Z + P beta (same solution).
+ * new directions: beta = -Gamma^-1 Q^T Z, P = Z + P beta (same solution);
+ * with BLOCKOA_PRECOND_ZLINE, Z = M^-1 R with M the part of A that couples
+ * the cells of one (x, y) column (solved by the Thomas recurrences per
+ * column); it needs every chip's nz <= the solver's tile (64 cells for
+ * s > 32, more for smaller s) and returns ERR_INVALID otherwise.
  * MIXED runs that loop in float32 (Gram products accumulated to float64)
  * inside float64 iterative refinement on the true residual B - A X.
  * Stops when every column meets ||B_j - A X_j|| <= rtol ||B_j||.

@@ -28,6 +28,7 @@ FP64 = 0
 MIXED = 1
 PRECOND_NONE = 0
 PRECOND_JACOBI = 1
+PRECOND_ZLINE = 2
 SMALL_AUTO = 0
 SMALL_FP64_CHOLESKY = 1
 

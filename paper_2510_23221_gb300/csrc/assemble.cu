@@ -5,6 +5,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace blockoa {
@@ -206,6 +208,44 @@ __global__ void inv_diag_kernel(const Unit *__restrict__ units, const ChipDev *_
   }
 }
 
+// z-line preconditioner factors: M is the part of A that couples cells of
+// one (x, y) column (the full diagonal and the vertical conductances), a
+// tridiagonal matrix per column.  One thread per column runs the Thomas
+// elimination and stores 1 / den_z, den_0 = d_0, den_z = d_z - e_z^2 / den_{z-1}
+// with e_z the conductance between z-1 and z (float64, same diagonal sum as
+// inv_diag_kernel).  M^-1 r is then, with f_z the conductance from z to z+1,
+//   w_z = (r_z + e_z w_{z-1}) / den_z,   x_z = w_z + f_z / den_z x_{z+1}.
+__global__ void zfactor_kernel(const ChipDev *__restrict__ chips, int n_chips, const double *__restrict__ g64,
+                               double *__restrict__ z64, float *__restrict__ z32) {
+  const int c = blockIdx.y;
+  if (c >= n_chips) return;
+  const ChipDev ch = chips[c];
+  const long long nxny = (long long)ch.nx * ch.ny;
+  const double4 *g = reinterpret_cast<const double4 *>(g64);
+  for (long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x; col < nxny;
+       col += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(col % ch.nx), y = (int)(col / ch.nx);
+    double den_prev = 1.0;
+    for (int z = 0; z < ch.nz; ++z) {
+      const long long a = ch.off + z * nxny + col;
+      const double4 cf = g[a];
+      double d = cf.x + cf.y + cf.z + cf.w;
+      if (x > 0) d += g[a - 1].x;
+      if (y > 0) d += g[a - ch.nx].y;
+      double e = 0.0;
+      if (z > 0) {
+        e = g[a - nxny].z;
+        d += e;
+      }
+      const double den = z > 0 ? d - e * e / den_prev : d;
+      const double inv = den > 0.0 ? 1.0 / den : 0.0;
+      z64[a] = inv;
+      z32[a] = (float)inv;
+      den_prev = den;
+    }
+  }
+}
+
 // One thread per z-row of a layered chip: the row's interior face
 // conductances and the Robin conductance of every edge class, with the same
 // float64 operations (and order) as assemble_kernel.
@@ -373,6 +413,10 @@ extern "C" int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips,
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc dinv64"));
   e = cudaMalloc((void **)&op->dinv32, sizeof(float) * op->n_total);
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc dinv32"));
+  e = cudaMalloc((void **)&op->zinv64, sizeof(double) * op->n_total);
+  if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc zinv64"));
+  e = cudaMalloc((void **)&op->zinv32, sizeof(float) * op->n_total);
+  if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc zinv32"));
   e = cudaMalloc((void **)&op->lt64, sizeof(double) * kLT * zk.size());
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc lt64"));
   e = cudaMalloc((void **)&op->lt32, sizeof(float) * kLT * zk.size());
@@ -401,6 +445,13 @@ extern "C" int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips,
   g_launches += 2;
   inv_diag_kernel<<<(unsigned)units.size(), 256, 0, st>>>((const Unit *)d_units, op->d_chips, op->g64,
                                                           op->dinv64, op->dinv32);
+  {
+    long long maxcols = 1;
+    for (const ChipDev &cd : op->chips) maxcols = std::max<long long>(maxcols, (long long)cd.nx * cd.ny);
+    dim3 zg((unsigned)std::min<long long>((maxcols + 255) / 256, 1024), (unsigned)n_chips);
+    zfactor_kernel<<<zg, 256, 0, st>>>(op->d_chips, n_chips, op->g64, op->zinv64, op->zinv32);
+    g_launches += 1;
+  }
   layer_table_kernel<<<(unsigned)n_chips, 64, 0, st>>>(op->d_chips, (const ChipPhys *)d_phys,
                                                       (const double *)d_zk, (const double *)d_zdz,
                                                       n_chips, op->lt64, op->lt32);
@@ -499,6 +550,8 @@ extern "C" void blockoa_destroy(blockoa_operator *op) {
   if (op->g32) cudaFree(op->g32);
   if (op->dinv64) cudaFree(op->dinv64);
   if (op->dinv32) cudaFree(op->dinv32);
+  if (op->zinv64) cudaFree(op->zinv64);
+  if (op->zinv32) cudaFree(op->zinv32);
   if (op->lt64) cudaFree(op->lt64);
   if (op->lt32) cudaFree(op->lt32);
   cudaGetLastError();

@@ -418,10 +418,11 @@ __device__ __forceinline__ void update_flush(const T *aw, const T *rn, double *r
   __syncthreads();
 }
 
-// X += P alpha, R -= Q alpha; W += Q^T Z_new and rn2 += ||R_new_j||^2.
-// Two CTAs per SM: the persistent loop keeps the Gram and norm partials of
-// the running chip live across units, which does not fit 80 registers.
-template <typename T, int S, bool PC>
+// X += P alpha, R -= Q alpha; W += Q^T Z_new and rn2 += ||R_new_j||^2, with
+// Z = R (PCM 0) or D^-1 R (PCM 1).  Two CTAs per SM: the persistent loop
+// keeps the Gram and norm partials of the running chip live across units,
+// which does not fit 80 registers.
+template <typename T, int S, int PCM>
 __global__ void __launch_bounds__(256, 2)
 update_gram_kernel(const UnitSched us, const T *__restrict__ P, const T *__restrict__ Q,
                    T *__restrict__ X, T *__restrict__ R, const T *__restrict__ dinv, const SmallArgs A) {
@@ -500,7 +501,7 @@ update_gram_kernel(const UnitSched us, const T *__restrict__ P, const T *__restr
       for (int k = 0; k < 4; ++k)
 #pragma unroll
         for (int v = 0; v < V; ++v) rn[v] += rv[k][v] * rv[k][v];  // zero past the end
-      if constexpr (PC) {
+      if constexpr (PCM == 1) {
         // Gram with Z = D^-1 R_new (R stays unscaled in memory)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -518,11 +519,12 @@ update_gram_kernel(const UnitSched us, const T *__restrict__ P, const T *__restr
   sched_finish(us);
 }
 
-// P = Z + P beta, Z = R or D^-1 R.
-template <typename T, int S, bool PC>
+// P = Z + P beta, Z = R (PCM 0), D^-1 R (PCM 1) or the z-line Z stored by
+// the update kernel (PCM 2, read from Zb).
+template <typename T, int S, int PCM>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 p_update_kernel(const UnitSched us, const ChipSolveState *__restrict__ state, const T *__restrict__ beta,
-                const T *__restrict__ R, T *__restrict__ P, const T *__restrict__ dinv) {
+                const T *__restrict__ R, T *__restrict__ P, const T *__restrict__ dinv, const T *__restrict__ Zb) {
   using G = BK<T, S>;
   constexpr int V = G::V;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -548,8 +550,8 @@ p_update_kernel(const UnitSched us, const ChipSolveState *__restrict__ state, co
         put_tile<T, G::LD>(sP, pv, cl0, j0);
       }
       T rv[4][V];
-      load_block<T, S>(rv, R, base + cl0, u.end, j0);
-      if constexpr (PC) {
+      load_block<T, S>(rv, PCM == 2 ? Zb : R, base + cl0, u.end, j0);
+      if constexpr (PCM == 1) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const T di = base + cl0 + k < u.end ? dinv[base + cl0 + k] : T(0);
@@ -569,6 +571,238 @@ p_update_kernel(const UnitSched us, const ChipSolveState *__restrict__ state, co
           for (int v = 0; v < V; ++v) rv[k][v] += p4[k] * bv[v];
       }
       store_block<T, S>(P, rv, base + cl0, u.end, j0);
+      __syncthreads();
+    }
+  }
+  sched_finish(us);
+}
+
+// ---------------------------------------------------------------- z-line preconditioning
+// Z = M^-1 R with M the part of A that couples the cells of one (x, y)
+// column (tridiagonal in z), by the Thomas recurrences with the per-cell
+// factors 1/den_z of the assembly:
+//   w_z = (r_z + e_z w_{z-1}) / den_z,   z_z = w_z + f_z / den_z z_{z+1},
+// e_z = conductance (z-1, z), f_z = conductance (z, z+1).
+
+// Restart: Z = P = M^-1 R.  One thread per (chip column, 16 bytes of columns).
+template <typename T, int S>
+__global__ void zline_init_kernel(const ChipDev *__restrict__ chips, int n_chips, const int *__restrict__ outer_active,
+                                  const T *__restrict__ g, const T *__restrict__ zinv, const T *__restrict__ R,
+                                  T *__restrict__ P, T *__restrict__ Zb) {
+  constexpr int V = 16 / sizeof(T), NQ = S / V;
+  const int c = blockIdx.y;
+  if (c >= n_chips || !outer_active[c]) return;
+  const ChipDev ch = chips[c];
+  const long long nxny = (long long)ch.nx * ch.ny;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < nxny * NQ;
+       it += (long long)gridDim.x * blockDim.x) {
+    const long long col = it / NQ;
+    const int j0 = (int)(it % NQ) * V;
+    T w[V], prev[V];
+    for (int v = 0; v < V; ++v) prev[v] = T(0);
+    T e = T(0);
+    for (int z = 0; z < ch.nz; ++z) {   // forward: w_z -> Z (temporary)
+      const long long a = ch.off + z * nxny + col;
+      const T inv = zinv[a];
+      T r[V];
+      vload<T>(r, R + a * S + j0);
+#pragma unroll
+      for (int v = 0; v < V; ++v) w[v] = (r[v] + e * prev[v]) * inv;
+      vstore<T>(Zb + a * S + j0, w);
+#pragma unroll
+      for (int v = 0; v < V; ++v) prev[v] = w[v];
+      e = coef_ld(g, a).z;
+    }
+    for (int z = ch.nz - 2; z >= 0; --z) {   // backward, prev = z_{z+1}
+      const long long a = ch.off + z * nxny + col;
+      const T fz = coef_ld(g, a).z * zinv[a];
+      T ww[V];
+      vload<T>(ww, Zb + a * S + j0);
+#pragma unroll
+      for (int v = 0; v < V; ++v) prev[v] = ww[v] + fz * prev[v];
+      vstore<T>(Zb + a * S + j0, prev);
+    }
+    for (int z = 0; z < ch.nz; ++z) {
+      const long long a = ch.off + z * nxny + col;
+      T ww[V];
+      vload<T>(ww, Zb + a * S + j0);
+      vstore<T>(P + a * S + j0, ww);
+    }
+  }
+}
+
+// Column tiles of the z-line update: XT = TC / nz x positions of one y row,
+// all z; slot s = z XT + dx of a tile.
+struct ColGeom {
+  int xt, tiles_x;
+  __device__ __forceinline__ ColGeom(const ChipDev &ch, int tc) {
+    xt = tc / ch.nz;
+    tiles_x = (ch.nx + xt - 1) / xt;
+  }
+  // global cell of slot s in column tile c (-1 when the slot is outside the chip)
+  __device__ __forceinline__ long long cell(const ChipDev &ch, int c, int s) const {
+    const int z = s / xt, dx = s % xt;
+    const int y = c / tiles_x, x = (c % tiles_x) * xt + dx;
+    if (z >= ch.nz || x >= ch.nx) return -1;
+    return ch.off + (long long)z * ch.nx * ch.ny + (long long)y * ch.nx + x;
+  }
+};
+
+// The update kernel with z-line preconditioning: as update_gram, over column
+// tiles (units are ranges of column tiles of one chip).  After X and R are
+// updated the tile holds whole cell columns of R_new: the tridiagonal
+// solves run in shared memory (one thread per (column of the block, x
+// position)), Z is stored for the P update, and W += Q^T Z.
+template <typename T, int S>
+__global__ void __launch_bounds__(256, 2)
+update_zline_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T *__restrict__ g,
+                    const T *__restrict__ zinv, const T *__restrict__ P, const T *__restrict__ Q,
+                    T *__restrict__ X, T *__restrict__ R, T *__restrict__ Zb, const SmallArgs A) {
+  using G = BK<T, S>;
+  constexpr int V = G::V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *sP = reinterpret_cast<T *>(smem);
+  T *sQ = sP + S * G::LD;
+  T *sR = sQ + S * G::LD;
+  T *sA = sR + S * G::LD;
+  T *sE = sA + S * S;        // per slot: e (conductance to z-1), f / den, 1 / den
+  T *sF = sE + G::TC;
+  T *sI = sF + G::TC;
+  double *red = reinterpret_cast<double *>(smem);   // reused between units
+  __shared__ int s_unit;
+  const int t = threadIdx.x;
+  const int j0 = (t % G::TPR) * V, cl0 = (t / G::TPR) * 4;
+  const int grp = t / G::NT, w = t % G::NT;
+  const int i0 = (w / G::NB) * 4, k0 = (w % G::NB) * 4;
+  T aw[16], rn[V];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) aw[e] = T(0);
+#pragma unroll
+  for (int v = 0; v < V; ++v) rn[v] = T(0);
+  int cur = -1, run = 0;
+  for (;;) {
+    const int ui = next_unit(us, A.state, &s_unit);
+    const int chip = ui < us.n_units ? us.units[ui].chip : -1;
+    if (run > 0 && chip != cur) {
+      update_flush<T, S>(aw, rn, red, A, cur);
+      if constexpr (sizeof(T) == 4) {
+        if (A.tail && last_flush_of_chip(A.ticket + A.n_chips + cur, run, A.zunit_count[cur]))
+          chip_beta<T, S>(A, cur);
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) aw[e] = T(0);
+#pragma unroll
+      for (int v = 0; v < V; ++v) rn[v] = T(0);
+      run = 0;
+    }
+    if (ui >= us.n_units) break;
+    const Unit u = us.units[ui];
+    if (u.chip != cur) {
+      const T *al = reinterpret_cast<const T *>(A.alpha) + (long long)u.chip * S * S;
+      for (int e = t; e < S * S; e += 256) sA[e] = al[e];
+    }
+    cur = u.chip;
+    ++run;
+    const ChipDev ch = chips[u.chip];
+    const ColGeom cg(ch, G::TC);
+    for (long long ct = u.begin; ct < u.end; ++ct) {
+      long long cell[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cell[k] = cg.cell(ch, (int)ct, cl0 + k);
+      auto ld = [&](T (&x)[4][V], const T *src) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (cell[k] >= 0) vload<T>(x[k], src + cell[k] * S + j0);
+          else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) x[k][v] = T(0);
+          }
+        }
+      };
+      auto st = [&](T *dst, const T (&x)[4][V]) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (cell[k] >= 0) vstore<T>(dst + cell[k] * S + j0, x[k]);
+      };
+      {
+        T pv[4][V], qv[4][V];
+        ld(pv, P);
+        ld(qv, Q);
+        put_tile<T, G::LD>(sP, pv, cl0, j0);
+        put_tile<T, G::LD>(sQ, qv, cl0, j0);
+      }
+      // the tridiagonal factors of the tile's slots
+      for (int sl = t; sl < G::TC; sl += 256) {
+        const long long a = cg.cell(ch, (int)ct, sl);
+        T e = T(0), f = T(0), iv = T(0);
+        if (a >= 0) {
+          const int z = sl / cg.xt;
+          iv = zinv[a];
+          f = coef_ld(g, a).z * iv;
+          if (z > 0) e = coef_ld(g, a - (long long)ch.nx * ch.ny).z;
+        }
+        sE[sl] = e;
+        sF[sl] = f;
+        sI[sl] = iv;
+      }
+      T xv[4][V], rv[4][V];
+      ld(xv, X);
+      ld(rv, R);
+      __syncthreads();
+#pragma unroll 4
+      for (int i = 0; i < S; ++i) {
+        T p4[4], q4[4], av[V];
+        ld4<T, G::LD>(p4, sP, i, cl0);
+        ld4<T, G::LD>(q4, sQ, i, cl0);
+        vload<T>(av, sA + i * S + j0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            xv[k][v] += p4[k] * av[v];
+            rv[k][v] -= q4[k] * av[v];
+          }
+      }
+      st(X, xv);
+      st(R, rv);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int v = 0; v < V; ++v) rn[v] += rv[k][v] * rv[k][v];  // zero outside the chip
+      put_tile<T, G::LD>(sR, rv, cl0, j0);
+      __syncthreads();
+      // Z = M^-1 R_new in place, one thread per (block column j, x position dx)
+      const int nz = ch.nz, xt = cg.xt;
+      for (int pr = t; pr < S * xt; pr += 256) {
+        const int j = pr / xt, dx = pr % xt;
+        T* row = sR + j * G::LD;
+        T prev = T(0);
+        for (int z = 0; z < nz; ++z) {
+          const int sl = z * xt + dx;
+          T &val = row[swz<T>(j, sl)];
+          prev = (val + sE[sl] * prev) * sI[sl];
+          val = prev;
+        }
+        for (int z = nz - 2; z >= 0; --z) {
+          const int sl = z * xt + dx;
+          T &val = row[swz<T>(j, sl)];
+          prev = val + sF[sl] * prev;
+          val = prev;
+        }
+      }
+      __syncthreads();
+      {   // store Z (this thread's slots, read back from the transposed tile)
+        T zv[4][V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          T z4[4];
+          ld4<T, G::LD>(z4, sR, j0 + v, cl0);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) zv[k][v] = z4[k];
+        }
+        st(Zb, zv);
+      }
+      gram_tile<T, S>(aw, sQ, sR, i0, k0, grp);
       __syncthreads();
     }
   }
@@ -621,7 +855,7 @@ __global__ void col_norms_kernel(const Unit *__restrict__ units, const double *_
 }
 
 // Start an inner solve on A D = R64: R = R64 / sigma_j, P = R, D = 0.
-template <typename T, int S, bool PC>
+template <typename T, int S, int PCM>
 __global__ void inner_init_kernel(const Unit *__restrict__ units, const int *__restrict__ outer_active,
                                   const double *__restrict__ R64, const double *__restrict__ inv_sigma,
                                   T *__restrict__ R, T *__restrict__ P, T *__restrict__ D,
@@ -632,7 +866,7 @@ __global__ void inner_init_kernel(const Unit *__restrict__ units, const int *__r
   for (long long i = u.begin * S + threadIdx.x; i < u.end * S; i += blockDim.x) {
     const T v = (T)(R64[i] * is[i % S]);
     R[i] = v;
-    P[i] = PC ? v * dinv[i / S] : v;
+    P[i] = PCM == 1 ? v * dinv[i / S] : v;   // z-line: zline_init_kernel follows
     D[i] = T(0);
   }
 }
@@ -681,6 +915,11 @@ struct SolveWS {
   Unit *units = nullptr;        // loop units (contiguous per chip)
   int n_units = 0;
   int grid_spmm = 0, grid_update = 0, grid_pupd = 0;   // persistent CTAs per loop kernel
+  Unit *zunits = nullptr;       // column-tile units of the z-line update
+  int n_zunits = 0, grid_zupdate = 0;
+  int *zunit_count = nullptr, *zchip_unit_end = nullptr;
+  bool zline_ok = false;        // every chip has nz <= TC
+  void *Zb = nullptr;           // z-line Z = M^-1 R in the loop's precision
   Unit *units_small = nullptr;  // elementwise units
   int n_units_small = 0;
   // host staging (pinned)
@@ -734,17 +973,25 @@ constexpr size_t update_smem() {
 }
 template <typename T, int S>
 constexpr size_t pupdate_smem() { return tile_bytes<T, S>() + S * S * sizeof(T); }
+template <typename T, int S>
+constexpr size_t zupdate_smem() {
+  return cmax(update_smem<T, S>(), 3 * tile_bytes<T, S>() + S * S * sizeof(T) + 3 * BK<T, S>::TC * sizeof(T));
+}
 
-template <typename T, int S, bool PC>
+template <typename T, int S, int PCM>
 static void set_smem_limits() {
   static bool done = false;
   if (done) return;
   done = true;
   cudaFuncSetAttribute(spmm_gram_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)spmm_smem<T, S>());
-  cudaFuncSetAttribute(update_gram_kernel<T, S, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)update_smem<T, S>());
-  cudaFuncSetAttribute(p_update_kernel<T, S, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if constexpr (PCM == 2)
+    cudaFuncSetAttribute(update_zline_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)zupdate_smem<T, S>());
+  else
+    cudaFuncSetAttribute(update_gram_kernel<T, S, PCM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)update_smem<T, S>());
+  cudaFuncSetAttribute(p_update_kernel<T, S, PCM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pupdate_smem<T, S>());
   cudaFuncSetAttribute(chol_alpha_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)chol_smem_bytes<S>());
@@ -752,7 +999,7 @@ static void set_smem_limits() {
 
 // One block-CG iteration for every active chip; with `ev`, an event is
 // recorded before each kernel and after the last (for live timing).
-template <typename T, int S, bool PC, bool CH>
+template <typename T, int S, int PCM, bool CH>
 static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const SmallArgs &sa,
                              cudaStream_t st, cudaEvent_t *ev) {
   const T *g = sizeof(T) == 4 ? (const T *)op->g32 : (const T *)op->g64;
@@ -773,15 +1020,22 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
     chol_alpha_kernel<T, S><<<ws->n_chips * S, 256, chol_smem_bytes<S>(), st>>>(sa);
   }
   mark(m++);
-  update_gram_kernel<T, S, PC><<<ws->grid_update, 256, update_smem<T, S>(), st>>>(
-      us_u, (const T *)ws->P, (const T *)ws->Q, (T *)ws->D, (T *)ws->R, dinv, sa);
+  if constexpr (PCM == 2) {
+    const UnitSched us_z{ws->zunits, ws->n_zunits, ws->zchip_unit_end, ws->work + 2};
+    const T *zinv = sizeof(T) == 4 ? (const T *)op->zinv32 : (const T *)op->zinv64;
+    update_zline_kernel<T, S><<<ws->grid_zupdate, 256, zupdate_smem<T, S>(), st>>>(
+        us_z, op->d_chips, g, zinv, (const T *)ws->P, (const T *)ws->Q, (T *)ws->D, (T *)ws->R, (T *)ws->Zb, sa);
+  } else {
+    update_gram_kernel<T, S, PCM><<<ws->grid_update, 256, update_smem<T, S>(), st>>>(
+        us_u, (const T *)ws->P, (const T *)ws->Q, (T *)ws->D, (T *)ws->R, dinv, sa);
+  }
   if constexpr (CH) {
     mark(m++);
     chol_beta_kernel<T, S><<<ws->n_chips * S, 32, 0, st>>>(sa);
   }
   mark(m++);
-  p_update_kernel<T, S, PC><<<ws->grid_pupd, 256, pupdate_smem<T, S>(), st>>>(
-      us_p, ws->state, (const T *)ws->beta, (const T *)ws->R, (T *)ws->P, dinv);
+  p_update_kernel<T, S, PCM><<<ws->grid_pupd, 256, pupdate_smem<T, S>(), st>>>(
+      us_p, ws->state, (const T *)ws->beta, (const T *)ws->R, (T *)ws->P, dinv, (const T *)ws->Zb);
   mark(m++);
 }
 
@@ -829,15 +1083,18 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     using G = BK<T, S>;
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, op->device);
-    set_smem_limits<T, S, false>();
-    set_smem_limits<T, S, true>();
-    int occ_s = 1, occ_u = 1, occ_p = 1;
+    set_smem_limits<T, S, 0>();
+    set_smem_limits<T, S, 1>();
+    set_smem_limits<T, S, 2>();
+    int occ_s = 1, occ_u = 1, occ_p = 1, occ_z = 1;
     BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, spmm_gram_kernel<T, S>, 256,
                                                                spmm_smem<T, S>()));
-    BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, update_gram_kernel<T, S, true>, 256,
+    BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, update_gram_kernel<T, S, 1>, 256,
                                                                update_smem<T, S>()));
-    BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, p_update_kernel<T, S, true>, 256,
+    BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, p_update_kernel<T, S, 1>, 256,
                                                                pupdate_smem<T, S>()));
+    BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_z, update_zline_kernel<T, S>, 256,
+                                                               zupdate_smem<T, S>()));
     long long tiles = 0;
     for (const ChipDev &cd : op->chips) tiles += (cd.n + G::TC - 1) / G::TC;
     long long tpu = tiles / (16LL * std::max(occ_s, 1) * nsm);
@@ -861,6 +1118,43 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     }
     BLOCKOA_CUDA(ws_alloc(ws, &ws->units, sizeof(Unit) * units.size()));
     BLOCKOA_CUDA(cudaMemcpy(ws->units, units.data(), sizeof(Unit) * units.size(), cudaMemcpyHostToDevice));
+    {   // column-tile units of the z-line update (chips with nz <= TC)
+      std::vector<Unit> zu;
+      std::vector<int> zcnt(nc, 0), zend(nc, 0);
+      long long ztiles = 0;
+      for (const ChipDev &cd : op->chips)
+        if (cd.nz <= G::TC) ztiles += (long long)cd.ny * ((cd.nx + G::TC / cd.nz - 1) / (G::TC / cd.nz));
+      long long ztpu = ztiles / (16LL * std::max(occ_z, 1) * nsm);
+      ztpu = std::min<long long>(std::max<long long>(ztpu, 1), 8);
+      for (int c = 0; c < nc; ++c) {
+        const ChipDev &cd = op->chips[c];
+        if (cd.nz > G::TC) continue;   // no z-line units: such chips cannot use PRECOND_ZLINE
+        const int xt = G::TC / cd.nz;
+        const long long nt = (long long)cd.ny * ((cd.nx + xt - 1) / xt);
+        for (long long b = 0; b < nt; b += ztpu) {
+          Unit zz;
+          zz.chip = c;
+          zz.pad = 0;
+          zz.begin = b;
+          zz.end = std::min(nt, b + ztpu);
+          zu.push_back(zz);
+          zcnt[c] += 1;
+          zend[c] = (int)zu.size();
+        }
+      }
+      ws->n_zunits = (int)zu.size();
+      ws->zline_ok = true;
+      for (const ChipDev &cd : op->chips) ws->zline_ok = ws->zline_ok && cd.nz <= G::TC;
+      BLOCKOA_CUDA(ws_alloc(ws, &ws->zunits, sizeof(Unit) * std::max<size_t>(zu.size(), 1)));
+      if (!zu.empty())
+        BLOCKOA_CUDA(cudaMemcpy(ws->zunits, zu.data(), sizeof(Unit) * zu.size(), cudaMemcpyHostToDevice));
+      BLOCKOA_CUDA(ws_alloc(ws, &ws->zunit_count, sizeof(int) * (size_t)nc));
+      BLOCKOA_CUDA(cudaMemcpy(ws->zunit_count, zcnt.data(), sizeof(int) * (size_t)nc, cudaMemcpyHostToDevice));
+      BLOCKOA_CUDA(ws_alloc(ws, &ws->zchip_unit_end, sizeof(int) * (size_t)nc));
+      BLOCKOA_CUDA(cudaMemcpy(ws->zchip_unit_end, zend.data(), sizeof(int) * (size_t)nc, cudaMemcpyHostToDevice));
+      ws->grid_zupdate = (int)std::max<long long>(1, std::min<long long>(ws->n_zunits, (long long)std::max(occ_z, 1) * nsm));
+      BLOCKOA_CUDA(ws_alloc(ws, &ws->Zb, sizeof(T) * (size_t)n * S));
+    }
     ws->grid_spmm = (int)std::min<long long>(ws->n_units, (long long)std::max(occ_s, 1) * nsm);
     ws->grid_update = (int)std::min<long long>(ws->n_units, (long long)std::max(occ_u, 1) * nsm);
     ws->grid_pupd = (int)std::min<long long>(ws->n_units, (long long)std::max(occ_p, 1) * nsm);
@@ -878,8 +1172,6 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     BLOCKOA_CUDA(cudaMemset(ws->rn2, 0, sv));
     BLOCKOA_CUDA(cudaMemset(ws->ginv, 0, sm));
     BLOCKOA_CUDA(cudaMemset(ws->rank, 0, sizeof(int) * (size_t)nc));
-    set_smem_limits<T, S, false>();
-    set_smem_limits<T, S, true>();
   }
 
   const double rtol = o->rtol;
@@ -888,7 +1180,11 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
   const int max_refine = o->max_refine > 0 ? o->max_refine : 12;
   const double tol = o->deflate_tol > 0 ? o->deflate_tol : (prec == BLOCKOA_MIXED ? 1e-6 : 1e-14);
   const int check_every = o->check_every > 0 ? o->check_every : 8;
-  const int pc = o->precond == BLOCKOA_PRECOND_JACOBI ? 1 : 0;
+  const int pc = o->precond == BLOCKOA_PRECOND_JACOBI ? 1 : (o->precond == BLOCKOA_PRECOND_ZLINE ? 2 : 0);
+  if (pc == 2 && !ws->zline_ok) {
+    set_last_error(cudaErrorInvalidValue, "block_solve: PRECOND_ZLINE needs nz <= the tile cells of every chip");
+    return BLOCKOA_ERR_INVALID;
+  }
   // the float64 form always factors by Cholesky in kernels of their own
   const bool ch = prec == BLOCKOA_FP64 || o->small_solve == BLOCKOA_SMALL_FP64_CHOLESKY;
 
@@ -897,7 +1193,8 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
   sa.target2 = ws->target2; sa.ginv = ws->ginv; sa.dsc = ws->dsc; sa.rank = ws->rank;
   sa.rinv = ws->rinv; sa.perm = ws->perm;
   sa.alpha = ws->alpha; sa.beta = ws->beta;
-  sa.ticket = ws->ticket; sa.unit_count = ws->unit_count; sa.n_chips = nc; sa.tail = ch ? 0 : 1;
+  sa.ticket = ws->ticket; sa.unit_count = ws->unit_count; sa.zunit_count = ws->zunit_count;
+  sa.n_chips = nc; sa.tail = ch ? 0 : 1;
   sa.s = s; sa.maxiter = maxiter; sa.tol = tol;
 
   // Build (or reuse) the graph of `check_every` iterations.
@@ -911,11 +1208,13 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     for (int k = 0; k < check_every; ++k) {
       cudaEvent_t *ev = k == 0 ? ws->tev : nullptr;
       if (ch) {
-        if (pc) launch_iteration<T, S, true, true>(op, ws, sa, ws->cap, ev);
-        else launch_iteration<T, S, false, true>(op, ws, sa, ws->cap, ev);
+        if (pc == 1) launch_iteration<T, S, 1, true>(op, ws, sa, ws->cap, ev);
+        else if (pc == 2) launch_iteration<T, S, 2, true>(op, ws, sa, ws->cap, ev);
+        else launch_iteration<T, S, 0, true>(op, ws, sa, ws->cap, ev);
       } else if constexpr (sizeof(T) == 4) {
-        if (pc) launch_iteration<T, S, true, false>(op, ws, sa, ws->cap, ev);
-        else launch_iteration<T, S, false, false>(op, ws, sa, ws->cap, ev);
+        if (pc == 1) launch_iteration<T, S, 1, false>(op, ws, sa, ws->cap, ev);
+        else if (pc == 2) launch_iteration<T, S, 2, false>(op, ws, sa, ws->cap, ev);
+        else launch_iteration<T, S, 0, false>(op, ws, sa, ws->cap, ev);
       }
     }
     cudaError_t e = cudaStreamEndCapture(ws->cap, &graph);
@@ -1017,14 +1316,25 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     g_launches += 2;
     {
       const T *dinv = sizeof(T) == 4 ? (const T *)op->dinv32 : (const T *)op->dinv64;
-      if (pc)
-        inner_init_kernel<T, S, true><<<ws->n_units_small, 256, 0, st>>>(
+      if (pc == 1)
+        inner_init_kernel<T, S, 1><<<ws->n_units_small, 256, 0, st>>>(
             ws->units_small, ws->outer_active, ws->R64, ws->inv_sigma, (T *)ws->R, (T *)ws->P,
             (T *)ws->D, dinv);
       else
-        inner_init_kernel<T, S, false><<<ws->n_units_small, 256, 0, st>>>(
+        inner_init_kernel<T, S, 0><<<ws->n_units_small, 256, 0, st>>>(
             ws->units_small, ws->outer_active, ws->R64, ws->inv_sigma, (T *)ws->R, (T *)ws->P,
             (T *)ws->D, dinv);
+      if (pc == 2) {   // P = Z = M^-1 R
+        long long maxcols = 1;
+        for (const ChipDev &cd : op->chips) maxcols = std::max<long long>(maxcols, (long long)cd.nx * cd.ny);
+        const int nq = S / (16 / (int)sizeof(T));
+        dim3 zg((unsigned)std::min<long long>((maxcols * nq + 255) / 256, 2048), (unsigned)nc);
+        const T *gco = sizeof(T) == 4 ? (const T *)op->g32 : (const T *)op->g64;
+        const T *zinv = sizeof(T) == 4 ? (const T *)op->zinv32 : (const T *)op->zinv64;
+        zline_init_kernel<T, S><<<zg, 256, 0, st>>>(op->d_chips, nc, ws->outer_active, gco, zinv,
+                                                   (const T *)ws->R, (T *)ws->P, (T *)ws->Zb);
+        g_launches += 1;
+      }
     }
     BLOCKOA_CUDA(cudaGetLastError());
     // Inner block-CG iterations, polled every `check_every` iterations.
@@ -1089,7 +1399,9 @@ extern "C" int blockoa_block_solve(blockoa_operator *op, const double *B, double
   }
   if (!(opts->rtol > 0.0) || opts->maxiter < 0) return BLOCKOA_ERR_INVALID;
   if (opts->precision != BLOCKOA_FP64 && opts->precision != BLOCKOA_MIXED) return BLOCKOA_ERR_INVALID;
-  if (opts->precond != BLOCKOA_PRECOND_NONE && opts->precond != BLOCKOA_PRECOND_JACOBI) return BLOCKOA_ERR_INVALID;
+  if (opts->precond != BLOCKOA_PRECOND_NONE && opts->precond != BLOCKOA_PRECOND_JACOBI &&
+      opts->precond != BLOCKOA_PRECOND_ZLINE)
+    return BLOCKOA_ERR_INVALID;
   if (opts->small_solve != BLOCKOA_SMALL_AUTO && opts->small_solve != BLOCKOA_SMALL_FP64_CHOLESKY)
     return BLOCKOA_ERR_INVALID;
   if (s == 0) {

@@ -76,6 +76,8 @@ struct blockoa_operator {
   float *g32 = nullptr;                  // [n_total][4]: float32 copies
   double *dinv64 = nullptr;              // [n_total] 1 / diag(A) (Jacobi)
   float *dinv32 = nullptr;               // [n_total] float32 copy
+  double *zinv64 = nullptr;              // [n_total] z-line preconditioner: 1 / (Thomas pivot) per cell
+  float *zinv32 = nullptr;               // [n_total] float32 copy
   double *lt64 = nullptr;                // [sum nz][kLT] layer tables (float64)
   float *lt32 = nullptr;                 // [sum nz][kLT] float32 copies
   cudaMemPool_t pool = nullptr;          // stream-ordered pool for workspaces

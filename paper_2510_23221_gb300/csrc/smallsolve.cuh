@@ -58,6 +58,7 @@ struct SmallArgs {
   void *beta;       // [chip][S][S]
   int *ticket;      // [2][chip] flushed-unit counters of the two Gram kernels (zero between launches)
   const int *unit_count;  // [chip] units per chip of the loop kernels
+  const int *zunit_count; // [chip] column-tile units per chip of the z-line update
   int n_chips;
   int tail;         // 1: the Gram kernels' last CTAs solve (mixed form, sweep)
   int s;            // caller's columns (for deflation counts)

@@ -309,6 +309,39 @@ def test_mixed_with_fp64_cholesky_small_solves(precond):
         assert np.all(relcols(Xs[c], ref) < 1e-8)
 
 
+@pytest.mark.parametrize("precision", [bo.FP64, bo.MIXED])
+def test_zline_preconditioned_solve(precision):
+    """z-line preconditioning changes the iteration, not the solution: the
+    reference stack at 1e-12 against the oracle, and uneven chips (several
+    layer counts, multi-cell layers, ragged column tiles) against dense solves."""
+    w = synth.small_fp64_workload()
+    chip = w.chips[0]
+    A = orc.assemble(chip)
+    B = orc.rhs(chip, w.density[0])
+    U_or, _ = orc.block_cg(A, B, rtol=1e-12)
+    (X,), (st,) = _solve([chip], [B], 8, precision, 1e-12, precond=bo.PRECOND_ZLINE)
+    assert st.status == bo.OK and st.relres_max <= 1e-12
+    assert np.all(relcols(X, U_or) < 1e-9)
+    chips = small_chips() + [synth.random_small_chip(105, 37, 21, 5)]
+    rng = np.random.default_rng(80)
+    for s in (4, 12):
+        Bs = [rng.uniform(0, 1e-2, (c.n, s)) for c in chips]
+        Xs, stats = _solve(chips, Bs, s, precision, 1e-11, precond=bo.PRECOND_ZLINE)
+        for c, ch in enumerate(chips):
+            assert stats[c].status == bo.OK, (s, c, stats[c])
+            ref = np.linalg.solve(orc.assemble(ch).toarray(), Bs[c])
+            assert np.all(relcols(Xs[c], ref) < 1e-8)
+
+
+def test_zline_needs_columns_that_fit_a_tile():
+    chip = synth.random_small_chip(106, 3, 3, 70)          # 70 cells in z > the 64-cell tile at s = 64
+    op = bo.assemble([chip])
+    B = cuda(np.random.default_rng(1).uniform(0, 1, chip.n * 64))
+    with pytest.raises(bo.BlockoaError) as e:
+        bo.block_solve(op, B, torch.empty_like(B), 64, precision=bo.MIXED, precond=bo.PRECOND_ZLINE)
+    assert e.value.code == bo.ERR_INVALID
+
+
 def test_deflation_duplicate_and_zero_columns():
     chip = synth.random_small_chip(81, 12, 10, 3)
     B = np.random.default_rng(81).uniform(0, 1e-2, (chip.n, 6))
