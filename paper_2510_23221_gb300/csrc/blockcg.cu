@@ -149,10 +149,37 @@ __device__ __forceinline__ void put_tile(T *tile, const T (&x)[4][16 / sizeof(T)
 
 // acc[a*4+b] += sum over cells [cbeg, cbeg + nc) of A[i0+a][c] * B[j0+b][c]
 // for transposed tiles A, B.
+// float32: paired FMAs (fma.rn.f32x2) over adjacent cells, two partial sums
+// per entry folded into acc at the end of the range -- half the FMA
+// instructions of the scalar form for the same arithmetic.
 template <typename T, int S>
 __device__ __forceinline__ void gram_range(T *acc, const T *A, const T *B, int i0, int j0,
                                            int cbeg, int nc) {
   using G = BK<T, S>;
+  if constexpr (sizeof(T) == 4) {
+    float2 pr[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) pr[e] = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int c = cbeg; c < cbeg + nc; c += 4) {
+      float a[4][4], b[4][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        ld4<float, G::LD>(a[q], A, i0 + q, c);
+        ld4<float, G::LD>(b[q], B, j0 + q, c);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          pr[q * 4 + r] = __ffma2_rn(make_float2(a[q][0], a[q][1]), make_float2(b[r][0], b[r][1]), pr[q * 4 + r]);
+          pr[q * 4 + r] = __ffma2_rn(make_float2(a[q][2], a[q][3]), make_float2(b[r][2], b[r][3]), pr[q * 4 + r]);
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc[e] += pr[e].x + pr[e].y;
+    return;
+  }
 #pragma unroll 2
   for (int c = cbeg; c < cbeg + nc; c += 4) {
     T a[4][4], b[4][4];
@@ -289,10 +316,76 @@ __device__ __forceinline__ void sched_finish(const UnitSched &us) {
   }
 }
 
+// ---------------------------------------------------------------- staged tiles (float32)
+// The staged loop kernels copy whole tiles (TC cells x S columns of a block
+// vector, 16 KB) into shared memory with cp.async several tiles ahead of
+// the one they compute on, so global latency overlaps arithmetic.  A staged
+// tile keeps the global [cell][column] order; the 16-byte chunks of row r
+// are XOR-swizzled with r & 7 (r & 3 for 64-byte rows) so that one chunk
+// read from four consecutive rows hits four different bank groups.
+template <int S>
+struct Stage32 {
+  static constexpr int NQ = S / 4;                   // 16-byte chunks per row
+  static constexpr int TC = BK<float, S>::TC;        // cells per tile
+  static constexpr int MASK = NQ < 8 ? NQ - 1 : 7;
+  static constexpr int FLOATS = TC * S;              // floats per staged tile
+  static_assert(TC * NQ % 256 == 0, "a tile is a whole number of chunks per thread");
+  __device__ static __forceinline__ int off(int row, int q) { return row * S + ((q ^ (row & MASK)) << 2); }
+};
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Stage rows [base, base + TC) of a [cell][S] block vector (zeros past end).
+template <int S>
+__device__ __forceinline__ void stage_tile(float *dst, const float *src, long long base, long long end) {
+  using SG = Stage32<S>;
+#pragma unroll
+  for (int m = 0; m < SG::TC * SG::NQ / 256; ++m) {
+    const int c = threadIdx.x + 256 * m;
+    const int row = c / SG::NQ, q = c % SG::NQ;
+    const bool in = base + row < end;
+    cp_async16(dst + SG::off(row, q), in ? src + (base + row) * S + q * 4 : src, in ? 16 : 0);
+  }
+}
+
+// The tiles of the calling CTA, in order: units blockIdx.x, blockIdx.x +
+// gridDim.x, ... of chips that are still active, each cut into tiles of TC
+// cells.  Every thread walks the same sequence.
+struct TileWalk {
+  int ui = 0, chip = -1;
+  long long base = 0, end = 0;
+  __device__ void seek(const UnitSched &us, const ChipSolveState *state, int u) {
+    const int G = (int)gridDim.x;
+    while (u < us.n_units) {
+      const Unit un = us.units[u];
+      if (state[un.chip].active) {
+        ui = u; chip = un.chip; base = un.begin; end = un.end;
+        return;
+      }
+      const int e = us.chip_unit_end[un.chip];   // skip the chip's other units
+      u += ((e - u + G - 1) / G) * G;
+    }
+    ui = us.n_units;
+    chip = -1;
+  }
+  template <int TC>
+  __device__ void next(const UnitSched &us, const ChipSolveState *state) {
+    base += TC;
+    if (base >= end) seek(us, state, ui + (int)gridDim.x);
+  }
+  __device__ bool valid(const UnitSched &us) const { return ui < us.n_units; }
+};
+
 // ---------------------------------------------------------------- kernels
 // Q = A P on the block layout; Gamma += P^T Q and rho += P^T R per chip.
 template <typename T, int S>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(256, 2)
 spmm_gram_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T *__restrict__ g,
                  const T *__restrict__ P, const T *__restrict__ R, T *__restrict__ Q, const SmallArgs A) {
   using G = BK<T, S>;
@@ -303,6 +396,8 @@ spmm_gram_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T 
   T *sR = sQ + S * G::LD;
   double *red = reinterpret_cast<double *>(smem);   // reused between units
   __shared__ int s_unit;
+  grid_release_next();
+  grid_wait_prior();
   const int t = threadIdx.x;
   const int j0 = (t % G::TPR) * V, cl0 = (t / G::TPR) * 4;
   const int grp = t / G::NT, w = t % G::NT;
@@ -435,6 +530,8 @@ update_gram_kernel(const UnitSched us, const T *__restrict__ P, const T *__restr
   T *sA = sR + S * G::LD;
   double *red = reinterpret_cast<double *>(smem);   // reused between units
   __shared__ int s_unit;
+  grid_release_next();
+  grid_wait_prior();
   const int t = threadIdx.x;
   const int j0 = (t % G::TPR) * V, cl0 = (t / G::TPR) * 4;
   const int grp = t / G::NT, w = t % G::NT;
@@ -531,6 +628,8 @@ p_update_kernel(const UnitSched us, const ChipSolveState *__restrict__ state, co
   T *sP = reinterpret_cast<T *>(smem);
   T *sB = sP + S * G::LD;
   __shared__ int s_unit;
+  grid_release_next();
+  grid_wait_prior();
   const int t = threadIdx.x;
   const int j0 = (t % G::TPR) * V, cl0 = (t / G::TPR) * 4;
   int cur = -1;
@@ -575,6 +674,91 @@ p_update_kernel(const UnitSched us, const ChipSolveState *__restrict__ state, co
     }
   }
   sched_finish(us);
+}
+
+// Staged float32 form of p_update_kernel: P = Z + P beta with the old P and
+// Z tiles copied NST - 1 tiles ahead.  P is updated in place (every tile is
+// read and written by one CTA only).
+template <int S, int PCM, int NST>
+__global__ void __launch_bounds__(256, 2)
+p_update_staged_kernel(const UnitSched us, const ChipSolveState *__restrict__ state, const float *__restrict__ beta,
+                       const float *__restrict__ R, float *__restrict__ P, const float *__restrict__ dinv,
+                       const float *__restrict__ Zb) {
+  using SG = Stage32<S>;
+  constexpr int TC = SG::TC, TPR = S / 4;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float *sB = reinterpret_cast<float *>(smem);
+  float *sP = sB + S * S;                 // NST staged tiles of P
+  float *sZ = sP + NST * SG::FLOATS;      // NST staged tiles of Z (R under PCM 0 and 1)
+  grid_release_next();
+  grid_wait_prior();
+  const int t = threadIdx.x;
+  const int jq = t % TPR, cl0 = (t / TPR) * 4;
+  const float *zsrc = PCM == 2 ? Zb : R;
+  TileWalk pre, cur;
+  pre.seek(us, state, (int)blockIdx.x);
+  cur = pre;
+#pragma unroll
+  for (int st = 0; st < NST - 1; ++st) {
+    if (pre.valid(us)) {
+      stage_tile<S>(sP + st * SG::FLOATS, P, pre.base, pre.end);
+      stage_tile<S>(sZ + st * SG::FLOATS, zsrc, pre.base, pre.end);
+      pre.next<TC>(us, state);
+    }
+    cp_async_commit();
+  }
+  int bchip = -1;
+  for (int k = 0; cur.valid(us); ++k) {
+    const int sn = (k + NST - 1) % NST, sc = k % NST;
+    if (pre.valid(us)) {
+      stage_tile<S>(sP + sn * SG::FLOATS, P, pre.base, pre.end);
+      stage_tile<S>(sZ + sn * SG::FLOATS, zsrc, pre.base, pre.end);
+      pre.next<TC>(us, state);
+    }
+    cp_async_commit();
+    if (cur.chip != bchip) {   // the previous tile's readers of sB passed the trailing barrier
+      const float *be = beta + (long long)cur.chip * S * S;
+      for (int e = t; e < S * S; e += 256) sB[e] = be[e];
+      bchip = cur.chip;
+    }
+    float di[4];
+    if constexpr (PCM == 1) {
+#pragma unroll
+      for (int k4 = 0; k4 < 4; ++k4) di[k4] = cur.base + cl0 + k4 < cur.end ? dinv[cur.base + cl0 + k4] : 0.f;
+    }
+    cp_async_wait<NST - 1>();
+    __syncthreads();
+    const float *tP = sP + sc * SG::FLOATS, *tZ = sZ + sc * SG::FLOATS;
+    float rv[4][4];
+#pragma unroll
+    for (int k4 = 0; k4 < 4; ++k4) {
+      vload<float>(rv[k4], tZ + SG::off(cl0 + k4, jq));
+      if constexpr (PCM == 1) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) rv[k4][v] *= di[k4];
+      }
+    }
+#pragma unroll 2
+    for (int iq = 0; iq < TPR; ++iq) {
+      float p[4][4], b[4][4];
+#pragma unroll
+      for (int k4 = 0; k4 < 4; ++k4) vload<float>(p[k4], tP + SG::off(cl0 + k4, iq));
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii) vload<float>(b[ii], sB + (4 * iq + ii) * S + 4 * jq);
+#pragma unroll
+      for (int k4 = 0; k4 < 4; ++k4)
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) rv[k4][v] += p[k4][ii] * b[ii][v];
+    }
+#pragma unroll
+    for (int k4 = 0; k4 < 4; ++k4)
+      if (cur.base + cl0 + k4 < cur.end) vstore<float>(P + (cur.base + cl0 + k4) * S + 4 * jq, rv[k4]);
+    __syncthreads();   // stage sc is refilled in the next iteration
+    cur.next<TC>(us, state);
+  }
+  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------- z-line preconditioning
@@ -670,6 +854,8 @@ update_zline_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const
   T *sI = sF + G::TC;
   double *red = reinterpret_cast<double *>(smem);   // reused between units
   __shared__ int s_unit;
+  grid_release_next();
+  grid_wait_prior();
   const int t = threadIdx.x;
   const int j0 = (t % G::TPR) * V, cl0 = (t / G::TPR) * 4;
   const int grp = t / G::NT, w = t % G::NT;
@@ -973,6 +1159,10 @@ constexpr size_t update_smem() {
 }
 template <typename T, int S>
 constexpr size_t pupdate_smem() { return tile_bytes<T, S>() + S * S * sizeof(T); }
+// staged float32 P update: tiles in flight per CTA and its shared memory
+constexpr int kPStages = 3;
+template <int S>
+constexpr size_t pstaged_smem() { return (size_t)S * S * 4 + 2 * (size_t)kPStages * Stage32<S>::FLOATS * 4; }
 template <typename T, int S>
 constexpr size_t zupdate_smem() {
   return cmax(update_smem<T, S>(), 3 * tile_bytes<T, S>() + S * S * sizeof(T) + 3 * BK<T, S>::TC * sizeof(T));
@@ -993,50 +1183,72 @@ static void set_smem_limits() {
                          (int)update_smem<T, S>());
   cudaFuncSetAttribute(p_update_kernel<T, S, PCM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pupdate_smem<T, S>());
+  if constexpr (sizeof(T) == 4)
+    cudaFuncSetAttribute(p_update_staged_kernel<S, PCM, kPStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)pstaged_smem<S>());
   cudaFuncSetAttribute(chol_alpha_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)chol_smem_bytes<S>());
 }
 
 // One block-CG iteration for every active chip; with `ev`, an event is
 // recorded before each kernel and after the last (for live timing).
+// `chain` says whether the previous node on the stream is a loop kernel:
+// a kernel that follows one is launched chained (programmatic dependent
+// launch), so its CTAs are scheduled while the previous kernel drains.
 template <typename T, int S, int PCM, bool CH>
 static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const SmallArgs &sa,
-                             cudaStream_t st, cudaEvent_t *ev) {
+                             cudaStream_t st, cudaEvent_t *ev, bool &chain) {
   const T *g = sizeof(T) == 4 ? (const T *)op->g32 : (const T *)op->g64;
   const T *dinv = sizeof(T) == 4 ? (const T *)op->dinv32 : (const T *)op->dinv64;
   // external record nodes: the events carry timestamps when the graph runs
-  auto mark = [&](int i) {
-    if (ev) cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal);
-  };
   int m = 0;
-  mark(m++);
+  auto mark = [&]() {
+    if (ev) {
+      cudaEventRecordWithFlags(ev[m], st, cudaEventRecordExternal);
+      chain = false;
+    }
+    ++m;
+  };
+  auto launched = [&]() { chain = true; };
+  mark();
   const UnitSched us_s{ws->units, ws->n_units, ws->chip_unit_end, ws->work};
   const UnitSched us_u{ws->units, ws->n_units, ws->chip_unit_end, ws->work + 2};
   const UnitSched us_p{ws->units, ws->n_units, ws->chip_unit_end, ws->work + 4};
-  spmm_gram_kernel<T, S><<<ws->grid_spmm, 256, spmm_smem<T, S>(), st>>>(
-      us_s, op->d_chips, g, (const T *)ws->P, (const T *)ws->R, (T *)ws->Q, sa);
+  launch_chained(spmm_gram_kernel<T, S>, ws->grid_spmm, 256, spmm_smem<T, S>(), st, chain,
+                 us_s, op->d_chips, g, (const T *)ws->P, (const T *)ws->R, (T *)ws->Q, sa);
+  launched();
   if constexpr (CH) {
-    mark(m++);
-    chol_alpha_kernel<T, S><<<ws->n_chips * S, 256, chol_smem_bytes<S>(), st>>>(sa);
+    mark();
+    launch_chained(chol_alpha_kernel<T, S>, ws->n_chips * S, 256, chol_smem_bytes<S>(), st, chain, sa);
+    launched();
   }
-  mark(m++);
+  mark();
   if constexpr (PCM == 2) {
     const UnitSched us_z{ws->zunits, ws->n_zunits, ws->zchip_unit_end, ws->work + 2};
     const T *zinv = sizeof(T) == 4 ? (const T *)op->zinv32 : (const T *)op->zinv64;
-    update_zline_kernel<T, S><<<ws->grid_zupdate, 256, zupdate_smem<T, S>(), st>>>(
-        us_z, op->d_chips, g, zinv, (const T *)ws->P, (const T *)ws->Q, (T *)ws->D, (T *)ws->R, (T *)ws->Zb, sa);
+    launch_chained(update_zline_kernel<T, S>, ws->grid_zupdate, 256, zupdate_smem<T, S>(), st, chain,
+                   us_z, op->d_chips, g, zinv, (const T *)ws->P, (const T *)ws->Q, (T *)ws->D, (T *)ws->R,
+                   (T *)ws->Zb, sa);
   } else {
-    update_gram_kernel<T, S, PCM><<<ws->grid_update, 256, update_smem<T, S>(), st>>>(
-        us_u, (const T *)ws->P, (const T *)ws->Q, (T *)ws->D, (T *)ws->R, dinv, sa);
+    launch_chained(update_gram_kernel<T, S, PCM>, ws->grid_update, 256, update_smem<T, S>(), st, chain,
+                   us_u, (const T *)ws->P, (const T *)ws->Q, (T *)ws->D, (T *)ws->R, dinv, sa);
   }
+  launched();
   if constexpr (CH) {
-    mark(m++);
-    chol_beta_kernel<T, S><<<ws->n_chips * S, 32, 0, st>>>(sa);
+    mark();
+    launch_chained(chol_beta_kernel<T, S>, ws->n_chips * S, 32, 0, st, chain, sa);
+    launched();
   }
-  mark(m++);
-  p_update_kernel<T, S, PCM><<<ws->grid_pupd, 256, pupdate_smem<T, S>(), st>>>(
-      us_p, ws->state, (const T *)ws->beta, (const T *)ws->R, (T *)ws->P, dinv, (const T *)ws->Zb);
-  mark(m++);
+  mark();
+  if constexpr (sizeof(T) == 4)
+    launch_chained(p_update_staged_kernel<S, PCM, kPStages>, ws->grid_pupd, 256, pstaged_smem<S>(), st, chain,
+                   us_p, ws->state, (const float *)ws->beta, (const float *)ws->R, (float *)ws->P,
+                   (const float *)dinv, (const float *)ws->Zb);
+  else
+    launch_chained(p_update_kernel<T, S, PCM>, ws->grid_pupd, 256, pupdate_smem<T, S>(), st, chain,
+                   us_p, ws->state, (const T *)ws->beta, (const T *)ws->R, (T *)ws->P, dinv, (const T *)ws->Zb);
+  launched();
+  mark();
 }
 
 template <typename T, int S>
@@ -1091,8 +1303,12 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
                                                                spmm_smem<T, S>()));
     BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, update_gram_kernel<T, S, 1>, 256,
                                                                update_smem<T, S>()));
-    BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, p_update_kernel<T, S, 1>, 256,
-                                                               pupdate_smem<T, S>()));
+    if constexpr (sizeof(T) == 4)
+      BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, p_update_staged_kernel<S, 1, kPStages>,
+                                                                 256, pstaged_smem<S>()));
+    else
+      BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, p_update_kernel<T, S, 1>, 256,
+                                                                 pupdate_smem<T, S>()));
     BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_z, update_zline_kernel<T, S>, 256,
                                                                zupdate_smem<T, S>()));
     long long tiles = 0;
@@ -1205,16 +1421,17 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     for (int i = 0; i <= kMaxLoopKernels; ++i)
       if (!ws->tev[i]) BLOCKOA_CUDA(cudaEventCreate(&ws->tev[i]));
     BLOCKOA_CUDA(cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal));
+    bool chain = false;   // the graph's first kernel waits for whatever precedes the launch
     for (int k = 0; k < check_every; ++k) {
       cudaEvent_t *ev = k == 0 ? ws->tev : nullptr;
       if (ch) {
-        if (pc == 1) launch_iteration<T, S, 1, true>(op, ws, sa, ws->cap, ev);
-        else if (pc == 2) launch_iteration<T, S, 2, true>(op, ws, sa, ws->cap, ev);
-        else launch_iteration<T, S, 0, true>(op, ws, sa, ws->cap, ev);
+        if (pc == 1) launch_iteration<T, S, 1, true>(op, ws, sa, ws->cap, ev, chain);
+        else if (pc == 2) launch_iteration<T, S, 2, true>(op, ws, sa, ws->cap, ev, chain);
+        else launch_iteration<T, S, 0, true>(op, ws, sa, ws->cap, ev, chain);
       } else if constexpr (sizeof(T) == 4) {
-        if (pc == 1) launch_iteration<T, S, 1, false>(op, ws, sa, ws->cap, ev);
-        else if (pc == 2) launch_iteration<T, S, 2, false>(op, ws, sa, ws->cap, ev);
-        else launch_iteration<T, S, 0, false>(op, ws, sa, ws->cap, ev);
+        if (pc == 1) launch_iteration<T, S, 1, false>(op, ws, sa, ws->cap, ev, chain);
+        else if (pc == 2) launch_iteration<T, S, 2, false>(op, ws, sa, ws->cap, ev, chain);
+        else launch_iteration<T, S, 0, false>(op, ws, sa, ws->cap, ev, chain);
       }
     }
     cudaError_t e = cudaStreamEndCapture(ws->cap, &graph);

@@ -63,6 +63,34 @@ struct KernelTimes {
 // count every kernel node).
 extern std::atomic<long long> g_launches;
 
+// Programmatic dependent launch.  A kernel launched with
+// launch_chained(..., chained = true) may be scheduled while the previous
+// kernel on the stream is still running; it must call grid_wait_prior()
+// before it touches memory that kernel writes (the wait returns once the
+// prior grid has completed and its writes are visible, and immediately for
+// a kernel launched without the attribute).  grid_release_next() lets the
+// next chained kernel be scheduled as soon as SM space frees up.
+#ifdef __CUDACC__
+__device__ __forceinline__ void grid_wait_prior() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_release_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                         cudaStream_t st, bool chained, Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = chained ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+#endif
+
 }  // namespace blockoa
 
 struct blockoa_operator {

@@ -164,6 +164,8 @@ __global__ void __launch_bounds__(256) chol_alpha_kernel(SmallArgs A) {
   CholSmem<S> &sh = *reinterpret_cast<CholSmem<S> *>(smem_raw);
   const int c = blockIdx.x / S, j = blockIdx.x % S;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  grid_release_next();
+  grid_wait_prior();
   ChipSolveState &st = A.state[c];
   if (!st.active) return;
   const double *g = A.gram + (long long)c * S * S;
@@ -291,6 +293,8 @@ __global__ void __launch_bounds__(32) chol_beta_kernel(SmallArgs A) {
   __shared__ int perm[S];
   const int c = blockIdx.x / S, j = blockIdx.x % S;
   const int t = threadIdx.x;
+  grid_release_next();
+  grid_wait_prior();
   ChipSolveState &st = A.state[c];
   if (!st.active) return;
   const int r = A.rank[c];
