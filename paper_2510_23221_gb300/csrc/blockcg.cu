@@ -34,6 +34,7 @@
 #include "common.cuh"
 #include "smallsolve.cuh"
 #include "smallsolve_chol.cuh"
+#include "tc.cuh"
 
 namespace blockoa {
 
@@ -761,6 +762,182 @@ p_update_staged_kernel(const UnitSched us, const ChipSolveState *__restrict__ st
   cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------- tensor-core P update
+// P = Z + P beta on the tensor cores (float32 form, S = 32).  Each CTA walks
+// its 128-cell tiles with the next tile's P and Z rows in flight
+// (cp.async, coalesced, two stages).  Per tile, thread t owns cell t: it
+// splits its P row into tf32 pairs x = hi + lo (hi rounded to nearest,
+// lo = x - hi exact in float32) written as K-major operand images without
+// swizzle, one thread issues
+//   D = P_lo beta_hi + P_hi beta_lo + P_hi beta_hi
+// (tcgen05.mma kind::tf32, M = 128, N = 32, K = 8 per instruction, float32
+// accumulator in TMEM), and thread t adds its TMEM row to its Z row.  The
+// dropped P_lo beta_lo term and the tf32 rounding of the lo parts leave a
+// relative error of order 2^-22 per product, the order of float32 rounding.
+// Results go back through shared memory for coalesced stores.
+constexpr int TCP_M = 128;
+
+struct TcImg32 {
+  static constexpr int S = 32;
+  static constexpr int SBO = (S / 4) * 128;       // bytes between 8-row groups
+  static constexpr int BYTES_A = TCP_M * S * 4;   // one plane of a 128 x 32 operand
+  static constexpr int BYTES_B = S * S * 4;       // one plane of the 32 x 32 operand
+  // byte offset of element (r, k): 8 x 16-byte core matrices, K-adjacent ones 128 bytes apart
+  __device__ static __forceinline__ int off(int r, int k) {
+    return (r >> 3) * SBO + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
+  }
+};
+
+constexpr size_t ptc_smem() {
+  // 2 stages x (P, Z) staged tiles, P hi / lo planes, beta^T hi / lo planes, barrier + TMEM slot
+  return 4 * (size_t)Stage32<32>::FLOATS * 4 + 2 * (size_t)TcImg32::BYTES_A + 2 * (size_t)TcImg32::BYTES_B + 64;
+}
+
+template <int PCM>
+__global__ void __launch_bounds__(128, 2)
+p_update_tc_kernel(const UnitSched us, ChipSolveState *__restrict__ state, const float *__restrict__ beta,
+                   const float *__restrict__ R, float *__restrict__ P, const float *__restrict__ dinv,
+                   const float *__restrict__ Zb) {
+  constexpr int S = 32, NQ = S / 4;
+  using I = TcImg32;
+  using SG = Stage32<S>;
+  static_assert(SG::TC == TCP_M, "one staged tile per MMA tile");
+  constexpr uint32_t TCOLS = 32;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  float *stP = reinterpret_cast<float *>(smem);      // [2][TC * S] staged P rows
+  float *stZ = stP + 2 * SG::FLOATS;                  // [2][TC * S] staged Z rows, then results
+  unsigned char *aHi = reinterpret_cast<unsigned char *>(stZ + 2 * SG::FLOATS);
+  unsigned char *aLo = aHi + I::BYTES_A;
+  unsigned char *bHi = aLo + I::BYTES_A, *bLo = bHi + I::BYTES_B;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(bLo + I::BYTES_B);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+  __shared__ int s_fail;
+  const int t = threadIdx.x, warp = t >> 5;
+  if (t == 0) {
+    mbar_init(bar, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tslot, TCOLS);   // before dependents may launch and allocate
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  grid_release_next();
+  grid_wait_prior();
+  const uint32_t idesc = idesc_tf32(TCP_M, S);
+  const float *zsrc = PCM == 2 ? Zb : R;
+  // rows [base, base + 128) of P and Z into stage st (128 threads, 8 chunks each per array)
+  auto stage = [&](int st, long long base, long long end) {
+#pragma unroll
+    for (int m = 0; m < SG::TC * NQ / 128; ++m) {
+      const int c = t + 128 * m, row = c / NQ, q = c % NQ;
+      const bool in = base + row < end;
+      const long long g = in ? (base + row) * S + q * 4 : 0;
+      cp_async16(stP + st * SG::FLOATS + SG::off(row, q), P + g, in ? 16 : 0);
+      cp_async16(stZ + st * SG::FLOATS + SG::off(row, q), zsrc + g, in ? 16 : 0);
+    }
+  };
+  TileWalk pre, cur;
+  pre.seek(us, state, (int)blockIdx.x);
+  cur = pre;
+  if (pre.valid(us)) {
+    stage(0, pre.base, pre.end);
+    pre.next<TCP_M>(us, state);
+  }
+  cp_async_commit();
+  int bchip = -1, fail_chip = -1;
+  uint32_t phase = 0;
+  for (int k = 0; cur.valid(us); ++k, cur.next<TCP_M>(us, state)) {
+    const int sc = k & 1;
+    if (pre.valid(us)) {
+      stage(sc ^ 1, pre.base, pre.end);
+      pre.next<TCP_M>(us, state);
+    }
+    cp_async_commit();
+    if (cur.chip != bchip) {   // beta^T planes: B(n, k) = beta(k, n)
+      const float *be = beta + (long long)cur.chip * S * S;
+      for (int e = t; e < S * S; e += 128) {
+        const int kk = e / S, n = e % S;
+        const float v = be[e];
+        const float hi = tf32_rna(v);
+        *reinterpret_cast<float *>(bHi + I::off(n, kk)) = hi;
+        *reinterpret_cast<float *>(bLo + I::off(n, kk)) = v - hi;
+      }
+      bchip = cur.chip;
+    }
+    float di = 1.f;
+    if constexpr (PCM == 1) di = cur.base + t < cur.end ? dinv[cur.base + t] : 0.f;
+    cp_async_wait<1>();
+    __syncthreads();   // tile k staged by all threads
+    const float *tP = stP + sc * SG::FLOATS;
+    float *tZ = stZ + sc * SG::FLOATS;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {   // this thread's P row -> hi / lo planes
+      const float4 v = *reinterpret_cast<const float4 *>(tP + SG::off(t, q));
+      const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+      *reinterpret_cast<float4 *>(aHi + I::off(t, 4 * q)) = h;
+      *reinterpret_cast<float4 *>(aLo + I::off(t, 4 * q)) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int ks = 0; ks < S / 8; ++ks)   // small terms first
+        mma_tf32(tmem, smem_desc(aLo + ks * 256, 128, I::SBO), smem_desc(bHi + ks * 256, 128, I::SBO), idesc,
+                 ks > 0 ? 1u : 0u);
+#pragma unroll
+      for (int ks = 0; ks < S / 8; ++ks)
+        mma_tf32(tmem, smem_desc(aHi + ks * 256, 128, I::SBO), smem_desc(bLo + ks * 256, 128, I::SBO), idesc, 1u);
+#pragma unroll
+      for (int ks = 0; ks < S / 8; ++ks)
+        mma_tf32(tmem, smem_desc(aHi + ks * 256, 128, I::SBO), smem_desc(bHi + ks * 256, 128, I::SBO), idesc, 1u);
+      mma_commit(bar);
+    }
+    float z[S];   // Z row while the MMAs run
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const float4 v = *reinterpret_cast<const float4 *>(tZ + SG::off(t, q));
+      z[4 * q] = v.x * di; z[4 * q + 1] = v.y * di; z[4 * q + 2] = v.z * di; z[4 * q + 3] = v.w * di;
+    }
+    if (!mbar_wait(bar, phase)) s_fail = 1;
+    __syncthreads();
+    if (s_fail) {
+      fail_chip = cur.chip;
+      break;
+    }
+    phase ^= 1;
+    tc_fence_after();
+    uint32_t d[S];
+    BLOCKOA_TMEM_LD32(tmem + ((uint32_t)(warp * 32) << 16), d);
+    tmem_wait_ld();
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      *reinterpret_cast<float4 *>(tZ + SG::off(t, q)) =
+          make_float4(z[4 * q] + __uint_as_float(d[4 * q]), z[4 * q + 1] + __uint_as_float(d[4 * q + 1]),
+                      z[4 * q + 2] + __uint_as_float(d[4 * q + 2]), z[4 * q + 3] + __uint_as_float(d[4 * q + 3]));
+    tc_fence_before();
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < SG::TC * NQ / 128; ++m) {   // coalesced stores of the new P rows
+      const int c = t + 128 * m, row = c / NQ, q = c % NQ;
+      if (cur.base + row < cur.end)
+        *reinterpret_cast<float4 *>(P + (cur.base + row) * S + q * 4) =
+            *reinterpret_cast<const float4 *>(tZ + SG::off(row, q));
+    }
+    __syncthreads();   // stage sc, the planes and TMEM are reused
+  }
+  cp_async_wait<0>();
+  if (fail_chip >= 0 && t == 0) {   // MMA completion timed out: report, let it land, release TMEM
+    state[fail_chip].status = BLOCKOA_ERR_TIMEOUT;
+    state[fail_chip].active = 0;
+    mbar_wait(bar, phase);
+  }
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, TCOLS);
+}
+
 // ---------------------------------------------------------------- z-line preconditioning
 // Z = M^-1 R with M the part of A that couples the cells of one (x, y)
 // column (tridiagonal in z), by the Thomas recurrences with the per-cell
@@ -1159,6 +1336,26 @@ constexpr size_t update_smem() {
 }
 template <typename T, int S>
 constexpr size_t pupdate_smem() { return tile_bytes<T, S>() + S * S * sizeof(T); }
+
+// Resident CTAs per SM from the kernel's registers, threads and shared
+// memory against the SM's limits (the largest shared-memory carveout).
+template <typename K>
+static int resident_ctas(K kernel, int threads, size_t dyn_smem, int device) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return 1;
+  int smem_sm = 0, resv = 0, regs_sm = 0, thr_sm = 0;
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+  cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, device);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, device);
+  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, device);
+  const long long per_block_smem = (long long)dyn_smem + (long long)fa.sharedSizeBytes + resv;
+  const int warps = (threads + 31) / 32;
+  const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;   // allocation unit: 256 registers per warp
+  int n = std::min(thr_sm / threads, 32);
+  if (per_block_smem > 0) n = std::min<long long>(n, smem_sm / per_block_smem);
+  if (warp_regs > 0) n = std::min(n, regs_sm / (warps * warp_regs));
+  return std::max(n, 1);
+}
 // staged float32 P update: tiles in flight per CTA and its shared memory
 constexpr int kPStages = 3;
 template <int S>
@@ -1183,7 +1380,13 @@ static void set_smem_limits() {
                          (int)update_smem<T, S>());
   cudaFuncSetAttribute(p_update_kernel<T, S, PCM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pupdate_smem<T, S>());
-  if constexpr (sizeof(T) == 4)
+  if constexpr (sizeof(T) == 4 && S == 32) {
+    cudaFuncSetAttribute(p_update_tc_kernel<PCM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ptc_smem());
+    // two CTAs of ~107 KB per SM need the largest shared-memory carveout
+    cudaFuncSetAttribute(p_update_tc_kernel<PCM>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+  }
+  else if constexpr (sizeof(T) == 4)
     cudaFuncSetAttribute(p_update_staged_kernel<S, PCM, kPStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)pstaged_smem<S>());
   cudaFuncSetAttribute(chol_alpha_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1240,7 +1443,11 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
     launched();
   }
   mark();
-  if constexpr (sizeof(T) == 4)
+  if constexpr (sizeof(T) == 4 && S == 32)
+    launch_chained(p_update_tc_kernel<PCM>, ws->grid_pupd, 128, ptc_smem(), st, chain,
+                   us_p, ws->state, (const float *)ws->beta, (const float *)ws->R, (float *)ws->P,
+                   (const float *)dinv, (const float *)ws->Zb);
+  else if constexpr (sizeof(T) == 4)
     launch_chained(p_update_staged_kernel<S, PCM, kPStages>, ws->grid_pupd, 256, pstaged_smem<S>(), st, chain,
                    us_p, ws->state, (const float *)ws->beta, (const float *)ws->R, (float *)ws->P,
                    (const float *)dinv, (const float *)ws->Zb);
@@ -1303,7 +1510,9 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
                                                                spmm_smem<T, S>()));
     BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_u, update_gram_kernel<T, S, 1>, 256,
                                                                update_smem<T, S>()));
-    if constexpr (sizeof(T) == 4)
+    if constexpr (sizeof(T) == 4 && S == 32)
+      occ_p = resident_ctas(p_update_tc_kernel<1>, 128, ptc_smem(), op->device);
+    else if constexpr (sizeof(T) == 4)
       BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, p_update_staged_kernel<S, 1, kPStages>,
                                                                  256, pstaged_smem<S>()));
     else
@@ -1581,7 +1790,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       iters[c] = cs.iters;
       defl[c] = cs.deflated;
       refine[c] += 1;
-      if (cs.status == BLOCKOA_ERR_BREAKDOWN) { status[c] = cs.status; done[c] = 1; }
+      if (cs.status != BLOCKOA_OK) { status[c] = cs.status; done[c] = 1; }   // breakdown or a device wait timed out
     }
   }
   g_launches += 1;
