@@ -127,6 +127,21 @@ typedef struct blockoa_operator blockoa_operator;
 int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips, blockoa_stream stream,
                      blockoa_operator **out);
 
+/*
+ * Re-discretise an existing operator in place (Eq. 1 -> Eq. 2, same stencil
+ * and arithmetic as blockoa_assemble) for chips of the same geometry: the
+ * same chip count and, per chip, the same nx, ny and layer rows (layer
+ * thicknesses, conductivities, cell sizes and film coefficients may
+ * change).  The operator's arrays, its solve workspace and its captured
+ * block-CG graph are kept, so a stream of same-shaped chips costs no
+ * allocation or graph build.  Stream-ordered: work already queued on the
+ * operator must be on `stream` or complete.
+ * Errors: ERR_INVALID (bad descriptor or different geometry; the operator
+ * is unchanged), ERR_OOM, ERR_CUDA.
+ */
+int blockoa_reassemble(blockoa_operator *op, const blockoa_chip_desc *chips, int n_chips,
+                       blockoa_stream stream);
+
 /* Sizes of chip `chip` (host outputs, any may be NULL).  Synchronous. */
 int blockoa_operator_size(const blockoa_operator *op, int chip, int64_t *n_cells,
                           int64_t *cell_offset, int *nx, int *ny, int *nz);

@@ -33,7 +33,7 @@ SMALL_AUTO = 0
 SMALL_FP64_CHOLESKY = 1
 
 EXPORTED = (
-    "blockoa_assemble", "blockoa_operator_size", "blockoa_operator_total", "blockoa_build_rhs",
+    "blockoa_assemble", "blockoa_reassemble", "blockoa_operator_size", "blockoa_operator_total", "blockoa_build_rhs",
     "blockoa_block_solve", "blockoa_combine", "blockoa_apply_operator", "blockoa_pair_check",
     "blockoa_export_conductances", "blockoa_destroy", "blockoa_status_string",
     "blockoa_last_error", "blockoa_kernel_times", "blockoa_reset_kernel_times",
@@ -82,6 +82,7 @@ def _lib():
         lib = ct.CDLL(LIB_PATH)
         vp, i, d = ct.c_void_p, ct.c_int, ct.c_double
         lib.blockoa_assemble.argtypes = [ct.POINTER(ChipDesc), i, vp, ct.POINTER(vp)]
+        lib.blockoa_reassemble.argtypes = [vp, ct.POINTER(ChipDesc), i, vp]
         lib.blockoa_operator_size.argtypes = [vp, i, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int64),
                                               ct.POINTER(i), ct.POINTER(i), ct.POINTER(i)]
         lib.blockoa_operator_total.argtypes = [vp, ct.POINTER(ct.c_int64), ct.POINTER(i)]
@@ -196,6 +197,16 @@ def assemble(chips: Sequence, stream=None) -> Operator:
     h = ct.c_void_p()
     _check(_lib().blockoa_assemble(arr, len(chips), _stream(stream), ct.byref(h)), "assemble")
     return Operator(h.value, chips)
+
+
+def reassemble(op: Operator, chips: Sequence, stream=None) -> Operator:
+    """blockoa_reassemble: new chips of the same geometry into `op` (kept
+    arrays, solve workspace and graph); returns op."""
+    keep: list = []
+    arr = (ChipDesc * len(chips))(*[_desc(c, keep) for c in chips])
+    _check(_lib().blockoa_reassemble(op.handle, arr, len(chips), _stream(stream)), "reassemble")
+    op.chips = list(chips)
+    return op
 
 
 def operator_size(op: Operator, chip: int):

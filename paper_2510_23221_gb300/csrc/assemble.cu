@@ -332,17 +332,19 @@ extern "C" const char *blockoa_last_error(void) { return g_last_error; }
 static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 static bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
 
-extern "C" int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips,
-                                blockoa_stream stream, blockoa_operator **out) {
-  if (!out) return BLOCKOA_ERR_INVALID;
-  *out = nullptr;
-  if (!chips || n_chips <= 0) return BLOCKOA_ERR_INVALID;
-  cudaStream_t st = (cudaStream_t)stream;
-
-  // Validate on the host and build tables.
-  std::vector<ChipDev> tab(n_chips);
-  std::vector<ChipPhys> phys(n_chips);
+// Host-side validation of the chip descriptions and the tables the assembly
+// kernels read.
+struct ChipTables {
+  std::vector<ChipDev> tab;
+  std::vector<ChipPhys> phys;
   std::vector<double> zk, zdz, kcell;
+  long long n_total = 0;
+};
+
+static int build_tables(const blockoa_chip_desc *chips, int n_chips, ChipTables &t) {
+  if (!chips || n_chips <= 0) return BLOCKOA_ERR_INVALID;
+  t.tab.assign(n_chips, ChipDev());
+  t.phys.assign(n_chips, ChipPhys());
   long long off = 0;
   for (int c = 0; c < n_chips; ++c) {
     const blockoa_chip_desc &d = chips[c];
@@ -354,14 +356,14 @@ extern "C" int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips,
     long long nz = 0;
     ChipPhys ph;
     ph.dx = d.dx; ph.dy = d.dy; ph.h_top = d.h_top; ph.h_bottom = d.h_bottom; ph.h_side = d.h_side;
-    ph.zoff = (long long)zk.size();
+    ph.zoff = (long long)t.zk.size();
     for (int l = 0; l < d.n_layers; ++l) {
       if (d.layer_nz[l] < 1 || !finite_pos(d.layer_dz[l])) return BLOCKOA_ERR_INVALID;
       double kl = d.layer_k ? d.layer_k[l] : 1.0;
       if (!d.k_cell && !finite_pos(kl)) return BLOCKOA_ERR_INVALID;
       for (int r = 0; r < d.layer_nz[l]; ++r) {
-        zk.push_back(kl);
-        zdz.push_back(d.layer_dz[l]);
+        t.zk.push_back(kl);
+        t.zdz.push_back(d.layer_dz[l]);
       }
       nz += d.layer_nz[l];
     }
@@ -370,35 +372,93 @@ extern "C" int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips,
     if (n > (1LL << 40)) return BLOCKOA_ERR_INVALID;
     ph.kcell_off = -1;
     if (d.k_cell) {
-      ph.kcell_off = (long long)kcell.size();
+      ph.kcell_off = (long long)t.kcell.size();
       for (long long i = 0; i < n; ++i) {
         if (!finite_pos(d.k_cell[i])) return BLOCKOA_ERR_INVALID;
-        kcell.push_back(d.k_cell[i]);
+        t.kcell.push_back(d.k_cell[i]);
       }
     }
-    tab[c].nx = d.nx; tab[c].ny = d.ny; tab[c].nz = (int)nz;
-    tab[c].layered = d.k_cell ? 0 : 1;
-    tab[c].n = n; tab[c].off = off;
-    tab[c].lz = ph.zoff;
-    phys[c] = ph;
+    t.tab[c].nx = d.nx; t.tab[c].ny = d.ny; t.tab[c].nz = (int)nz;
+    t.tab[c].layered = d.k_cell ? 0 : 1;
+    t.tab[c].n = n; t.tab[c].off = off;
+    t.tab[c].lz = ph.zoff;
+    t.phys[c] = ph;
     off += n;
   }
+  t.n_total = off;
+  return BLOCKOA_OK;
+}
+
+// Upload the tables and run the assembly kernels into the operator's
+// (already allocated) arrays: conductances, 1/diag, z-line factors, layer
+// tables.  Temporaries come from the stream-ordered pool.
+static int run_assembly(blockoa_operator *op, const ChipTables &t, cudaStream_t st) {
+  const int n_chips = op->n_chips;
+  std::vector<Unit> units = make_units(op, 4096);
+  void *d_units = nullptr, *d_phys = nullptr, *d_zk = nullptr, *d_zdz = nullptr, *d_kc = nullptr;
+  auto done = [&](int code) {
+    pool_free(d_units, st); pool_free(d_phys, st); pool_free(d_zk, st);
+    pool_free(d_zdz, st); pool_free(d_kc, st);
+    return code;
+  };
+  int rc;
+  if ((rc = pool_alloc(op, &d_units, sizeof(Unit) * units.size(), st))) return done(rc);
+  if ((rc = pool_alloc(op, &d_phys, sizeof(ChipPhys) * n_chips, st))) return done(rc);
+  if ((rc = pool_alloc(op, &d_zk, sizeof(double) * t.zk.size(), st))) return done(rc);
+  if ((rc = pool_alloc(op, &d_zdz, sizeof(double) * t.zdz.size(), st))) return done(rc);
+  if (!t.kcell.empty() && (rc = pool_alloc(op, &d_kc, sizeof(double) * t.kcell.size(), st))) return done(rc);
+  // Host tables are pageable; cudaMemcpyAsync from pageable memory returns
+  // only after the source has been consumed, so the vectors may die after.
+  cudaError_t e = cudaMemcpyAsync(op->d_chips, t.tab.data(), sizeof(ChipDev) * n_chips, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_units, units.data(), sizeof(Unit) * units.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_phys, t.phys.data(), sizeof(ChipPhys) * n_chips, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_zk, t.zk.data(), sizeof(double) * t.zk.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_zdz, t.zdz.data(), sizeof(double) * t.zdz.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && d_kc) e = cudaMemcpyAsync(d_kc, t.kcell.data(), sizeof(double) * t.kcell.size(), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return done(cuda_status(e, "upload chip tables"));
+  g_launches += 1;
+  assemble_kernel<<<(unsigned)units.size(), 256, 0, st>>>(
+      (const Unit *)d_units, op->d_chips, (const ChipPhys *)d_phys, (const double *)d_zk,
+      (const double *)d_zdz, (const double *)d_kc, op->g64, op->g32);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return done(cuda_status(e, "assemble_kernel"));
+  g_launches += 2;
+  inv_diag_kernel<<<(unsigned)units.size(), 256, 0, st>>>((const Unit *)d_units, op->d_chips, op->g64,
+                                                          op->dinv64, op->dinv32);
+  {
+    long long maxcols = 1;
+    for (const ChipDev &cd : op->chips) maxcols = std::max<long long>(maxcols, (long long)cd.nx * cd.ny);
+    dim3 zg((unsigned)std::min<long long>((maxcols + 255) / 256, 1024), (unsigned)n_chips);
+    zfactor_kernel<<<zg, 256, 0, st>>>(op->d_chips, n_chips, op->g64, op->zinv64, op->zinv32);
+    g_launches += 1;
+  }
+  layer_table_kernel<<<(unsigned)n_chips, 64, 0, st>>>(op->d_chips, (const ChipPhys *)d_phys,
+                                                      (const double *)d_zk, (const double *)d_zdz,
+                                                      n_chips, op->lt64, op->lt32);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return done(cuda_status(e, "layer_table_kernel"));
+  return done(BLOCKOA_OK);
+}
+
+extern "C" int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips,
+                                blockoa_stream stream, blockoa_operator **out) {
+  if (!out) return BLOCKOA_ERR_INVALID;
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  ChipTables t;
+  int rc = build_tables(chips, n_chips, t);
+  if (rc) return rc;
 
   blockoa_operator *op = new blockoa_operator();
   cudaGetDevice(&op->device);
   op->pool = device_pool(op->device);
   op->n_chips = n_chips;
-  op->n_total = off;
-  op->chips = tab;
+  op->n_total = t.n_total;
+  op->chips = t.tab;
+  op->n_zrows = (long long)t.zk.size();
   op->cell_area.resize(n_chips);
   for (int c = 0; c < n_chips; ++c) op->cell_area[c] = chips[c].dx * chips[c].dy;
-
-  std::vector<Unit> units = make_units(op, 4096);
-  void *d_units = nullptr, *d_phys = nullptr, *d_zk = nullptr, *d_zdz = nullptr, *d_kc = nullptr;
-  int rc = BLOCKOA_OK;
   auto fail = [&](int code) {
-    pool_free(d_units, st); pool_free(d_phys, st); pool_free(d_zk, st);
-    pool_free(d_zdz, st); pool_free(d_kc, st);
     blockoa_destroy(op);
     return code;
   };
@@ -417,50 +477,32 @@ extern "C" int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips,
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc zinv64"));
   e = cudaMalloc((void **)&op->zinv32, sizeof(float) * op->n_total);
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc zinv32"));
-  e = cudaMalloc((void **)&op->lt64, sizeof(double) * kLT * zk.size());
+  e = cudaMalloc((void **)&op->lt64, sizeof(double) * kLT * t.zk.size());
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc lt64"));
-  e = cudaMalloc((void **)&op->lt32, sizeof(float) * kLT * zk.size());
+  e = cudaMalloc((void **)&op->lt32, sizeof(float) * kLT * t.zk.size());
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc lt32"));
-  if ((rc = pool_alloc(op, &d_units, sizeof(Unit) * units.size(), st))) return fail(rc);
-  if ((rc = pool_alloc(op, &d_phys, sizeof(ChipPhys) * n_chips, st))) return fail(rc);
-  if ((rc = pool_alloc(op, &d_zk, sizeof(double) * zk.size(), st))) return fail(rc);
-  if ((rc = pool_alloc(op, &d_zdz, sizeof(double) * zdz.size(), st))) return fail(rc);
-  if (!kcell.empty() && (rc = pool_alloc(op, &d_kc, sizeof(double) * kcell.size(), st)))
-    return fail(rc);
-  // Host tables are pageable; cudaMemcpyAsync from pageable memory returns
-  // only after the source has been consumed, so the vectors may die after.
-  e = cudaMemcpyAsync(op->d_chips, tab.data(), sizeof(ChipDev) * n_chips, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_units, units.data(), sizeof(Unit) * units.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_phys, phys.data(), sizeof(ChipPhys) * n_chips, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_zk, zk.data(), sizeof(double) * zk.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_zdz, zdz.data(), sizeof(double) * zdz.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && d_kc) e = cudaMemcpyAsync(d_kc, kcell.data(), sizeof(double) * kcell.size(), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return fail(cuda_status(e, "upload chip tables"));
-  g_launches += 1;
-  assemble_kernel<<<(unsigned)units.size(), 256, 0, st>>>(
-      (const Unit *)d_units, op->d_chips, (const ChipPhys *)d_phys, (const double *)d_zk,
-      (const double *)d_zdz, (const double *)d_kc, op->g64, op->g32);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(cuda_status(e, "assemble_kernel"));
-  g_launches += 2;
-  inv_diag_kernel<<<(unsigned)units.size(), 256, 0, st>>>((const Unit *)d_units, op->d_chips, op->g64,
-                                                          op->dinv64, op->dinv32);
-  {
-    long long maxcols = 1;
-    for (const ChipDev &cd : op->chips) maxcols = std::max<long long>(maxcols, (long long)cd.nx * cd.ny);
-    dim3 zg((unsigned)std::min<long long>((maxcols + 255) / 256, 1024), (unsigned)n_chips);
-    zfactor_kernel<<<zg, 256, 0, st>>>(op->d_chips, n_chips, op->g64, op->zinv64, op->zinv32);
-    g_launches += 1;
-  }
-  layer_table_kernel<<<(unsigned)n_chips, 64, 0, st>>>(op->d_chips, (const ChipPhys *)d_phys,
-                                                      (const double *)d_zk, (const double *)d_zdz,
-                                                      n_chips, op->lt64, op->lt32);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(cuda_status(e, "layer_table_kernel"));
-  pool_free(d_units, st); pool_free(d_phys, st); pool_free(d_zk, st);
-  pool_free(d_zdz, st); pool_free(d_kc, st);
+  if ((rc = run_assembly(op, t, st))) return fail(rc);
   *out = op;
   return BLOCKOA_OK;
+}
+
+extern "C" int blockoa_reassemble(blockoa_operator *op, const blockoa_chip_desc *chips, int n_chips,
+                                  blockoa_stream stream) {
+  if (!op) return BLOCKOA_ERR_INVALID;
+  ChipTables t;
+  int rc = build_tables(chips, n_chips, t);
+  if (rc) return rc;
+  // same geometry: chip count, grid of every chip and layer rows
+  if (n_chips != op->n_chips || t.n_total != op->n_total || (long long)t.zk.size() != op->n_zrows)
+    return BLOCKOA_ERR_INVALID;
+  for (int c = 0; c < n_chips; ++c) {
+    const ChipDev &a = t.tab[c], &b = op->chips[c];
+    if (a.nx != b.nx || a.ny != b.ny || a.nz != b.nz || a.n != b.n || a.off != b.off || a.lz != b.lz)
+      return BLOCKOA_ERR_INVALID;
+  }
+  op->chips = t.tab;   // the layered flag may change with the conductivity description
+  for (int c = 0; c < n_chips; ++c) op->cell_area[c] = chips[c].dx * chips[c].dy;
+  return run_assembly(op, t, (cudaStream_t)stream);
 }
 
 extern "C" int blockoa_operator_size(const blockoa_operator *op, int chip, int64_t *n_cells,

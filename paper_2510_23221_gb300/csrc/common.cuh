@@ -97,6 +97,7 @@ struct blockoa_operator {
   int device = 0;
   int n_chips = 0;
   long long n_total = 0;
+  long long n_zrows = 0;                 // z-rows of all chips (layer table records)
   std::vector<blockoa::ChipDev> chips;   // host copy
   std::vector<double> cell_area;         // dx * dy per chip (m^2)
   blockoa::ChipDev *d_chips = nullptr;   // device copy

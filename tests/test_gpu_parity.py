@@ -333,6 +333,38 @@ def test_zline_preconditioned_solve(precision):
             assert np.all(relcols(Xs[c], ref) < 1e-8)
 
 
+def test_reassemble_in_place_matches_fresh_assembly():
+    """Re-discretising an operator in place equals a fresh assembly bit for
+    bit; a solve on it, reusing the workspace and graph built by a solve on
+    the previous chip, matches a dense solve of the new chip; a chip of
+    another grid is refused and leaves the operator unchanged."""
+    a = synth.random_small_chip(301, 33, 17, 5, h_top=3e4, h_bottom=2e3)
+    b = synth.random_small_chip(302, 33, 17, 5, h_top=1e4, h_side=4e3)   # same grid, other k, dz, films
+    s = 8
+    rng = np.random.default_rng(9)
+    op = bo.assemble([a])
+    Ba = cuda(rng.uniform(0, 1e-2, (a.n, s)).ravel())
+    bo.block_solve(op, Ba, torch.empty_like(Ba), s, rtol=1e-10, precision=bo.MIXED, precond=bo.PRECOND_ZLINE)
+    bo.reassemble(op, [b])
+    ref = bo.export_conductances(bo.assemble([b]), 0)
+    got = bo.export_conductances(op, 0)
+    for k in ref:
+        assert np.array_equal(got[k], ref[k]), k
+    Bb = rng.uniform(0, 1e-2, (b.n, s))
+    X = torch.empty(b.n * s, dtype=torch.float64, device="cuda")
+    (st,) = bo.block_solve(op, cuda(Bb.ravel()), X, s, rtol=1e-11, precision=bo.MIXED,
+                           precond=bo.PRECOND_ZLINE)
+    assert st.status == bo.OK
+    dense = np.linalg.solve(orc.assemble(b).toarray(), Bb)
+    assert np.all(relcols(X.cpu().numpy().reshape(-1, s), dense) < 1e-8)
+    with pytest.raises(bo.BlockoaError) as e:
+        bo.reassemble(op, [synth.random_small_chip(303, 33, 16, 5)])
+    assert e.value.code == bo.ERR_INVALID
+    got = bo.export_conductances(op, 0)
+    for k in ref:
+        assert np.array_equal(got[k], ref[k]), k
+
+
 def test_zline_needs_columns_that_fit_a_tile():
     chip = synth.random_small_chip(106, 3, 3, 70)          # 70 cells in z > the 64-cell tile at s = 64
     op = bo.assemble([chip])
