@@ -332,6 +332,23 @@ extern "C" const char *blockoa_last_error(void) { return g_last_error; }
 static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 static bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
 
+namespace blockoa {
+__global__ void read_small_kernel(const unsigned long long *__restrict__ src, unsigned long long *dst, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+}  // namespace blockoa
+
+cudaError_t blockoa::read_small(void *host_pinned, const void *dev, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return cudaSuccess;
+  void *dptr = nullptr;
+  cudaError_t e = cudaHostGetDevicePointer(&dptr, host_pinned, 0);
+  if (e != cudaSuccess) return e;
+  g_launches += 1;
+  read_small_kernel<<<1, 256, 0, st>>>((const unsigned long long *)dev, (unsigned long long *)dptr,
+                                       (int)(bytes / 8));
+  return cudaGetLastError();
+}
+
 // Host-side validation of the chip descriptions and the tables the assembly
 // kernels read.
 struct ChipTables {
@@ -481,6 +498,8 @@ extern "C" int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips,
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc lt64"));
   e = cudaMalloc((void **)&op->lt32, sizeof(float) * kLT * t.zk.size());
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMalloc lt32"));
+  e = cudaMallocHost((void **)&op->h_flag, 2 * sizeof(int));
+  if (e != cudaSuccess) return fail(cuda_status(e, "cudaMallocHost flag"));
   if ((rc = run_assembly(op, t, st))) return fail(rc);
   *out = op;
   return BLOCKOA_OK;
@@ -596,6 +615,7 @@ extern "C" void blockoa_destroy(blockoa_operator *op) {
   if (op->zinv32) cudaFree(op->zinv32);
   if (op->lt64) cudaFree(op->lt64);
   if (op->lt32) cudaFree(op->lt32);
+  if (op->h_flag) cudaFreeHost(op->h_flag);
   cudaGetLastError();
   delete op;
 }

@@ -1665,7 +1665,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
   col_norms_kernel<S><<<ws->n_units_small, 256, 0, st>>>(ws->units_small, ws->B64, ws->bn2);
   BLOCKOA_CUDA(cudaGetLastError());
   std::vector<double> bn2((size_t)nc * S);
-  BLOCKOA_CUDA(cudaMemcpyAsync(ws->h_small, ws->bn2, sizeof(double) * nc * S, cudaMemcpyDeviceToHost, st));
+  BLOCKOA_CUDA(read_small(ws->h_small, ws->bn2, sizeof(double) * nc * S, st));
   BLOCKOA_CUDA(cudaStreamSynchronize(st));
   memcpy(bn2.data(), ws->h_small, sizeof(double) * nc * S);
 
@@ -1677,7 +1677,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     BLOCKOA_CUDA(cudaMemsetAsync(ws->rn64, 0, sizeof(double) * nc * S, st));
     int rc = launch_residual64(op, ws->B64, ws->X64, ws->R64, S, ws->rn64, st);
     if (rc) return rc;
-    BLOCKOA_CUDA(cudaMemcpyAsync(ws->h_small, ws->rn64, sizeof(double) * nc * S, cudaMemcpyDeviceToHost, st));
+    BLOCKOA_CUDA(read_small(ws->h_small, ws->rn64, sizeof(double) * nc * S, st));
     BLOCKOA_CUDA(cudaStreamSynchronize(st));
     int n_active = 0;
     for (int c = 0; c < nc; ++c) {
@@ -1768,7 +1768,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       g_launches += (long long)loop_kernels(ch) * check_every;
       for (int i = 0; i < loop_kernels(ch); ++i) add_launches(op, loop_class(ch, i), check_every);
       BLOCKOA_CUDA(cudaGraphLaunch(ws->graph, st));
-      BLOCKOA_CUDA(cudaMemcpyAsync(ws->h_state, ws->state, sizeof(ChipSolveState) * nc, cudaMemcpyDeviceToHost, st));
+      BLOCKOA_CUDA(read_small(ws->h_state, ws->state, sizeof(ChipSolveState) * nc, st));
       BLOCKOA_CUDA(cudaStreamSynchronize(st));
       for (int i = 0; i < loop_kernels(ch); ++i) {   // live timing of this chunk's first iteration
         float ms = 0.f;

@@ -227,7 +227,7 @@ int launch_combine_tc(blockoa_operator *op, const double *U, const double *C, fl
   int rc = pool_alloc(op, &d_tiles, sizeof(TcTile) * tiles.size(), st);
   if (!rc) rc = pool_alloc(op, &uimg, a_bytes * tiles.size(), st);
   if (!rc) rc = pool_alloc(op, &cimg, b_bytes * n_chunks * op->n_chips, st);
-  if (!rc) rc = pool_alloc(op, &err, sizeof(int), st);
+  if (!rc) rc = pool_alloc(op, &err, 8, st);   // one int flag, read back as one 8-byte word
   auto done = [&](int code) {
     pool_free(d_tiles, st); pool_free(uimg, st); pool_free(cimg, st); pool_free(err, st);
     return code;
@@ -242,7 +242,7 @@ int launch_combine_tc(blockoa_operator *op, const double *U, const double *C, fl
   }
   cudaError_t e = cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(TcTile) * tiles.size(),
                                   cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 8, st);
   if (e == cudaSuccess) {
     cudaEvent_t ev0, ev1;
     time_begin(op, st, &ev0);
@@ -259,11 +259,11 @@ int launch_combine_tc(blockoa_operator *op, const double *U, const double *C, fl
     time_end(op, st, KC_COMBINE_TC, ev1);
   }
   if (e != cudaSuccess) return done(cuda_status(e, "combine_tc"));
-  int h_err = 0;
-  e = cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  op->h_flag[0] = 0;
+  e = read_small(op->h_flag, err, 8, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return done(cuda_status(e, "combine_tc"));
-  return done(h_err ? BLOCKOA_ERR_TIMEOUT : BLOCKOA_OK);
+  return done(op->h_flag[0] ? BLOCKOA_ERR_TIMEOUT : BLOCKOA_OK);
 }
 
 }  // namespace blockoa

@@ -43,6 +43,7 @@ struct ChipSolveState {
   int rank;         // kept columns in the current factorisation
   int pad0, pad1, pad2;
 };
+static_assert(sizeof(ChipSolveState) % 8 == 0, "chip states are read back in 8-byte words");
 
 // Kernel classes with live event timing.
 enum KernelClass {
@@ -116,6 +117,7 @@ struct blockoa_operator {
   int n_apply_blocks = 0;
   void *apply_vec_blocks = nullptr;      // same for the vectorised form
   int n_apply_vec_blocks = 0;
+  int *h_flag = nullptr;                 // pinned status word for small device -> host reads
 };
 
 namespace blockoa {
@@ -129,6 +131,14 @@ int cuda_status(cudaError_t e, const char *where);  // BLOCKOA_OK or ERR_CUDA/ER
     cudaError_t e_ = (call);                                 \
     if (e_ != cudaSuccess) return ::blockoa::cuda_status(e_, #call); \
   } while (0)
+
+// Small device -> host reads (a few KB) into pinned host memory, done by a
+// one-block kernel writing through the mapping rather than by a copy:
+// copies of other streams (e.g. results streaming back to the host) then
+// never delay the read, which the solver issues at every convergence poll.
+// `bytes` must be a multiple of 8 and both addresses 8-byte aligned; the
+// data is on the host once `st` has been synchronised.
+cudaError_t read_small(void *host_pinned, const void *dev, size_t bytes, cudaStream_t st);
 
 // Stream-ordered allocation from the operator's pool.
 int pool_alloc(blockoa_operator *op, void **p, size_t bytes, cudaStream_t st);

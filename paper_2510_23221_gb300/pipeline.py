@@ -91,3 +91,66 @@ def chip_block(res: Result, chip: int, which: str = "U"):
     sz = res.op.sizes[chip]
     buf = getattr(res, which)
     return buf[sz["off"] * res.s:(sz["off"] + sz["n"]) * res.s].view(sz["n"], res.s)
+
+
+class PairStreamer:
+    """The hot path over a stream of same-shaped inputs, with each step's
+    pairs (T, q) copied to host memory while the next step computes.
+
+    Each ``step`` copies its inputs from (pinned) host arrays, re-discretises
+    the operator in place, solves, combines and applies into one of two
+    device result buffers, then queues the device-to-host copy of that
+    buffer on a copy stream; the step after next waits for that copy before
+    reusing the buffer.  Compute runs on a stream of its own: work on the
+    legacy default stream would wait for every pending copy.  Host outputs
+    must be pinned for the copies to overlap.  ``finish`` makes the caller's
+    stream wait for all queued work.
+    """
+
+    def __init__(self, op: bo.Operator, s: int, M: int, precision: int, chunk_bytes: int = 256 << 20):
+        import torch
+        n = op.n_total
+        dev = torch.device("cuda")
+        self.op, self.s, self.M, self.precision = op, s, M, precision
+        self.B = torch.empty(n * s, dtype=torch.float64, device=dev)
+        self.U = torch.empty_like(self.B)
+        fdt = field_dtype(precision)
+        self.T = [torch.empty(n * M, dtype=fdt, device=dev) for _ in range(2)]
+        self.q = [torch.empty(n * M, dtype=fdt, device=dev) for _ in range(2)]
+        self.compute_stream = torch.cuda.Stream(device=dev)
+        self.copy_stream = torch.cuda.Stream(device=dev)
+        self.ready = [torch.cuda.Event() for _ in range(2)]
+        self.freed = [torch.cuda.Event() for _ in range(2)]
+        self.chunk = max(1, chunk_bytes // self.T[0].element_size())
+        self.k = 0
+
+    def step(self, chips, dens_h, C_h, dens_d, C_d, T_h, q_h, **solve_kw):
+        import torch
+        b = self.k % 2
+        cs = self.compute_stream
+        cs.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cs):
+            if self.k >= 2:
+                cs.wait_event(self.freed[b])
+            dens_d.copy_(dens_h, non_blocking=True)
+            C_d.copy_(C_h, non_blocking=True)
+            bo.reassemble(self.op, chips)
+            bo.build_rhs(self.op, dens_d, self.B, self.s)
+            stats = bo.block_solve(self.op, self.B, self.U, self.s, precision=self.precision, **solve_kw)
+            bo.combine(self.op, self.U, C_d, self.T[b], self.s, self.M, self.precision)
+            bo.apply_operator(self.op, self.T[b], self.q[b], self.M, self.precision)
+            self.ready[b].record(cs)
+        self.copy_stream.wait_event(self.ready[b])
+        with torch.cuda.stream(self.copy_stream):
+            for src, dst in ((self.T[b], T_h), (self.q[b], q_h)):
+                for i in range(0, src.numel(), self.chunk):
+                    dst[i:i + self.chunk].copy_(src[i:i + self.chunk], non_blocking=True)
+            self.freed[b].record(self.copy_stream)
+        self.k += 1
+        return stats
+
+    def finish(self):
+        import torch
+        cur = torch.cuda.current_stream()
+        cur.wait_stream(self.compute_stream)
+        cur.wait_stream(self.copy_stream)

@@ -45,6 +45,18 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(bo.EXPORTED) <= set(_declared())
 
 
+def test_library_resolves_all_its_own_symbols(lib):
+    """Every symbol the library references is defined or comes from a system
+    or CUDA library: loading with immediate binding fails otherwise (ctypes
+    binds lazily, so a missing internal definition would only surface at the
+    first call on a GPU)."""
+    import subprocess
+    import sys
+    code = f"import ctypes, os; ctypes.CDLL({bo.LIB_PATH!r}, mode=os.RTLD_NOW)"
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+
+
 def test_status_strings(lib):
     assert bo.status_string(bo.OK) == "ok"
     assert "invalid" in bo.status_string(bo.ERR_INVALID)
