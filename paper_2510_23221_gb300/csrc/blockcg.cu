@@ -440,14 +440,23 @@ spmm_gram_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T 
       T pc[4][V], qv[4][V], rv[4][V];
       load_block<T, S>(pc, P, base + cl0, u.end, j0);
       load_block<T, S>(rv, R, base + cl0, u.end, j0);
+      // grid position of the first of this thread's four consecutive cells;
+      // the others follow by increments (one division per tile, not per cell)
+      const int loc0 = (int)(base + cl0 - ch.off);
+      int x = loc0 % nx, y = (loc0 / nx) % ny, z = loc0 / nxny;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const long long a = base + cl0 + k;
+        if (k > 0) {
+          ++x;
+          while (x >= nx) {
+            x -= nx;
+            if (++y >= ny) { y = 0; ++z; }
+          }
+        }
 #pragma unroll
         for (int v = 0; v < V; ++v) qv[k][v] = T(0);
         if (a < u.end) {
-          const int loc = (int)(a - ch.off);
-          const int x = loc % nx, y = (loc / nx) % ny, z = loc / nxny;
           const auto c4 = coef_ld(g, a);
 #pragma unroll
           for (int v = 0; v < V; ++v) qv[k][v] = c4.w * pc[k][v];
@@ -1007,6 +1016,16 @@ struct ColGeom {
     if (z >= ch.nz || x >= ch.nx) return -1;
     return ch.off + (long long)z * ch.nx * ch.ny + (long long)y * ch.nx + x;
   }
+  // the same split in two: per tile, its first cell (z = 0, dx = 0) and the
+  // x positions it has inside the chip; per slot, (z, dx)
+  __device__ __forceinline__ void tile(const ChipDev &ch, int c, long long &cell0, int &xin) const {
+    const int xb = (c % tiles_x) * xt;
+    cell0 = ch.off + (long long)(c / tiles_x) * ch.nx + xb;
+    xin = ch.nx - xb;
+  }
+  __device__ __forceinline__ static long long slot_cell(const ChipDev &ch, long long cell0, int xin, int z, int dx) {
+    return (z < ch.nz && dx < xin) ? cell0 + (long long)z * ch.nx * ch.ny + dx : -1;
+  }
 };
 
 // The update kernel with z-line preconditioning: as update_gram, over column
@@ -1068,10 +1087,21 @@ update_zline_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const
     ++run;
     const ChipDev ch = chips[u.chip];
     const ColGeom cg(ch, G::TC);
+    // (z, dx) of this thread's four slots and of its tridiagonal-factor slot
+    int sz[4], sdx[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      sz[k] = (cl0 + k) / cg.xt;
+      sdx[k] = (cl0 + k) - sz[k] * cg.xt;
+    }
+    const int fz = t / cg.xt, fdx = t - fz * cg.xt;
     for (long long ct = u.begin; ct < u.end; ++ct) {
+      long long cell0;
+      int xin;
+      cg.tile(ch, (int)ct, cell0, xin);
       long long cell[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) cell[k] = cg.cell(ch, (int)ct, cl0 + k);
+      for (int k = 0; k < 4; ++k) cell[k] = ColGeom::slot_cell(ch, cell0, xin, sz[k], sdx[k]);
       auto ld = [&](T (&x)[4][V], const T *src) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -1096,10 +1126,10 @@ update_zline_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const
       }
       // the tridiagonal factors of the tile's slots
       for (int sl = t; sl < G::TC; sl += 256) {
-        const long long a = cg.cell(ch, (int)ct, sl);
+        const int z = sl == t ? fz : sl / cg.xt, dx = sl == t ? fdx : sl % cg.xt;
+        const long long a = ColGeom::slot_cell(ch, cell0, xin, z, dx);
         T e = T(0), f = T(0), iv = T(0);
         if (a >= 0) {
-          const int z = sl / cg.xt;
           iv = zinv[a];
           f = coef_ld(g, a).z * iv;
           if (z > 0) e = coef_ld(g, a - (long long)ch.nx * ch.ny).z;
@@ -1118,13 +1148,26 @@ update_zline_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const
         ld4<T, G::LD>(p4, sP, i, cl0);
         ld4<T, G::LD>(q4, sQ, i, cl0);
         vload<T>(av, sA + i * S + j0);
+        if constexpr (sizeof(T) == 4) {   // paired FMAs over adjacent columns
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+          for (int k = 0; k < 4; ++k)
 #pragma unroll
-          for (int v = 0; v < V; ++v) {
-            xv[k][v] += p4[k] * av[v];
-            rv[k][v] -= q4[k] * av[v];
-          }
+            for (int v = 0; v < V; v += 2) {
+              const float2 a2 = make_float2(av[v], av[v + 1]);
+              float2 x2 = __ffma2_rn(make_float2(p4[k], p4[k]), a2, make_float2(xv[k][v], xv[k][v + 1]));
+              float2 r2 = __ffma2_rn(make_float2(-q4[k], -q4[k]), a2, make_float2(rv[k][v], rv[k][v + 1]));
+              xv[k][v] = x2.x; xv[k][v + 1] = x2.y;
+              rv[k][v] = r2.x; rv[k][v + 1] = r2.y;
+            }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              xv[k][v] += p4[k] * av[v];
+              rv[k][v] -= q4[k] * av[v];
+            }
+        }
       }
       st(X, xv);
       st(R, rv);
