@@ -53,8 +53,8 @@ METRIC = "verified sample pairs/s at <=1e-6 rel err, chosen vs plain FP64, one G
 UNIT = "pairs/s"
 RTOL = 1e-6
 PAIR_TOL = 1e-6
-# inner tolerance of each float32 block-CG pass of the chosen (z-line) form;
-# two refinement passes at 1e-4 beat three at the library default of 1e-3
+# inner tolerance of each float32 block-CG pass of the chosen (z-line) form
+# (the library default; at 1e-3 it takes three refinement passes, not two)
 INNER_RTOL = 1e-4
 # convergence polls of the chosen form: every 16 block-CG iterations (one
 # CUDA graph of 16 iterations per poll; fewer host round trips)

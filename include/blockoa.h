@@ -69,7 +69,10 @@ typedef struct {
   const double *layer_k;      /* [n_layers] conductivity, W/m/K, > 0; ignored if k_cell != NULL */
   const double *k_cell;       /* optional [nz][ny][nx] per-cell conductivity, W/m/K */
   double dx, dy;              /* lateral cell size, m, > 0 */
-  double h_top, h_bottom, h_side; /* convective coefficients, W/m^2/K; 0 = adiabatic */
+  double h_top, h_bottom, h_side; /* convective coefficients, W/m^2/K; 0 = adiabatic;
+                                     * +INFINITY = Dirichlet face held at t_ambient
+                                     * (theta = 0 on the face: Gb = 2 k A / d, the
+                                     * half-cell conductance to the face) */
   double t_ambient;           /* K; reporting only (unknowns are excess temperature) */
 } blockoa_chip_desc;
 
@@ -77,7 +80,7 @@ typedef struct {
   double rtol;          /* per-column ||B_j - A X_j|| / ||B_j|| target, > 0 */
   int maxiter;          /* limit on block iterations (summed over refinement steps) */
   int precision;        /* blockoa_precision */
-  double inner_rtol;    /* MIXED: residual reduction asked of each float32 inner solve (<= 0: 1e-3) */
+  double inner_rtol;    /* MIXED: residual reduction asked of each float32 inner solve (<= 0: 1e-4) */
   int max_refine;       /* MIXED: limit on float64 refinement steps (<= 0: 12) */
   double deflate_tol;   /* pivot threshold on the scaled Gram (<= 0: 1e-14 FP64, 1e-6 float32 inner) */
   const double *x0;     /* device [n_total][s] initial guess, or NULL for zero */

@@ -52,7 +52,10 @@ def _series(area, half_a, k_a, half_b, k_b):
 
 
 def _robin(area, d, k, h):
-    """Boundary conductance of a convective face: area / (d/(2k) + 1/h)."""
+    """Boundary conductance of a convective face: area / (d/(2k) + 1/h).
+
+    h = inf is a face held at the reference temperature (Dirichlet, theta =
+    0 on the face): 1/h = 0 leaves the half-cell conductance 2 k area / d."""
     return area / (d / (2.0 * k) + 1.0 / h)
 
 

@@ -330,7 +330,8 @@ extern "C" const char *blockoa_status_string(int status) {
 extern "C" const char *blockoa_last_error(void) { return g_last_error; }
 
 static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
-static bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
+// film coefficient: >= 0, and +inf for a face held at the reference temperature
+static bool film_ok(double v) { return v >= 0.0 && !std::isnan(v); }
 
 namespace blockoa {
 __global__ void read_small_kernel(const unsigned long long *__restrict__ src, unsigned long long *dst, int n) {
@@ -368,7 +369,7 @@ static int build_tables(const blockoa_chip_desc *chips, int n_chips, ChipTables 
     if (d.nx < 1 || d.ny < 1 || d.n_layers < 1 || !d.layer_nz || !d.layer_dz) return BLOCKOA_ERR_INVALID;
     if (!d.k_cell && !d.layer_k) return BLOCKOA_ERR_INVALID;
     if (!finite_pos(d.dx) || !finite_pos(d.dy)) return BLOCKOA_ERR_INVALID;
-    if (!finite_nonneg(d.h_top) || !finite_nonneg(d.h_bottom) || !finite_nonneg(d.h_side))
+    if (!film_ok(d.h_top) || !film_ok(d.h_bottom) || !film_ok(d.h_side))
       return BLOCKOA_ERR_INVALID;
     long long nz = 0;
     ChipPhys ph;

@@ -1644,7 +1644,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
 
   const double rtol = o->rtol;
   const int maxiter = o->maxiter;
-  const double inner_rtol = prec == BLOCKOA_MIXED ? (o->inner_rtol > 0 ? o->inner_rtol : 1e-3) : 0.0;
+  const double inner_rtol = prec == BLOCKOA_MIXED ? (o->inner_rtol > 0 ? o->inner_rtol : 1e-4) : 0.0;
   const int max_refine = o->max_refine > 0 ? o->max_refine : 12;
   const double tol = o->deflate_tol > 0 ? o->deflate_tol : (prec == BLOCKOA_MIXED ? 1e-6 : 1e-14);
   const int check_every = o->check_every > 0 ? o->check_every : 8;

@@ -78,6 +78,7 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.blockoa_pair_check(None, None, None, 4, bo.FP64, None, None) == bo.ERR_INVALID
     assert lib.blockoa_build_rhs(None, None, None, 4, None) == bo.ERR_INVALID
     assert lib.blockoa_export_conductances(None, 0, None, None, None, None) == bo.ERR_INVALID
+    assert lib.blockoa_reassemble(None, None, 1, None) == bo.ERR_INVALID
     lib.blockoa_destroy(None)
 
 
@@ -86,7 +87,8 @@ def test_bad_chip_descriptors_rejected(lib):
     keep = []
     from paper_2510_23221_gb300 import synth
     chip = synth.random_small_chip(1, 3, 3, 2)
-    for field, value in (("dx", -1.0), ("h_top", float("nan")), ("dy", 0.0)):
+    for field, value in (("dx", -1.0), ("h_top", float("nan")), ("dy", 0.0), ("h_side", -1.0),
+                         ("h_bottom", float("-inf")), ("dx", float("inf"))):
         d = bo._desc(chip, keep)
         setattr(d, field, value)
         h = ct.c_void_p()

@@ -48,11 +48,15 @@ def small_chips():
         synth.random_small_chip(103, 9, 4, 3, h_top=0.0, h_side=5e3),
         synth.random_small_chip(104, 7, 6, 3, h_top=1e4, h_bottom=1e3, h_side=1e3, layer_nz=[2, 1, 3]),
         synth.reference_stack_chip(),
+        # faces held at the reference temperature (h = inf): all faces, and
+        # Robin top and bottom (h = 3e4) with held sides
+        synth.random_small_chip(107, 11, 7, 4, h_top=np.inf, h_bottom=np.inf, h_side=np.inf),
+        synth.random_small_chip(108, 13, 9, 3, h_top=3e4, h_bottom=3e4, h_side=np.inf),
     ]
 
 
 # ---------------------------------------------------------------- assembly / rhs
-@pytest.mark.parametrize("idx", range(5))
+@pytest.mark.parametrize("idx", range(len(small_chips())))
 def test_assemble_bitexact(idx):
     chip = small_chips()[idx]
     op = bo.assemble([chip])
@@ -91,7 +95,7 @@ def test_build_rhs_exact():
 
 
 # ---------------------------------------------------------------- operator action
-@pytest.mark.parametrize("idx", range(5))
+@pytest.mark.parametrize("idx", range(len(small_chips())))
 def test_apply_fp64(idx):
     chip = small_chips()[idx]
     M = 7
@@ -103,7 +107,7 @@ def test_apply_fp64(idx):
     assert np.all(relcols(q.cpu().numpy().reshape(M, -1), ref, axis=1) < 1e-13)
 
 
-@pytest.mark.parametrize("idx", range(5))
+@pytest.mark.parametrize("idx", range(len(small_chips())))
 def test_apply_fp32(idx):
     chip = small_chips()[idx]
     M = 9
@@ -200,7 +204,7 @@ def _solve(chips, B_list, s, precision, rtol, **kw):
 
 
 @pytest.mark.parametrize("precision", [bo.FP64, bo.MIXED])
-@pytest.mark.parametrize("idx", range(4))
+@pytest.mark.parametrize("idx", [0, 1, 2, 3, 5, 6])
 def test_block_solve_tiny_vs_dense(idx, precision):
     chip = small_chips()[idx]
     B = np.random.default_rng(idx).uniform(0, 1e-2, (chip.n, 3))

@@ -17,10 +17,13 @@ def _run_pins():
     """Run every pin once; return the names of the pins that failed."""
     failed = []
     checks = [
-        ("slab_chain", pins.test_slab_resistor_chain_closed_form),
-        ("slab_continuous", pins.test_slab_converges_to_continuous_solution),
-        ("ladder_x", lambda: pins.test_lateral_ladder_closed_form("x")),
-        ("ladder_y", lambda: pins.test_lateral_ladder_closed_form("y")),
+        ("slab_chain", lambda: pins.test_slab_resistor_chain_closed_form(2.5e4)),
+        ("slab_chain_held", lambda: pins.test_slab_resistor_chain_closed_form(np.inf)),
+        ("slab_continuous", lambda: pins.test_slab_converges_to_continuous_solution(1e4)),
+        ("slab_continuous_held", lambda: pins.test_slab_converges_to_continuous_solution(np.inf)),
+        ("ladder_x", lambda: pins.test_lateral_ladder_closed_form("x", 4e4)),
+        ("ladder_y", lambda: pins.test_lateral_ladder_closed_form("y", 4e4)),
+        ("ladder_x_held", lambda: pins.test_lateral_ladder_closed_form("x", np.inf)),
         ("rhs", pins.test_rhs_total_power_and_placement),
         ("finite_termination", pins.test_finite_termination),
         ("textbook_cg", pins.test_single_column_equals_textbook_cg),
@@ -43,6 +46,7 @@ def _run_pins():
 
 REAL = {name: getattr(orc, name) for name in
         ("rhs", "block_cg", "face_conductances", "_gram_solve", "_series")}
+REAL_ROBIN = orc._robin
 
 
 def test_unmutated_oracle_passes_every_pin():
@@ -59,6 +63,11 @@ def _mut_robin_no_half_cell(area, d, k, h):
 
 def _mut_robin_full_cell(area, d, k, h):
     return area / (d / k + 1.0 / h)
+
+
+def _mut_robin_held_as_adiabatic(area, d, k, h):
+    # a held face (h = inf) treated like an insulated one
+    return 0.0 * area if np.isinf(h) else REAL_ROBIN(area, d, k, h)
 
 
 def _mut_rhs_bottom_layer(chip, density):
@@ -110,6 +119,7 @@ MUTANTS = {
     "series_full_width": ("_series", _mut_series_full_width),
     "robin_no_half_cell": ("_robin", _mut_robin_no_half_cell),
     "robin_full_cell": ("_robin", _mut_robin_full_cell),
+    "robin_held_as_adiabatic": ("_robin", _mut_robin_held_as_adiabatic),
     "rhs_bottom_layer": ("rhs", _mut_rhs_bottom_layer),
     "combine_no_transpose": ("combine", _mut_combine_no_transpose),
     "beta_sign": ("block_cg", _make_bcg_mutant("beta_sign")),
