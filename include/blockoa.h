@@ -90,6 +90,12 @@ typedef struct {
                            BLOCKOA_PRECOND_ZLINE (z-line: directions from M^-1 R, M the
                            tridiagonal coupling of each (x, y) cell column) */
   int small_solve;      /* BLOCKOA_SMALL_AUTO or BLOCKOA_SMALL_FP64_CHOLESKY (below) */
+  int independent;      /* 0: block CG (the s columns share one Krylov space);
+                           1: the s columns iterate as s independent (single
+                           right-hand side) CG solves -- the per-sample "direct"
+                           baseline: every off-diagonal entry of Gamma, P^T R and
+                           Q^T Z is dropped, so alpha_jj = (p_j . r_j) / (p_j . A p_j)
+                           and beta_jj = -(A p_j . z_j) / (p_j . A p_j) */
 } blockoa_solve_opts;
 
 enum { BLOCKOA_PRECOND_NONE = 0, BLOCKOA_PRECOND_JACOBI = 1, BLOCKOA_PRECOND_ZLINE = 2 };

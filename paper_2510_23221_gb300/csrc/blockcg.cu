@@ -212,7 +212,7 @@ __device__ __forceinline__ void gram_tile(T *acc, const T *A, const T *B, int i0
 // one float64 atomic per CTA; float64 arithmetic runs at 1/64 of the float32
 // rate on this part.
 template <typename T, int S>
-__device__ void gram_flush(const T *acc, double *red, double *dst) {
+__device__ void gram_flush(const T *acc, double *red, double *dst, bool diag) {
   using G = BK<T, S>;
   const int t = threadIdx.x;
   const int g = t / G::NT, w = t % G::NT;
@@ -222,6 +222,7 @@ __device__ void gram_flush(const T *acc, double *red, double *dst) {
   for (int e = 0; e < 16; ++e) rt[g * S * S + (i0 + e / 4) * S + j0 + (e % 4)] = acc[e];
   __syncthreads();
   for (int e = t; e < S * S; e += 256) {
+    if (diag && e / S != e % S) continue;   // independent columns: diagonal only
     if constexpr (sizeof(T) == 4) {
       float hi = 0.f, lo = 0.f;
       for (int gg = 0; gg < G::NG; ++gg) {
@@ -243,7 +244,7 @@ __device__ void gram_flush(const T *acc, double *red, double *dst) {
 
 // Flush when the first NG/2 groups hold P^T Q partials and the rest P^T R.
 template <typename T, int S>
-__device__ void gram_flush_split(const T *acc, double *red, double *dst_a, double *dst_b) {
+__device__ void gram_flush_split(const T *acc, double *red, double *dst_a, double *dst_b, bool diag) {
   using G = BK<T, S>;
   const int t = threadIdx.x;
   const int g = t / G::NT, w = t % G::NT;
@@ -254,6 +255,7 @@ __device__ void gram_flush_split(const T *acc, double *red, double *dst_a, doubl
   __syncthreads();
   constexpr int H = G::NG / 2;
   for (int e = t; e < S * S; e += 256) {
+    if (diag && e / S != e % S) continue;   // independent columns: diagonal only
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       T hi = T(0), lo = T(0);
@@ -417,10 +419,10 @@ spmm_gram_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T 
     const int chip = ui < us.n_units ? us.units[ui].chip : -1;
     if (run > 0 && chip != cur) {   // flush the running chip
       if constexpr (SPLIT) {
-        gram_flush_split<T, S>(acc, red, A.gram + (long long)cur * S * S, A.rho + (long long)cur * S * S);
+        gram_flush_split<T, S>(acc, red, A.gram + (long long)cur * S * S, A.rho + (long long)cur * S * S, A.diag);
       } else {
-        gram_flush<T, S>(acc, red, A.gram + (long long)cur * S * S);
-        gram_flush<T, S>(acc + 16, red, A.rho + (long long)cur * S * S);
+        gram_flush<T, S>(acc, red, A.gram + (long long)cur * S * S, A.diag);
+        gram_flush<T, S>(acc + 16, red, A.rho + (long long)cur * S * S, A.diag);
       }
       // mixed form: the flush that completes the chip sweeps Gamma and forms alpha
       if constexpr (sizeof(T) == 4) {
@@ -501,7 +503,7 @@ __device__ __forceinline__ void update_flush(const T *aw, const T *rn, double *r
   using G = BK<T, S>;
   constexpr int V = G::V;
   const int t = threadIdx.x;
-  gram_flush<T, S>(aw, red, A.wg + (long long)c * S * S);
+  gram_flush<T, S>(aw, red, A.wg + (long long)c * S * S, A.diag);
   T *rt = reinterpret_cast<T *>(red);
 #pragma unroll
   for (int v = 0; v < V; ++v) rt[t * V + v] = rn[v];
@@ -1335,7 +1337,7 @@ struct SolveWS {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t tev[kMaxLoopKernels + 1] = {};   // recorded around the kernels of each chunk's first iteration
-  int graph_iters = 0, graph_maxiter = -1, graph_s = -1, graph_pc = -1, graph_ch = -1;
+  int graph_iters = 0, graph_maxiter = -1, graph_s = -1, graph_pc = -1, graph_ch = -1, graph_diag = -1;
   double graph_tol = -1.0;
   std::vector<void *> allocs;
 };
@@ -1663,11 +1665,13 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
   sa.alpha = ws->alpha; sa.beta = ws->beta;
   sa.ticket = ws->ticket; sa.unit_count = ws->unit_count; sa.zunit_count = ws->zunit_count;
   sa.n_chips = nc; sa.tail = ch ? 0 : 1;
+  sa.diag = o->independent ? 1 : 0;
   sa.s = s; sa.maxiter = maxiter; sa.tol = tol;
 
   // Build (or reuse) the graph of `check_every` iterations.
   if (!ws->graph || ws->graph_iters != check_every || ws->graph_maxiter != maxiter ||
-      ws->graph_s != s || ws->graph_tol != tol || ws->graph_pc != pc || ws->graph_ch != (int)ch) {
+      ws->graph_s != s || ws->graph_tol != tol || ws->graph_pc != pc || ws->graph_ch != (int)ch ||
+      ws->graph_diag != sa.diag) {
     if (ws->graph) { cudaGraphExecDestroy(ws->graph); ws->graph = nullptr; }
     cudaGraph_t graph = nullptr;
     for (int i = 0; i <= kMaxLoopKernels; ++i)
@@ -1697,6 +1701,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     ws->graph_tol = tol;
     ws->graph_pc = pc;
     ws->graph_ch = (int)ch;
+    ws->graph_diag = sa.diag;
   }
 
   // Inputs: padded B and X0, ||B_j||^2.

@@ -61,6 +61,7 @@ struct SmallArgs {
   const int *zunit_count; // [chip] column-tile units per chip of the z-line update
   int n_chips;
   int tail;         // 1: the Gram kernels' last CTAs solve (mixed form, sweep)
+  int diag;         // 1: independent columns -- only the diagonals of Gamma, rho, W accumulate
   int s;            // caller's columns (for deflation counts)
   int maxiter;      // limit on total iterations per chip
   double tol;       // deflation threshold on scaled pivots

@@ -369,6 +369,30 @@ def test_reassemble_in_place_matches_fresh_assembly():
         assert np.array_equal(got[k], ref[k]), k
 
 
+@pytest.mark.parametrize("precision", [bo.FP64, bo.MIXED])
+def test_independent_columns_are_single_rhs_cg(precision):
+    """independent=True runs the s columns as s separate CG solves (the
+    per-sample baseline): the solution matches a dense solve; in float64 the
+    chip's iteration count is the largest single-column CG count of the
+    oracle (within 3), and the block solve of the same columns needs fewer
+    iterations (block Krylov shares one space across the columns)."""
+    chip = synth.random_small_chip(109, 17, 13, 4)
+    s = 6
+    rng = np.random.default_rng(11)
+    B = np.stack([synth.rect_power_map(rng, chip.nx, chip.ny) for _ in range(s)])
+    Bc = orc.rhs(chip, B)
+    (X,), (st,) = _solve([chip], [Bc], s, precision, 1e-10, independent=True)
+    assert st.status == bo.OK and st.relres_max <= 1e-10
+    A = orc.assemble(chip)
+    dense = np.linalg.solve(A.toarray(), Bc)
+    assert np.all(relcols(X, dense) < 1e-7)
+    if precision == bo.FP64:
+        single = [orc.block_cg(A, Bc[:, j:j + 1], rtol=1e-10)[1]["iters"] for j in range(s)]
+        assert abs(st.iters - max(single)) <= 3, (st.iters, single)
+        (_,), (stb,) = _solve([chip], [Bc], s, precision, 1e-10)
+        assert stb.iters < st.iters, (stb.iters, st.iters)
+
+
 def test_zline_needs_columns_that_fit_a_tile():
     chip = synth.random_small_chip(106, 3, 3, 70)          # 70 cells in z > the 64-cell tile at s = 64
     op = bo.assemble([chip])
