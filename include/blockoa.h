@@ -205,6 +205,21 @@ int blockoa_combine(blockoa_operator *op, const double *U, const double *C, void
                     int M, int dtype, blockoa_stream stream);
 
 /*
+ * Operator action on the basis, AU = A U (Eq. 6 applied to the s basis
+ * columns), float64.  U, AU: device float64 [n_total][s], cell-major like
+ * blockoa_block_solve's X; they must not overlap.  By linearity
+ * A (U C) = (A U) C, so blockoa_combine(op, AU, C, q, ...) yields the
+ * operator action of T = U C carrying only the combination's rounding:
+ * with float32 fields it is within ~1e-7 of A applied to the exact U C,
+ * where blockoa_apply_operator on a float32 T inherits T's storage error
+ * amplified by A (the q of the pair (T, q) -- consistent with the stored
+ * T -- comes from blockoa_apply_operator).
+ * Errors: ERR_INVALID (s < 1 or s > 4096, NULL pointers), ERR_OOM, ERR_CUDA.
+ */
+int blockoa_apply_basis(const blockoa_operator *op, const double *U, double *AU, int s,
+                        blockoa_stream stream);
+
+/*
  * Operator action q = A T (Eq. 6, Sec. III-C) on M fields of every chip.
  * T, q: device fields [chip][M][n_c]; float64 for FP64, float32 for MIXED.
  * T and q must not overlap.

@@ -18,8 +18,14 @@ batches of 64 independent columns (the widest block this library solves
 at once); a sample is verified when its float64 true residual is <= 1e-6.
 The basis route (assemble, s basis solves, T = U C, q = A T for M fields)
 is timed on the same chip with the same verification rule applied to its
-basis.  Both are reported as verified pairs per second.  Prints one JSON
-line per measurement.
+basis.  Both are reported as verified pairs per second.
+
+Part 3 (q by linearity): on the basis of part 2, q = (A U) C
+(blockoa_apply_basis + blockoa_combine) against q = A T on the float32 T
+(blockoa_apply_operator): time, and the largest e_q of each against a
+float64 reference (float64 combination and operator action of the same U).
+
+Prints one JSON line per measurement.
 """
 from __future__ import annotations
 
@@ -122,6 +128,35 @@ def main():
     print(json.dumps({"part": "throughput", "chip": a.chip, "rtol": tol, "form": "chosen",
                       "direct_method": direct, "basis_route": basis,
                       "speedup": round(basis["pairs_per_s"] / max(direct["pairs_per_s"], 1e-9), 1)}), flush=True)
+
+    # ---- part 3: q by linearity, q = (A U) C, against q = A T on the float32 T
+    del T, q
+    T = torch.empty(n * a.M, dtype=torch.float32, device=dev)
+    q_apply = torch.empty_like(T)
+    q_lin = torch.empty_like(T)
+    AU = torch.empty(n * s, dtype=torch.float64, device=dev)
+    bo.combine(op, U, inputs.C, T, s, a.M, bo.MIXED)
+    _, ms_apply = timed(lambda: bo.apply_operator(op, T, q_apply, a.M, bo.MIXED))
+
+    def linear():
+        bo.apply_basis(op, U, AU, s)
+        bo.combine(op, AU, inputs.C, q_lin, s, a.M, bo.MIXED)
+
+    _, ms_lin = timed(linear)
+    # float64 reference of the same basis: T64 = U C and q64 = A T64 in float64
+    T64 = torch.empty(n * a.M, dtype=torch.float64, device=dev)
+    q64 = torch.empty_like(T64)
+    bo.combine(op, U, inputs.C, T64, s, a.M, bo.FP64)
+    bo.apply_operator(op, T64, q64, a.M, bo.FP64)
+    ref = q64.view(a.M, n)
+
+    def e_q(x):
+        d = torch.linalg.vector_norm(x.view(a.M, n).double() - ref, dim=1)
+        return float((d / torch.linalg.vector_norm(ref, dim=1)).max())
+
+    print(json.dumps({"part": "q_by_linearity", "chip": a.chip, "M": a.M,
+                      "apply_ms": round(ms_apply, 3), "linearity_ms": round(ms_lin, 3),
+                      "e_q_apply_max": e_q(q_apply), "e_q_linearity_max": e_q(q_lin)}), flush=True)
     op.close()
 
 

@@ -34,7 +34,7 @@ SMALL_FP64_CHOLESKY = 1
 
 EXPORTED = (
     "blockoa_assemble", "blockoa_reassemble", "blockoa_operator_size", "blockoa_operator_total", "blockoa_build_rhs",
-    "blockoa_block_solve", "blockoa_combine", "blockoa_apply_operator", "blockoa_pair_check",
+    "blockoa_block_solve", "blockoa_combine", "blockoa_apply_basis", "blockoa_apply_operator", "blockoa_pair_check",
     "blockoa_export_conductances", "blockoa_destroy", "blockoa_status_string",
     "blockoa_last_error", "blockoa_kernel_times", "blockoa_reset_kernel_times",
     "blockoa_launch_count",
@@ -91,6 +91,7 @@ def _lib():
                                             ct.POINTER(SolveStats), vp]
         lib.blockoa_combine.argtypes = [vp, vp, vp, vp, i, i, i, vp]
         lib.blockoa_apply_operator.argtypes = [vp, vp, vp, i, i, vp]
+        lib.blockoa_apply_basis.argtypes = [vp, vp, vp, i, vp]
         lib.blockoa_pair_check.argtypes = [vp, vp, vp, i, i, vp, vp]
         lib.blockoa_export_conductances.argtypes = [vp, i, vp, vp, vp, vp]
         lib.blockoa_destroy.argtypes = [vp]
@@ -264,6 +265,13 @@ def apply_operator(op: Operator, T, q, M: int, dtype: int, stream=None):
     tdt = torch.float64 if dtype == FP64 else torch.float32
     _check(_lib().blockoa_apply_operator(op.handle, _ptr(T, tdt, "T"), _ptr(q, tdt, "q"), M, dtype,
                                          _stream(stream)), "apply_operator")
+
+
+def apply_basis(op: Operator, U, AU, s: int, stream=None):
+    """AU = A U on a float64 [n][s] block (blockoa_apply_basis)."""
+    import torch
+    _check(_lib().blockoa_apply_basis(op.handle, _ptr(U, torch.float64, "U"), _ptr(AU, torch.float64, "AU"), s,
+                                      _stream(stream)), "apply_basis")
 
 
 def pair_check(op: Operator, T, q, M: int, dtype: int, e_pair, stream=None):

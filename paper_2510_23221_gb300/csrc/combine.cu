@@ -99,6 +99,12 @@ extern "C" int blockoa_combine(blockoa_operator *op, const double *U, const doub
   return launch_combine(op, U, C, T, s, M, dtype, (cudaStream_t)stream);
 }
 
+extern "C" int blockoa_apply_basis(const blockoa_operator *op, const double *U, double *AU, int s,
+                                   blockoa_stream stream) {
+  if (!op || !U || !AU || s < 1 || s > 4096) return BLOCKOA_ERR_INVALID;
+  return launch_apply_block64(op, U, AU, s, (cudaStream_t)stream);
+}
+
 extern "C" int blockoa_apply_operator(const blockoa_operator *op, const void *T, void *q, int M,
                                       int dtype, blockoa_stream stream) {
   if (!op || M < 0 || !valid_dtype(dtype)) return BLOCKOA_ERR_INVALID;

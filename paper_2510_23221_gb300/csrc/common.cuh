@@ -165,6 +165,8 @@ int launch_pair_check(const blockoa_operator *op, const void *T, const void *q, 
 // per-chip column norms ||R_j||^2 into rn2 [chip][S] (must be zeroed).
 int launch_residual64(const blockoa_operator *op, const double *B, const double *X, double *R,
                       int S, double *rn2, cudaStream_t st);
+// AU = A U, float64 block of s columns [n][s] (blockoa_apply_basis).
+int launch_apply_block64(const blockoa_operator *op, const double *U, double *AU, int s, cudaStream_t st);
 
 // blockcg.cu
 void free_solve_ws(void *ws);

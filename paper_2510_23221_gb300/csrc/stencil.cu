@@ -584,6 +584,53 @@ residual64_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ ch
   }
 }
 
+// AU = A U for a float64 block of s columns (any s), [n][s] cell-major; one
+// thread per (cell, column) entry of its unit.
+__global__ void __launch_bounds__(256)
+apply_block64_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chips,
+                     const double *__restrict__ g, const double *__restrict__ U, double *__restrict__ AU, int s) {
+  const Unit u = units[blockIdx.x];
+  const ChipDev ch = chips[u.chip];
+  const long long nxny = (long long)ch.nx * ch.ny;
+  const long long total = (u.end - u.begin) * s;
+  for (long long i = threadIdx.x; i < total; i += blockDim.x) {
+    const long long a = u.begin + i / s;
+    const int j = (int)(i % s);
+    const long long loc = a - ch.off;
+    const int x = (int)(loc % ch.nx);
+    const int y = (int)((loc / ch.nx) % ch.ny);
+    const int z = (int)(loc / nxny);
+    const double4 c4 = load_coef<double>(g, a);
+    const double c = U[a * s + j];
+    double r = c4.w * c;
+    if (x + 1 < ch.nx) r += c4.x * (c - U[(a + 1) * s + j]);
+    if (x > 0) r += load_coef<double>(g, a - 1).x * (c - U[(a - 1) * s + j]);
+    if (y + 1 < ch.ny) r += c4.y * (c - U[(a + ch.nx) * s + j]);
+    if (y > 0) r += load_coef<double>(g, a - ch.nx).y * (c - U[(a - ch.nx) * s + j]);
+    if (z + 1 < ch.nz) r += c4.z * (c - U[(a + nxny) * s + j]);
+    if (z > 0) r += load_coef<double>(g, a - nxny).z * (c - U[(a - nxny) * s + j]);
+    AU[a * s + j] = r;
+  }
+}
+
+int launch_apply_block64(const blockoa_operator *op, const double *U, double *AU, int s, cudaStream_t st) {
+  std::vector<Unit> units = make_units(op, 512);
+  blockoa_operator *mop = const_cast<blockoa_operator *>(op);
+  void *d_units = nullptr;
+  int rc = pool_alloc(mop, &d_units, sizeof(Unit) * units.size(), st);
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(d_units, units.data(), sizeof(Unit) * units.size(),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    g_launches += 1;
+    apply_block64_kernel<<<(unsigned)units.size(), 256, 0, st>>>((const Unit *)d_units, op->d_chips, op->g64,
+                                                                  U, AU, s);
+    e = cudaGetLastError();
+  }
+  pool_free(d_units, st);
+  return cuda_status(e, "apply_block64");
+}
+
 int launch_residual64(const blockoa_operator *op, const double *B, const double *X, double *R,
                       int S, double *rn2, cudaStream_t st) {
   std::vector<Unit> units = make_units(op, 1024);

@@ -189,6 +189,36 @@ def test_combine(s, M):
     assert np.all(relcols(T32.cpu().numpy().astype(np.float64).reshape(M, -1), ref, axis=1) < 1e-6)
 
 
+@pytest.mark.parametrize("precision", [bo.FP64, bo.MIXED])
+def test_q_by_linearity(precision):
+    """q = (A U) C -- blockoa_apply_basis then blockoa_combine -- equals the
+    oracle's A (U C) to the combination's rounding (1e-13 in float64, 1e-6
+    with float32 fields; the identity itself is pinned on the oracle), and
+    AU matches the oracle's sparse product to summation order."""
+    chip = synth.random_small_chip(7, 21, 13, 3)
+    s, M = 8, 40
+    rng = np.random.default_rng(5)
+    U = rng.standard_normal((chip.n, s)) * 10.0 ** rng.uniform(-3, 3, s)
+    C = synth.coefficients(rng, s, M)
+    op = bo.assemble([chip])
+    A = orc.assemble(chip)
+    AU = torch.empty(chip.n * s, dtype=torch.float64, device="cuda")
+    bo.apply_basis(op, cuda(U.ravel()), AU, s)
+    assert np.all(relcols(AU.cpu().numpy().reshape(-1, s), A @ U) < 1e-13)
+    q_ref = orc.apply_operator(A, orc.combine(U, C))
+    q = torch.empty(M * chip.n, dtype=torch.float64 if precision == bo.FP64 else torch.float32, device="cuda")
+    bo.combine(op, AU, cuda(C.ravel()), q, s, M, precision)
+    tol = 1e-13 if precision == bo.FP64 else 1e-6
+    assert np.all(relcols(q.cpu().numpy().astype(np.float64).reshape(M, -1), q_ref, axis=1) < tol)
+
+
+def test_apply_basis_rejects_bad_arguments():
+    op = bo.assemble([synth.random_small_chip(8, 5, 4, 2)])
+    with pytest.raises(bo.BlockoaError):
+        bo.apply_basis(op, torch.zeros(20 * 4, dtype=torch.float64, device="cuda"),
+                       torch.zeros(20 * 4, dtype=torch.float64, device="cuda"), 0)
+
+
 # ---------------------------------------------------------------- block solve
 def _solve(chips, B_list, s, precision, rtol, **kw):
     op = bo.assemble(chips)
