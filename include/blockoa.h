@@ -205,6 +205,32 @@ int blockoa_combine(blockoa_operator *op, const double *U, const double *C, void
                     int M, int dtype, blockoa_stream stream);
 
 /*
+ * Options of blockoa_combine_ex: the noise term epsilon of Eq. 5 (Sec.
+ * III-B).  With noise_amp > 0 every field value gets
+ *   T[m][a] += noise_amp * (2 u - 1),  u = (w >> 11) * 2^-53 in [0, 1),
+ * w = word (m % 4) of Philox4x64-10 (Salmon et al., SC 2011) with counter
+ * (a, m / 4, 0, 0) and key (noise_seed, 0), a the cell's index in the
+ * operator's concatenated numbering: a uniform perturbation in
+ * [-noise_amp, noise_amp) K that any kernel can reproduce.  MIXED (float32
+ * fields) takes u from the top 24 bits of w, u = (w >> 40) * 2^-24, in
+ * float32 (within noise_amp * 2^-23 of the float64 value).  The operator
+ * action of the stored (noisy) T stays exact, so pairs (T, A T) remain
+ * consistent.
+ */
+typedef struct {
+  uint64_t noise_seed;  /* Philox key word 0 */
+  double noise_amp;     /* K, >= 0; 0 = no noise */
+} blockoa_combine_opts;
+
+/*
+ * blockoa_combine with options (NULL opts: no noise, same as
+ * blockoa_combine).  Errors: as blockoa_combine, and ERR_INVALID for a
+ * negative or non-finite noise_amp.
+ */
+int blockoa_combine_ex(blockoa_operator *op, const double *U, const double *C, void *T, int s,
+                       int M, int dtype, const blockoa_combine_opts *opts, blockoa_stream stream);
+
+/*
  * Operator action on the basis, AU = A U (Eq. 6 applied to the s basis
  * columns), float64.  U, AU: device float64 [n_total][s], cell-major like
  * blockoa_block_solve's X; they must not overlap.  By linearity

@@ -22,6 +22,9 @@ against the paper:
 * ``combine``       -- new temperature fields T = U C (Eq. 5 without the
                        normalisation and noise terms; unknowns are excess
                        temperature, so any C keeps the boundary conditions).
+* ``noise``         -- the epsilon term of Eq. 5: uniform noise per cell and
+                       field from ``philox4x64_10``, a counter-based generator
+                       written from its published definition.
 * ``apply_operator``-- operator action q = A T (Eq. 6, Sec. III-C).
 * ``pair_errors``   -- relative L2 errors of generated pairs.
 
@@ -246,6 +249,46 @@ def block_cg(A, B, X0=None, rtol=1e-12, maxiter=10000, deflate_tol=1e-14,
 def combine(U, C) -> np.ndarray:
     """T [M][n]: field m is sum_i C[i, m] U[:, i]."""
     return (np.asarray(U, np.float64) @ np.asarray(C, np.float64)).T.copy()
+
+
+# ---------------------------------------------------------------- noise (Eq. 5's epsilon)
+_PHILOX_M = (0xD2E7470EE14C6C93, 0xCA5A826395121157)
+_PHILOX_W = (0x9E3779B97F4A7C15, 0xBB67AE8584CAA73B)
+_MASK64 = (1 << 64) - 1
+
+
+def philox4x64_10(counter, key):
+    """One block of the Philox4x64-10 generator (Salmon, Moraes, Dror, Shaw,
+    SC 2011), written from its definition with Python integers: ten rounds;
+    before every round after the first the key is bumped by the Weyl
+    constants; a round maps (c0, c1, c2, c3) to
+    (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))."""
+    c = [int(x) & _MASK64 for x in counter]
+    k0, k1 = (int(x) & _MASK64 for x in key)
+    for r in range(10):
+        if r > 0:
+            k0 = (k0 + _PHILOX_W[0]) & _MASK64
+            k1 = (k1 + _PHILOX_W[1]) & _MASK64
+        p0 = _PHILOX_M[0] * c[0]
+        p1 = _PHILOX_M[1] * c[2]
+        c = [(p1 >> 64) ^ c[1] ^ k0, p1 & _MASK64, (p0 >> 64) ^ c[3] ^ k1, p0 & _MASK64]
+    return c
+
+
+def noise(seed, cells, M, amp) -> np.ndarray:
+    """epsilon [M][len(cells)] of the combination: for global cell index a and
+    field m, word m % 4 of Philox4x64-10 at counter (a, m // 4, 0, 0) and key
+    (seed, 0) gives u = (w >> 11) 2^-53 in [0, 1) and epsilon = amp (2u - 1).
+    Plain loops: small cases only."""
+    out = np.empty((M, len(cells)))
+    for i, a in enumerate(cells):
+        for g in range((M + 3) // 4):
+            w = philox4x64_10((int(a), g, 0, 0), (seed, 0))
+            for j in range(4):
+                m = 4 * g + j
+                if m < M:
+                    out[m, i] = amp * (2.0 * ((w[j] >> 11) * 2.0 ** -53) - 1.0)
+    return out
 
 
 def apply_operator(A, T) -> np.ndarray:

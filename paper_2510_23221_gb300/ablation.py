@@ -23,7 +23,8 @@ basis.  Both are reported as verified pairs per second.
 Part 3 (q by linearity): on the basis of part 2, q = (A U) C
 (blockoa_apply_basis + blockoa_combine) against q = A T on the float32 T
 (blockoa_apply_operator): time, and the largest e_q of each against a
-float64 reference (float64 combination and operator action of the same U).
+float64 reference (float64 combination and operator action of the same U);
+and the cost of the combination's noise term on the same fields.
 
 Prints one JSON line per measurement.
 """
@@ -157,6 +158,11 @@ def main():
     print(json.dumps({"part": "q_by_linearity", "chip": a.chip, "M": a.M,
                       "apply_ms": round(ms_apply, 3), "linearity_ms": round(ms_lin, 3),
                       "e_q_apply_max": e_q(q_apply), "e_q_linearity_max": e_q(q_lin)}), flush=True)
+    # the epsilon term of Eq. 5 in the combination: its cost on M fields
+    _, ms_plain = timed(lambda: bo.combine(op, U, inputs.C, T, s, a.M, bo.MIXED))
+    _, ms_noise = timed(lambda: bo.combine(op, U, inputs.C, T, s, a.M, bo.MIXED, noise_seed=7, noise_amp=0.01))
+    print(json.dumps({"part": "combine_noise", "chip": a.chip, "M": a.M, "combine_ms": round(ms_plain, 3),
+                      "combine_with_noise_ms": round(ms_noise, 3)}), flush=True)
     op.close()
 
 

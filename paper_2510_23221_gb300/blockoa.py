@@ -34,7 +34,7 @@ SMALL_FP64_CHOLESKY = 1
 
 EXPORTED = (
     "blockoa_assemble", "blockoa_reassemble", "blockoa_operator_size", "blockoa_operator_total", "blockoa_build_rhs",
-    "blockoa_block_solve", "blockoa_combine", "blockoa_apply_basis", "blockoa_apply_operator", "blockoa_pair_check",
+    "blockoa_block_solve", "blockoa_combine", "blockoa_combine_ex", "blockoa_apply_basis", "blockoa_apply_operator", "blockoa_pair_check",
     "blockoa_export_conductances", "blockoa_destroy", "blockoa_status_string",
     "blockoa_last_error", "blockoa_kernel_times", "blockoa_reset_kernel_times",
     "blockoa_launch_count",
@@ -47,6 +47,10 @@ class ChipDesc(ct.Structure):
                 ("layer_k", ct.POINTER(ct.c_double)), ("k_cell", ct.POINTER(ct.c_double)),
                 ("dx", ct.c_double), ("dy", ct.c_double), ("h_top", ct.c_double),
                 ("h_bottom", ct.c_double), ("h_side", ct.c_double), ("t_ambient", ct.c_double)]
+
+
+class CombineOpts(ct.Structure):
+    _fields_ = [("noise_seed", ct.c_uint64), ("noise_amp", ct.c_double)]
 
 
 class SolveOpts(ct.Structure):
@@ -92,6 +96,7 @@ def _lib():
         lib.blockoa_combine.argtypes = [vp, vp, vp, vp, i, i, i, vp]
         lib.blockoa_apply_operator.argtypes = [vp, vp, vp, i, i, vp]
         lib.blockoa_apply_basis.argtypes = [vp, vp, vp, i, vp]
+        lib.blockoa_combine_ex.argtypes = [vp, vp, vp, vp, i, i, i, ct.POINTER(CombineOpts), vp]
         lib.blockoa_pair_check.argtypes = [vp, vp, vp, i, i, vp, vp]
         lib.blockoa_export_conductances.argtypes = [vp, i, vp, vp, vp, vp]
         lib.blockoa_destroy.argtypes = [vp]
@@ -253,11 +258,20 @@ def block_solve(op: Operator, B, X, s: int, rtol: float = 1e-12, maxiter: int = 
     return stats
 
 
-def combine(op: Operator, U, C, T, s: int, M: int, dtype: int, stream=None):
+def combine(op: Operator, U, C, T, s: int, M: int, dtype: int, stream=None, noise_seed: int = 0,
+            noise_amp: float = 0.0):
+    """T = U C; with noise_amp > 0, plus the epsilon term of Eq. 5
+    (blockoa_combine_ex: uniform in [-noise_amp, noise_amp) K from Philox)."""
     import torch
     tdt = torch.float64 if dtype == FP64 else torch.float32
-    _check(_lib().blockoa_combine(op.handle, _ptr(U, torch.float64, "U"), _ptr(C, torch.float64, "C"),
-                                  _ptr(T, tdt, "T"), s, M, dtype, _stream(stream)), "combine")
+    if noise_amp == 0.0:
+        _check(_lib().blockoa_combine(op.handle, _ptr(U, torch.float64, "U"), _ptr(C, torch.float64, "C"),
+                                      _ptr(T, tdt, "T"), s, M, dtype, _stream(stream)), "combine")
+        return
+    o = CombineOpts(noise_seed=int(noise_seed) & ((1 << 64) - 1), noise_amp=float(noise_amp))
+    _check(_lib().blockoa_combine_ex(op.handle, _ptr(U, torch.float64, "U"), _ptr(C, torch.float64, "C"),
+                                     _ptr(T, tdt, "T"), s, M, dtype, ct.byref(o), _stream(stream)),
+           "combine_ex")
 
 
 def apply_operator(op: Operator, T, q, M: int, dtype: int, stream=None):

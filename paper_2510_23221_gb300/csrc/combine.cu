@@ -4,9 +4,11 @@
 // FP64: float64 SIMT dot products of length s per output (this kernel).
 // MIXED: bfloat16x3 on the tensor cores (combine_tc.cu).
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "common.cuh"
+#include "noise.cuh"
 
 namespace blockoa {
 
@@ -18,12 +20,12 @@ struct CombTile {
 constexpr int CT_CELLS = 256;
 constexpr int CT_FIELDS = 32;
 
-// T[m][a] = sum_j U[a][j] C[j][m] for a 256-cell tile and 32 fields.
+// T[m][a] = sum_j U[a][j] C[j][m] (+ epsilon) for a 256-cell tile and 32 fields.
 template <typename T, int S>
 __global__ void __launch_bounds__(CT_CELLS)
 combine_simt_kernel(const CombTile *__restrict__ tiles, const ChipDev *__restrict__ chips,
                     const double *__restrict__ U, const double *__restrict__ C,
-                    T *__restrict__ Tout, int s, int M) {
+                    T *__restrict__ Tout, int s, int M, const NoiseSpec nz) {
   __shared__ T sC[S][CT_FIELDS];
   const CombTile tile = tiles[blockIdx.x];
   const ChipDev ch = chips[tile.chip];
@@ -41,17 +43,21 @@ combine_simt_kernel(const CombTile *__restrict__ tiles, const ChipDev *__restric
 #pragma unroll
   for (int j = 0; j < S; ++j) u[j] = j < s ? (T)U[a * s + j] : T(0);
   T *out = Tout + ch.off * (long long)M + (a - ch.off);
-  for (int f = 0; f < nf; ++f) {
-    T acc = T(0);
+  for (int f0 = 0; f0 < nf; f0 += 4) {   // m0 is a multiple of 4: one noise block per 4 fields
+    double eps[4] = {0.0, 0.0, 0.0, 0.0};
+    if (nz.amp > 0.0) noise4(nz, a, (m0 + f0) / 4, eps);
+    for (int f = f0; f < f0 + 4 && f < nf; ++f) {
+      T acc = T(0);
 #pragma unroll
-    for (int j = 0; j < S; ++j) acc += u[j] * sC[j][f];
-    out[(long long)(m0 + f) * ch.n] = acc;
+      for (int j = 0; j < S; ++j) acc += u[j] * sC[j][f];
+      out[(long long)(m0 + f) * ch.n] = acc + (T)eps[f - f0];
+    }
   }
 }
 
 int launch_combine(blockoa_operator *op, const double *U, const double *C, void *Tout, int s, int M,
-                   int dtype, cudaStream_t st) {
-  if (dtype == BLOCKOA_MIXED) return launch_combine_tc(op, U, C, (float *)Tout, s, M, st);
+                   int dtype, const NoiseSpec &nz, cudaStream_t st) {
+  if (dtype == BLOCKOA_MIXED) return launch_combine_tc(op, U, C, (float *)Tout, s, M, nz, st);
   std::vector<CombTile> tiles;
   for (int c = 0; c < op->n_chips; ++c)
     for (long long b = 0; b < op->chips[c].n; b += CT_CELLS)
@@ -66,7 +72,7 @@ int launch_combine(blockoa_operator *op, const double *U, const double *C, void 
     const CombTile *dt = (const CombTile *)d_tiles;
     const int S = s <= 8 ? 8 : s <= 16 ? 16 : s <= 32 ? 32 : 64;
 #define BLOCKOA_COMB(TT, SS) \
-  combine_simt_kernel<TT, SS><<<grid, CT_CELLS, 0, st>>>(dt, op->d_chips, U, C, (TT *)Tout, s, M)
+  combine_simt_kernel<TT, SS><<<grid, CT_CELLS, 0, st>>>(dt, op->d_chips, U, C, (TT *)Tout, s, M, nz)
     cudaEvent_t ev;
     time_begin(op, st, &ev);
     g_launches += 1;
@@ -90,13 +96,25 @@ using namespace blockoa;
 
 static bool valid_dtype(int d) { return d == BLOCKOA_FP64 || d == BLOCKOA_MIXED; }
 
-extern "C" int blockoa_combine(blockoa_operator *op, const double *U, const double *C, void *T,
-                               int s, int M, int dtype, blockoa_stream stream) {
+extern "C" int blockoa_combine_ex(blockoa_operator *op, const double *U, const double *C, void *T,
+                                  int s, int M, int dtype, const blockoa_combine_opts *opts,
+                                  blockoa_stream stream) {
   if (!op || s < 1 || s > 64 || M < 0 || !valid_dtype(dtype)) return BLOCKOA_ERR_INVALID;
+  NoiseSpec nz;
+  if (opts) {
+    if (!(opts->noise_amp >= 0.0) || !std::isfinite(opts->noise_amp)) return BLOCKOA_ERR_INVALID;
+    nz.seed = (unsigned long long)opts->noise_seed;
+    nz.amp = opts->noise_amp;
+  }
   if (M == 0) return BLOCKOA_OK;
   if (!U || !C || !T) return BLOCKOA_ERR_INVALID;
   if (dtype == BLOCKOA_FP64 && (M + CT_FIELDS - 1) / CT_FIELDS > 65535) return BLOCKOA_ERR_INVALID;
-  return launch_combine(op, U, C, T, s, M, dtype, (cudaStream_t)stream);
+  return launch_combine(op, U, C, T, s, M, dtype, nz, (cudaStream_t)stream);
+}
+
+extern "C" int blockoa_combine(blockoa_operator *op, const double *U, const double *C, void *T,
+                               int s, int M, int dtype, blockoa_stream stream) {
+  return blockoa_combine_ex(op, U, C, T, s, M, dtype, nullptr, stream);
 }
 
 extern "C" int blockoa_apply_basis(const blockoa_operator *op, const double *U, double *AU, int s,

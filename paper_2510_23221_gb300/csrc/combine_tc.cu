@@ -24,6 +24,7 @@
 
 #include "common.cuh"
 #include "tc.cuh"
+#include "noise.cuh"
 
 namespace blockoa {
 
@@ -110,7 +111,8 @@ __global__ void split_c_kernel(const double *__restrict__ C, int n_chips, int s,
 __global__ void __launch_bounds__(TC_THREADS)
 combine_tc_kernel(const TcTile *__restrict__ tiles, const ChipDev *__restrict__ chips,
                   const __nv_bfloat16 *__restrict__ uimg, const __nv_bfloat16 *__restrict__ cimg,
-                  float *__restrict__ Tout, int M, int Kdim, int n_chunks, int *__restrict__ err) {
+                  float *__restrict__ Tout, int M, int Kdim, int n_chunks, int *__restrict__ err,
+                  const NoiseSpec nz) {
   extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t a_bytes = TC_M * Kdim * 2, b_bytes = TC_N * Kdim * 2;
   unsigned char *sA = smem;
@@ -188,6 +190,15 @@ combine_tc_kernel(const TcTile *__restrict__ tiles, const ChipDev *__restrict__ 
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       const int fb = f0 + cc * 32;
       if (valid) {
+        if (nz.amp > 0.0) {   // epsilon of Eq. 5, 4 fields per generator block (fb is a multiple of 32)
+#pragma unroll 1
+          for (int g = 0; g < 8; ++g) {
+            float eps[4];
+            noise4f(nz, tile.cell0 + cell, (fb + 4 * g) / 4, eps);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) r[4 * g + i] = __float_as_uint(__uint_as_float(r[4 * g + i]) + eps[i]);
+          }
+        }
 #pragma unroll
         for (int i = 0; i < 32; ++i)
           if (fb + i < M) __stcs(out + (long long)(fb + i) * ch.n, __uint_as_float(r[i]));
@@ -208,7 +219,7 @@ combine_tc_kernel(const TcTile *__restrict__ tiles, const ChipDev *__restrict__ 
 }
 
 int launch_combine_tc(blockoa_operator *op, const double *U, const double *C, float *Tout, int s,
-                      int M, cudaStream_t st) {
+                      int M, const NoiseSpec &nz, cudaStream_t st) {
   const int Sp = tc_kpad(s), K = 3 * Sp;
   const int n_chunks = (M + TC_N - 1) / TC_N;
   std::vector<TcTile> tiles;
@@ -254,7 +265,7 @@ int launch_combine_tc(blockoa_operator *op, const double *U, const double *C, fl
     time_begin(op, st, &ev1);
     combine_tc_kernel<<<(unsigned)tiles.size(), TC_THREADS, smem, st>>>(
         (const TcTile *)d_tiles, op->d_chips, (const __nv_bfloat16 *)uimg,
-        (const __nv_bfloat16 *)cimg, Tout, M, K, n_chunks, (int *)err);
+        (const __nv_bfloat16 *)cimg, Tout, M, K, n_chunks, (int *)err, nz);
     e = cudaGetLastError();
     time_end(op, st, KC_COMBINE_TC, ev1);
   }

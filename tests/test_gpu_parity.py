@@ -212,6 +212,34 @@ def test_q_by_linearity(precision):
     assert np.all(relcols(q.cpu().numpy().astype(np.float64).reshape(M, -1), q_ref, axis=1) < tol)
 
 
+@pytest.mark.parametrize("precision", [bo.FP64, bo.MIXED])
+def test_combine_with_noise(precision):
+    """The epsilon term of Eq. 5: T = U C + epsilon with epsilon from the
+    oracle's own Philox4x64-10 at the global cell index; two chips so that
+    the second chip's cells are numbered after the first's.  The noise is
+    the same number on both sides, so the tolerances are those of U C."""
+    chips = [synth.random_small_chip(7, 21, 13, 3), synth.random_small_chip(8, 9, 11, 2)]
+    s, M, seed, amp = 8, 37, 2024, 0.01
+    rng = np.random.default_rng(6)
+    op = bo.assemble(chips)
+    Us = [rng.standard_normal((c.n, s)) for c in chips]
+    Cs = [synth.coefficients(rng, s, M) for c in chips]
+    T = torch.empty(M * op.n_total, dtype=torch.float64 if precision == bo.FP64 else torch.float32,
+                    device="cuda")
+    bo.combine(op, cuda(np.concatenate([u.ravel() for u in Us])), cuda(np.concatenate([c.ravel() for c in Cs])),
+               T, s, M, precision, noise_seed=seed, noise_amp=amp)
+    Th = T.cpu().numpy().astype(np.float64)
+    tol = 1e-14 if precision == bo.FP64 else 1e-6
+    for c, chip in enumerate(chips):
+        off = op.sizes[c]["off"]
+        ref = orc.combine(Us[c], Cs[c]) + orc.noise(seed, np.arange(off, off + chip.n), M, amp)
+        got = Th[off * M:(off + chip.n) * M].reshape(M, chip.n)
+        assert np.all(relcols(got, ref, axis=1) < tol)
+    with pytest.raises(bo.BlockoaError):
+        bo.combine(op, cuda(np.concatenate([u.ravel() for u in Us])), cuda(np.concatenate([c.ravel() for c in Cs])),
+                   T, s, M, precision, noise_seed=seed, noise_amp=-1.0)
+
+
 def test_apply_basis_rejects_bad_arguments():
     op = bo.assemble([synth.random_small_chip(8, 5, 4, 2)])
     with pytest.raises(bo.BlockoaError):

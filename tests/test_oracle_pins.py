@@ -333,6 +333,37 @@ def test_linearity_and_pair_consistency():
 
 
 # ---------------------------------------------------------------- inputs
+def test_philox_matches_library_generator():
+    """The oracle's Philox4x64-10 block equals numpy's Philox bit generator,
+    which draws block (counter + 1) first."""
+    rng = np.random.default_rng(4)
+    for t in range(40):
+        key = [int(x) for x in rng.integers(0, 2 ** 63, 2, dtype=np.uint64)]
+        ctr = [int(x) for x in rng.integers(1, 2 ** 63, 4, dtype=np.uint64)]
+        if t == 0:
+            key, ctr = [0, 0], [1, 0, 0, 0]
+        bg = np.random.Philox(counter=np.array([ctr[0] - 1] + ctr[1:], dtype=np.uint64),
+                              key=np.array(key, dtype=np.uint64))
+        assert [int(x) for x in bg.random_raw(4)] == orc.philox4x64_10(ctr, key)
+
+
+def test_noise_is_uniform_bounded_and_reproducible():
+    amp, M = 0.01, 64
+    cells = np.arange(1000, 1600)
+    e = orc.noise(77, cells, M, amp)
+    assert e.shape == (M, len(cells))
+    assert np.all(e >= -amp) and np.all(e < amp)
+    N = e.size
+    assert abs(e.mean()) < 4 * amp / np.sqrt(3 * N)             # mean 0, sd amp / sqrt(3)
+    assert abs(e.var() / (amp * amp / 3) - 1) < 0.05
+    assert np.array_equal(e, orc.noise(77, cells, M, amp))
+    assert np.array_equal(e[:, 5:9], orc.noise(77, cells[5:9], M, amp))   # per cell, not per call
+    assert not np.allclose(e, orc.noise(78, cells, M, amp))
+    # 4 fields per generator block: fields 4g..4g+3 are one block's four words
+    w = orc.philox4x64_10((int(cells[0]), 3, 0, 0), (77, 0))
+    assert np.allclose(e[12:16, 0], [amp * (2 * ((x >> 11) * 2.0 ** -53) - 1) for x in w], rtol=0, atol=0)
+
+
 def test_bf16_rounding_matches_torch():
     x = np.random.default_rng(5).standard_normal(4096)
     ours = synth.round_to_bf16(x)
