@@ -191,7 +191,7 @@ combine_tc_kernel(const TcTile *__restrict__ tiles, const ChipDev *__restrict__ 
       const int fb = f0 + cc * 32;
       if (valid) {
         if (nz.amp > 0.0) {   // epsilon of Eq. 5, 4 fields per generator block (fb is a multiple of 32)
-#pragma unroll 1
+#pragma unroll   // constant indices keep r[] in registers
           for (int g = 0; g < 8; ++g) {
             float eps[4];
             noise4f(nz, tile.cell0 + cell, (fb + 4 * g) / 4, eps);
