@@ -63,7 +63,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070 / 1000   # SMs x FP32 lanes x 2 flop x 
 FP64_PEAK_TFLOPS = 1.25                      # GB300 float64 (vector and tensor), nominal
 
 
-def parse_args():
+def parse_args(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=5)
@@ -73,12 +73,27 @@ def parse_args():
     p.add_argument("--e2e-steps", type=int, default=4)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    return p.parse_args()
+    return p.parse_args(argv)
 
 
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def aggregate(total_ms: float, verified: float, world: int, device=None):
+    """Whole-job figures of a replicas run: the timed duration is the
+    maximum over ranks and the verified pairs are summed over ranks (needs
+    an initialised process group when world > 1)."""
+    if world == 1:
+        return total_ms, float(verified)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms, float(verified)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
 
 
 def workload(rank: int):
@@ -280,14 +295,7 @@ def run_ours(args):
     clk = clocks.stop()
     launches = bo.launch_count() - launches0
     total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms, float(verified)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_ms_max, verified_all = float(tmax[0]), float(t[1])
-    else:
-        total_ms_max, verified_all = total_ms, float(verified)
+    total_ms_max, verified_all = aggregate(total_ms, verified, world, dev)
     value = verified_all / (total_ms_max / 1e3)
 
     # ---- plain float64 GPU form on the same chip
