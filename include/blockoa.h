@@ -88,7 +88,12 @@ typedef struct {
   int precond;          /* BLOCKOA_PRECOND_NONE (the paper's unpreconditioned block CG),
                            BLOCKOA_PRECOND_JACOBI (diagonal: directions from D^-1 R) or
                            BLOCKOA_PRECOND_ZLINE (z-line: directions from M^-1 R, M the
-                           tridiagonal coupling of each (x, y) cell column) */
+                           tridiagonal coupling of each (x, y) cell column) or
+                           BLOCKOA_PRECOND_ZLINE2 (two-step z-line: directions from
+                           M^-1 (2 R - A M^-1 R), the polynomial 2 - x of M^-1 A on
+                           M^-1 R; symmetric positive definite because the z-line
+                           splitting puts the spectrum of M^-1 A in (0, 2)).  Both
+                           z-line forms need nz <= the block tile's cells. */
   int small_solve;      /* BLOCKOA_SMALL_AUTO or BLOCKOA_SMALL_FP64_CHOLESKY (below) */
   int independent;      /* 0: block CG (the s columns share one Krylov space);
                            1: the s columns iterate as s independent (single
@@ -98,7 +103,8 @@ typedef struct {
                            and beta_jj = -(A p_j . z_j) / (p_j . A p_j) */
 } blockoa_solve_opts;
 
-enum { BLOCKOA_PRECOND_NONE = 0, BLOCKOA_PRECOND_JACOBI = 1, BLOCKOA_PRECOND_ZLINE = 2 };
+enum { BLOCKOA_PRECOND_NONE = 0, BLOCKOA_PRECOND_JACOBI = 1, BLOCKOA_PRECOND_ZLINE = 2,
+       BLOCKOA_PRECOND_ZLINE2 = 3 };
 
 /*
  * How the s x s systems Gamma alpha = rho and Gamma beta = -W are solved:

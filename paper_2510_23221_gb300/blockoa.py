@@ -29,6 +29,7 @@ MIXED = 1
 PRECOND_NONE = 0
 PRECOND_JACOBI = 1
 PRECOND_ZLINE = 2
+PRECOND_ZLINE2 = 3
 SMALL_AUTO = 0
 SMALL_FP64_CHOLESKY = 1
 

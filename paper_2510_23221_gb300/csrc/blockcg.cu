@@ -499,11 +499,12 @@ spmm_gram_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T 
 // (Gram blocks) and rn2 += ||R_new_j||^2 (threads with equal t % TPR own the
 // same columns).
 template <typename T, int S>
-__device__ __forceinline__ void update_flush(const T *aw, const T *rn, double *red, const SmallArgs &A, int c) {
+__device__ __forceinline__ void update_flush(const T *aw, const T *rn, double *red, const SmallArgs &A, int c,
+                                             bool with_w = true) {
   using G = BK<T, S>;
   constexpr int V = G::V;
   const int t = threadIdx.x;
-  gram_flush<T, S>(aw, red, A.wg + (long long)c * S * S, A.diag);
+  if (with_w) gram_flush<T, S>(aw, red, A.wg + (long long)c * S * S, A.diag);
   T *rt = reinterpret_cast<T *>(red);
 #pragma unroll
   for (int v = 0; v < V; ++v) rt[t * V + v] = rn[v];
@@ -1021,8 +1022,13 @@ struct ColGeom {
   // the same split in two: per tile, its first cell (z = 0, dx = 0) and the
   // x positions it has inside the chip; per slot, (z, dx)
   __device__ __forceinline__ void tile(const ChipDev &ch, int c, long long &cell0, int &xin) const {
-    const int xb = (c % tiles_x) * xt;
-    cell0 = ch.off + (long long)(c / tiles_x) * ch.nx + xb;
+    int y, xb;
+    tile(ch, c, cell0, xin, y, xb);
+  }
+  __device__ __forceinline__ void tile(const ChipDev &ch, int c, long long &cell0, int &xin, int &y, int &xb) const {
+    y = c / tiles_x;
+    xb = (c - y * tiles_x) * xt;
+    cell0 = ch.off + (long long)y * ch.nx + xb;
     xin = ch.nx - xb;
   }
   __device__ __forceinline__ static long long slot_cell(const ChipDev &ch, long long cell0, int xin, int z, int dx) {
@@ -1030,12 +1036,61 @@ struct ColGeom {
   }
 };
 
+// Tridiagonal factors of a column tile's slots into shared memory: e (the
+// conductance to z-1), f / den and 1 / den per slot.  fz, fdx: (z, dx) of
+// slot t, the calling thread's first slot.
+template <typename T, int TC>
+__device__ __forceinline__ void zline_factors(const ChipDev &ch, const ColGeom &cg, long long cell0, int xin,
+                                              int fz, int fdx, const T *__restrict__ g,
+                                              const T *__restrict__ zinv, T *sE, T *sF, T *sI) {
+  const int t = threadIdx.x;
+  for (int sl = t; sl < TC; sl += 256) {
+    const int z = sl == t ? fz : sl / cg.xt, dx = sl == t ? fdx : sl % cg.xt;
+    const long long a = ColGeom::slot_cell(ch, cell0, xin, z, dx);
+    T e = T(0), f = T(0), iv = T(0);
+    if (a >= 0) {
+      iv = zinv[a];
+      f = coef_ld(g, a).z * iv;
+      if (z > 0) e = coef_ld(g, a - (long long)ch.nx * ch.ny).z;
+    }
+    sE[sl] = e;
+    sF[sl] = f;
+    sI[sl] = iv;
+  }
+}
+
+// In place on a transposed [column][slot] tile: every cell column of every
+// block column is replaced by M^-1 of it (forward and back substitution of
+// the Thomas recurrences), one thread per (block column j, x position dx).
+template <typename T, int S, int LD>
+__device__ __forceinline__ void zline_solve_tile(T *sV, const T *sE, const T *sF, const T *sI, int nz, int xt) {
+  for (int pr = threadIdx.x; pr < S * xt; pr += 256) {
+    const int j = pr / xt, dx = pr % xt;
+    T *row = sV + j * LD;
+    T prev = T(0);
+    for (int z = 0; z < nz; ++z) {
+      const int sl = z * xt + dx;
+      T &val = row[swz<T>(j, sl)];
+      prev = (val + sE[sl] * prev) * sI[sl];
+      val = prev;
+    }
+    for (int z = nz - 2; z >= 0; --z) {
+      const int sl = z * xt + dx;
+      T &val = row[swz<T>(j, sl)];
+      prev = val + sF[sl] * prev;
+      val = prev;
+    }
+  }
+}
+
 // The update kernel with z-line preconditioning: as update_gram, over column
 // tiles (units are ranges of column tiles of one chip).  After X and R are
 // updated the tile holds whole cell columns of R_new: the tridiagonal
 // solves run in shared memory (one thread per (column of the block, x
 // position)), Z is stored for the P update, and W += Q^T Z.
-template <typename T, int S>
+// TWO (two-step z-line): Z1 = M^-1 R_new is stored and ||R_j||^2 flushed; the
+// second step, W and the beta tail belong to zline2_kernel.
+template <typename T, int S, bool TWO>
 __global__ void __launch_bounds__(256, 2)
 update_zline_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T *__restrict__ g,
                     const T *__restrict__ zinv, const T *__restrict__ P, const T *__restrict__ Q,
@@ -1068,8 +1123,8 @@ update_zline_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const
     const int ui = next_unit(us, A.state, &s_unit);
     const int chip = ui < us.n_units ? us.units[ui].chip : -1;
     if (run > 0 && chip != cur) {
-      update_flush<T, S>(aw, rn, red, A, cur);
-      if constexpr (sizeof(T) == 4) {
+      update_flush<T, S>(aw, rn, red, A, cur, !TWO);
+      if constexpr (sizeof(T) == 4 && !TWO) {
         if (A.tail && last_flush_of_chip(A.ticket + A.n_chips + cur, run, A.zunit_count[cur]))
           chip_beta<T, S>(A, cur);
       }
@@ -1126,20 +1181,7 @@ update_zline_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const
         put_tile<T, G::LD>(sP, pv, cl0, j0);
         put_tile<T, G::LD>(sQ, qv, cl0, j0);
       }
-      // the tridiagonal factors of the tile's slots
-      for (int sl = t; sl < G::TC; sl += 256) {
-        const int z = sl == t ? fz : sl / cg.xt, dx = sl == t ? fdx : sl % cg.xt;
-        const long long a = ColGeom::slot_cell(ch, cell0, xin, z, dx);
-        T e = T(0), f = T(0), iv = T(0);
-        if (a >= 0) {
-          iv = zinv[a];
-          f = coef_ld(g, a).z * iv;
-          if (z > 0) e = coef_ld(g, a - (long long)ch.nx * ch.ny).z;
-        }
-        sE[sl] = e;
-        sF[sl] = f;
-        sI[sl] = iv;
-      }
+      zline_factors<T, G::TC>(ch, cg, cell0, xin, fz, fdx, g, zinv, sE, sF, sI);
       T xv[4][V], rv[4][V];
       ld(xv, X);
       ld(rv, R);
@@ -1179,25 +1221,8 @@ update_zline_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const
         for (int v = 0; v < V; ++v) rn[v] += rv[k][v] * rv[k][v];  // zero outside the chip
       put_tile<T, G::LD>(sR, rv, cl0, j0);
       __syncthreads();
-      // Z = M^-1 R_new in place, one thread per (block column j, x position dx)
-      const int nz = ch.nz, xt = cg.xt;
-      for (int pr = t; pr < S * xt; pr += 256) {
-        const int j = pr / xt, dx = pr % xt;
-        T* row = sR + j * G::LD;
-        T prev = T(0);
-        for (int z = 0; z < nz; ++z) {
-          const int sl = z * xt + dx;
-          T &val = row[swz<T>(j, sl)];
-          prev = (val + sE[sl] * prev) * sI[sl];
-          val = prev;
-        }
-        for (int z = nz - 2; z >= 0; --z) {
-          const int sl = z * xt + dx;
-          T &val = row[swz<T>(j, sl)];
-          prev = val + sF[sl] * prev;
-          val = prev;
-        }
-      }
+      // Z = M^-1 R_new in place
+      zline_solve_tile<T, S, G::LD>(sR, sE, sF, sI, ch.nz, cg.xt);
       __syncthreads();
       {   // store Z (this thread's slots, read back from the transposed tile)
         T zv[4][V];
@@ -1210,7 +1235,146 @@ update_zline_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const
         }
         st(Zb, zv);
       }
-      gram_tile<T, S>(aw, sQ, sR, i0, k0, grp);
+      if constexpr (!TWO) gram_tile<T, S>(aw, sQ, sR, i0, k0, grp);
+      __syncthreads();
+    }
+  }
+  sched_finish(us);
+}
+
+// Second step of the two-step z-line preconditioner (PCM 3):
+//   Z = M^-1 (2 R - A Z1),  Z1 = M^-1 R from update_zline_kernel<TWO>,
+// i.e. the polynomial p(x) = 2 - x of M^-1 A applied to M^-1 R (symmetric
+// positive definite since the z-line splitting puts the spectrum of M^-1 A
+// in (0, 2)).  Over the same column tiles: the stencil reads Z1 of the
+// neighbouring cells from global memory (complete: the update kernel has
+// finished), the tridiagonal solves run in shared memory, Z goes to Zout,
+// and W += Q^T Z with the beta tail in the chip's last CTA.  INIT (the
+// restart of a refinement pass) writes Z to Zout (= P) and nothing else.
+template <typename T, int S, bool INIT>
+__global__ void __launch_bounds__(256, 2)
+zline2_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T *__restrict__ g,
+              const T *__restrict__ zinv, const T *__restrict__ Z1, const T *__restrict__ R,
+              const T *__restrict__ Q, T *__restrict__ Zout, const SmallArgs A) {
+  using G = BK<T, S>;
+  constexpr int V = G::V;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *sQ = reinterpret_cast<T *>(smem);
+  T *sR = sQ + S * G::LD;
+  T *sE = sR + S * G::LD;
+  T *sF = sE + G::TC;
+  T *sI = sF + G::TC;
+  double *red = reinterpret_cast<double *>(smem);   // reused between units
+  __shared__ int s_unit;
+  grid_release_next();
+  grid_wait_prior();
+  const int t = threadIdx.x;
+  const int j0 = (t % G::TPR) * V, cl0 = (t / G::TPR) * 4;
+  const int grp = t / G::NT, w = t % G::NT;
+  const int i0 = (w / G::NB) * 4, k0 = (w % G::NB) * 4;
+  T aw[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) aw[e] = T(0);
+  int cur = -1, run = 0;
+  for (;;) {
+    const int ui = next_unit(us, A.state, &s_unit);
+    const int chip = ui < us.n_units ? us.units[ui].chip : -1;
+    if constexpr (!INIT) {
+      if (run > 0 && chip != cur) {
+        gram_flush<T, S>(aw, red, A.wg + (long long)cur * S * S, A.diag);
+        if constexpr (sizeof(T) == 4) {
+          if (A.tail && last_flush_of_chip(A.ticket + A.n_chips + cur, run, A.zunit_count[cur]))
+            chip_beta<T, S>(A, cur);
+        }
+#pragma unroll
+        for (int e = 0; e < 16; ++e) aw[e] = T(0);
+        run = 0;
+      }
+    }
+    if (ui >= us.n_units) break;
+    const Unit u = us.units[ui];
+    cur = u.chip;
+    ++run;
+    const ChipDev ch = chips[u.chip];
+    const ColGeom cg(ch, G::TC);
+    const long long nxny = (long long)ch.nx * ch.ny;
+    int sz[4], sdx[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      sz[k] = (cl0 + k) / cg.xt;
+      sdx[k] = (cl0 + k) - sz[k] * cg.xt;
+    }
+    const int fz = t / cg.xt, fdx = t - fz * cg.xt;
+    for (long long ct = u.begin; ct < u.end; ++ct) {
+      long long cell0;
+      int xin, y, xb;
+      cg.tile(ch, (int)ct, cell0, xin, y, xb);
+      long long cell[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cell[k] = ColGeom::slot_cell(ch, cell0, xin, sz[k], sdx[k]);
+      {   // Y = 2 R - A Z1 on this thread's slots, into the transposed tile
+        T yv[4][V];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+#pragma unroll
+          for (int v = 0; v < V; ++v) yv[k][v] = T(0);
+          const long long a = cell[k];
+          if (a >= 0) {
+            const int x = xb + sdx[k], z = sz[k];
+            T zc[V], rr[V], az[V];
+            vload<T>(zc, Z1 + a * S + j0);
+            vload<T>(rr, R + a * S + j0);
+            const auto c4 = coef_ld(g, a);
+#pragma unroll
+            for (int v = 0; v < V; ++v) az[v] = c4.w * zc[v];
+            auto nb = [&](long long b, T gg) {
+              T o[V];
+              vload<T>(o, Z1 + b * S + j0);
+#pragma unroll
+              for (int v = 0; v < V; ++v) az[v] += gg * (zc[v] - o[v]);
+            };
+            if (x + 1 < ch.nx) nb(a + 1, c4.x);
+            if (x > 0) nb(a - 1, coef_ld(g, a - 1).x);
+            if (y + 1 < ch.ny) nb(a + ch.nx, c4.y);
+            if (y > 0) nb(a - ch.nx, coef_ld(g, a - ch.nx).y);
+            if (z + 1 < ch.nz) nb(a + nxny, c4.z);
+            if (z > 0) nb(a - nxny, coef_ld(g, a - nxny).z);
+#pragma unroll
+            for (int v = 0; v < V; ++v) yv[k][v] = T(2) * rr[v] - az[v];
+          }
+        }
+        put_tile<T, G::LD>(sR, yv, cl0, j0);
+      }
+      if constexpr (!INIT) {
+        T qv[4][V];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (cell[k] >= 0) vload<T>(qv[k], Q + cell[k] * S + j0);
+          else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) qv[k][v] = T(0);
+          }
+        }
+        put_tile<T, G::LD>(sQ, qv, cl0, j0);
+      }
+      zline_factors<T, G::TC>(ch, cg, cell0, xin, fz, fdx, g, zinv, sE, sF, sI);
+      __syncthreads();
+      zline_solve_tile<T, S, G::LD>(sR, sE, sF, sI, ch.nz, cg.xt);
+      __syncthreads();
+      {   // store Z (this thread's slots, read back from the transposed tile)
+        T zv[4][V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          T z4[4];
+          ld4<T, G::LD>(z4, sR, j0 + v, cl0);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) zv[k][v] = z4[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (cell[k] >= 0) vstore<T>(Zout + cell[k] * S + j0, zv[k]);
+      }
+      if constexpr (!INIT) gram_tile<T, S>(aw, sQ, sR, i0, k0, grp);
       __syncthreads();
     }
   }
@@ -1295,12 +1459,16 @@ __global__ void accumulate_kernel(const Unit *__restrict__ units, const int *__r
 // Launches per block-CG iteration and their timing classes: with the small
 // solves in the tails of the Gram kernels (CH = false) three, with the
 // Cholesky kernels (CH = true) five.
-constexpr int kMaxLoopKernels = 5;
-constexpr int loop_kernels(bool ch) { return ch ? 5 : 3; }
-constexpr int loop_class(bool ch, int i) {
-  return !ch ? (i == 0 ? KC_SPMM_GRAM : i == 1 ? KC_UPDATE_GRAM : KC_P_UPDATE)
-             : (i == 0 ? KC_SPMM_GRAM : i == 1 ? KC_ALPHA_SOLVE : i == 2 ? KC_UPDATE_GRAM
-                                       : i == 3 ? KC_BETA_SOLVE : KC_P_UPDATE);
+constexpr int kMaxLoopKernels = 6;
+// The two-step z-line form (pc 3) adds the second-step kernel after the update.
+constexpr int loop_kernels(bool ch, int pc) { return (ch ? 5 : 3) + (pc == 3 ? 1 : 0); }
+constexpr int loop_class(bool ch, int pc, int i) {
+  return pc == 3 ? (!ch ? (i == 0 ? KC_SPMM_GRAM : i == 1 ? KC_UPDATE_GRAM : i == 2 ? KC_ZLINE2 : KC_P_UPDATE)
+                        : (i == 0 ? KC_SPMM_GRAM : i == 1 ? KC_ALPHA_SOLVE : i == 2 ? KC_UPDATE_GRAM
+                                  : i == 3 ? KC_ZLINE2 : i == 4 ? KC_BETA_SOLVE : KC_P_UPDATE))
+                 : !ch ? (i == 0 ? KC_SPMM_GRAM : i == 1 ? KC_UPDATE_GRAM : KC_P_UPDATE)
+                       : (i == 0 ? KC_SPMM_GRAM : i == 1 ? KC_ALPHA_SOLVE : i == 2 ? KC_UPDATE_GRAM
+                                 : i == 3 ? KC_BETA_SOLVE : KC_P_UPDATE);
 }
 
 struct SolveWS {
@@ -1328,6 +1496,8 @@ struct SolveWS {
   int *zunit_count = nullptr, *zchip_unit_end = nullptr;
   bool zline_ok = false;        // every chip has nz <= TC
   void *Zb = nullptr;           // z-line Z = M^-1 R in the loop's precision
+  void *Zb2 = nullptr;          // two-step z-line: the second step's Z (Zb holds M^-1 R)
+  int grid_z2 = 0;              // persistent CTAs of the second-step kernel
   Unit *units_small = nullptr;  // elementwise units
   int n_units_small = 0;
   // host staging (pinned)
@@ -1406,6 +1576,11 @@ constexpr int kPStages = 3;
 template <int S>
 constexpr size_t pstaged_smem() { return (size_t)S * S * 4 + 2 * (size_t)kPStages * Stage32<S>::FLOATS * 4; }
 template <typename T, int S>
+constexpr size_t zline2_smem() {
+  return cmax(2 * tile_bytes<T, S>() + 3 * BK<T, S>::TC * sizeof(T), cmax(kRedBytes, tail_smem<T, S>()));
+}
+
+template <typename T, int S>
 constexpr size_t zupdate_smem() {
   return cmax(update_smem<T, S>(), 3 * tile_bytes<T, S>() + S * S * sizeof(T) + 3 * BK<T, S>::TC * sizeof(T));
 }
@@ -1417,22 +1592,28 @@ static void set_smem_limits() {
   done = true;
   cudaFuncSetAttribute(spmm_gram_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)spmm_smem<T, S>());
-  if constexpr (PCM == 2)
-    cudaFuncSetAttribute(update_zline_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if constexpr (PCM == 2 || PCM == 3) {
+    cudaFuncSetAttribute(update_zline_kernel<T, S, PCM == 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)zupdate_smem<T, S>());
+    cudaFuncSetAttribute(zline2_kernel<T, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)zline2_smem<T, S>());
+    cudaFuncSetAttribute(zline2_kernel<T, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)zline2_smem<T, S>());
+  }
   else
     cudaFuncSetAttribute(update_gram_kernel<T, S, PCM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)update_smem<T, S>());
-  cudaFuncSetAttribute(p_update_kernel<T, S, PCM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  constexpr int PP = PCM == 3 ? 2 : PCM;   // the two-step form's P update reads Z like the z-line form
+  cudaFuncSetAttribute(p_update_kernel<T, S, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pupdate_smem<T, S>());
   if constexpr (sizeof(T) == 4 && S == 32) {
-    cudaFuncSetAttribute(p_update_tc_kernel<PCM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ptc_smem());
+    cudaFuncSetAttribute(p_update_tc_kernel<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ptc_smem());
     // two CTAs of ~107 KB per SM need the largest shared-memory carveout
-    cudaFuncSetAttribute(p_update_tc_kernel<PCM>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaFuncSetAttribute(p_update_tc_kernel<PP>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          (int)cudaSharedmemCarveoutMaxShared);
   }
   else if constexpr (sizeof(T) == 4)
-    cudaFuncSetAttribute(p_update_staged_kernel<S, PCM, kPStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(p_update_staged_kernel<S, PP, kPStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)pstaged_smem<S>());
   cudaFuncSetAttribute(chol_alpha_kernel<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)chol_smem_bytes<S>());
@@ -1471,12 +1652,20 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
     launched();
   }
   mark();
-  if constexpr (PCM == 2) {
+  if constexpr (PCM == 2 || PCM == 3) {
     const UnitSched us_z{ws->zunits, ws->n_zunits, ws->zchip_unit_end, ws->work + 2};
     const T *zinv = sizeof(T) == 4 ? (const T *)op->zinv32 : (const T *)op->zinv64;
-    launch_chained(update_zline_kernel<T, S>, ws->grid_zupdate, 256, zupdate_smem<T, S>(), st, chain,
+    launch_chained(update_zline_kernel<T, S, PCM == 3>, ws->grid_zupdate, 256, zupdate_smem<T, S>(), st, chain,
                    us_z, op->d_chips, g, zinv, (const T *)ws->P, (const T *)ws->Q, (T *)ws->D, (T *)ws->R,
                    (T *)ws->Zb, sa);
+    if constexpr (PCM == 3) {   // second step: Zb2 = M^-1 (2 R - A Zb), W = Q^T Zb2, beta tail
+      launched();
+      mark();
+      const UnitSched us_z2{ws->zunits, ws->n_zunits, ws->zchip_unit_end, ws->work + 6};
+      launch_chained(zline2_kernel<T, S, false>, ws->grid_z2, 256, zline2_smem<T, S>(), st, chain,
+                     us_z2, op->d_chips, g, zinv, (const T *)ws->Zb, (const T *)ws->R, (const T *)ws->Q,
+                     (T *)ws->Zb2, sa);
+    }
   } else {
     launch_chained(update_gram_kernel<T, S, PCM>, ws->grid_update, 256, update_smem<T, S>(), st, chain,
                    us_u, (const T *)ws->P, (const T *)ws->Q, (T *)ws->D, (T *)ws->R, dinv, sa);
@@ -1488,17 +1677,19 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
     launched();
   }
   mark();
+  constexpr int PP = PCM == 3 ? 2 : PCM;   // the two-step form's P update reads its Z like the z-line form
+  const void *zfin = PCM == 3 ? ws->Zb2 : ws->Zb;
   if constexpr (sizeof(T) == 4 && S == 32)
-    launch_chained(p_update_tc_kernel<PCM>, ws->grid_pupd, 128, ptc_smem(), st, chain,
+    launch_chained(p_update_tc_kernel<PP>, ws->grid_pupd, 128, ptc_smem(), st, chain,
                    us_p, ws->state, (const float *)ws->beta, (const float *)ws->R, (float *)ws->P,
-                   (const float *)dinv, (const float *)ws->Zb);
+                   (const float *)dinv, (const float *)zfin);
   else if constexpr (sizeof(T) == 4)
-    launch_chained(p_update_staged_kernel<S, PCM, kPStages>, ws->grid_pupd, 256, pstaged_smem<S>(), st, chain,
+    launch_chained(p_update_staged_kernel<S, PP, kPStages>, ws->grid_pupd, 256, pstaged_smem<S>(), st, chain,
                    us_p, ws->state, (const float *)ws->beta, (const float *)ws->R, (float *)ws->P,
-                   (const float *)dinv, (const float *)ws->Zb);
+                   (const float *)dinv, (const float *)zfin);
   else
-    launch_chained(p_update_kernel<T, S, PCM>, ws->grid_pupd, 256, pupdate_smem<T, S>(), st, chain,
-                   us_p, ws->state, (const T *)ws->beta, (const T *)ws->R, (T *)ws->P, dinv, (const T *)ws->Zb);
+    launch_chained(p_update_kernel<T, S, PP>, ws->grid_pupd, 256, pupdate_smem<T, S>(), st, chain,
+                   us_p, ws->state, (const T *)ws->beta, (const T *)ws->R, (T *)ws->P, dinv, (const T *)zfin);
   launched();
   mark();
 }
@@ -1550,6 +1741,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     set_smem_limits<T, S, 0>();
     set_smem_limits<T, S, 1>();
     set_smem_limits<T, S, 2>();
+    set_smem_limits<T, S, 3>();
     int occ_s = 1, occ_u = 1, occ_p = 1, occ_z = 1;
     BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, spmm_gram_kernel<T, S>, 256,
                                                                spmm_smem<T, S>()));
@@ -1563,7 +1755,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     else
       BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, p_update_kernel<T, S, 1>, 256,
                                                                  pupdate_smem<T, S>()));
-    BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_z, update_zline_kernel<T, S>, 256,
+    BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_z, update_zline_kernel<T, S, false>, 256,
                                                                zupdate_smem<T, S>()));
     long long tiles = 0;
     for (const ChipDev &cd : op->chips) tiles += (cd.n + G::TC - 1) / G::TC;
@@ -1583,8 +1775,8 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       BLOCKOA_CUDA(cudaMemcpy(ws->chip_unit_end, uend.data(), sizeof(int) * (size_t)nc, cudaMemcpyHostToDevice));
       BLOCKOA_CUDA(ws_alloc(ws, &ws->ticket, sizeof(int) * 2 * (size_t)nc));
       BLOCKOA_CUDA(cudaMemset(ws->ticket, 0, sizeof(int) * 2 * (size_t)nc));
-      BLOCKOA_CUDA(ws_alloc(ws, &ws->work, sizeof(int) * 6));
-      BLOCKOA_CUDA(cudaMemset(ws->work, 0, sizeof(int) * 6));
+      BLOCKOA_CUDA(ws_alloc(ws, &ws->work, sizeof(int) * 8));   // [spmm, update, P update, z-line second step] x 2
+      BLOCKOA_CUDA(cudaMemset(ws->work, 0, sizeof(int) * 8));
     }
     BLOCKOA_CUDA(ws_alloc(ws, &ws->units, sizeof(Unit) * units.size()));
     BLOCKOA_CUDA(cudaMemcpy(ws->units, units.data(), sizeof(Unit) * units.size(), cudaMemcpyHostToDevice));
@@ -1624,6 +1816,11 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       BLOCKOA_CUDA(cudaMemcpy(ws->zchip_unit_end, zend.data(), sizeof(int) * (size_t)nc, cudaMemcpyHostToDevice));
       ws->grid_zupdate = (int)std::max<long long>(1, std::min<long long>(ws->n_zunits, (long long)std::max(occ_z, 1) * nsm));
       BLOCKOA_CUDA(ws_alloc(ws, &ws->Zb, sizeof(T) * (size_t)n * S));
+      BLOCKOA_CUDA(ws_alloc(ws, &ws->Zb2, sizeof(T) * (size_t)n * S));
+      int occ_z2 = 1;
+      BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_z2, zline2_kernel<T, S, false>, 256,
+                                                                 zline2_smem<T, S>()));
+      ws->grid_z2 = (int)std::max<long long>(1, std::min<long long>(ws->n_zunits, (long long)std::max(occ_z2, 1) * nsm));
     }
     ws->grid_spmm = (int)std::min<long long>(ws->n_units, (long long)std::max(occ_s, 1) * nsm);
     ws->grid_update = (int)std::min<long long>(ws->n_units, (long long)std::max(occ_u, 1) * nsm);
@@ -1650,8 +1847,9 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
   const int max_refine = o->max_refine > 0 ? o->max_refine : 12;
   const double tol = o->deflate_tol > 0 ? o->deflate_tol : (prec == BLOCKOA_MIXED ? 1e-6 : 1e-14);
   const int check_every = o->check_every > 0 ? o->check_every : 8;
-  const int pc = o->precond == BLOCKOA_PRECOND_JACOBI ? 1 : (o->precond == BLOCKOA_PRECOND_ZLINE ? 2 : 0);
-  if (pc == 2 && !ws->zline_ok) {
+  const int pc = o->precond == BLOCKOA_PRECOND_JACOBI ? 1 : o->precond == BLOCKOA_PRECOND_ZLINE ? 2
+               : o->precond == BLOCKOA_PRECOND_ZLINE2 ? 3 : 0;
+  if (pc >= 2 && !ws->zline_ok) {
     set_last_error(cudaErrorInvalidValue, "block_solve: PRECOND_ZLINE needs nz <= the tile cells of every chip");
     return BLOCKOA_ERR_INVALID;
   }
@@ -1683,10 +1881,12 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       if (ch) {
         if (pc == 1) launch_iteration<T, S, 1, true>(op, ws, sa, ws->cap, ev, chain);
         else if (pc == 2) launch_iteration<T, S, 2, true>(op, ws, sa, ws->cap, ev, chain);
+        else if (pc == 3) launch_iteration<T, S, 3, true>(op, ws, sa, ws->cap, ev, chain);
         else launch_iteration<T, S, 0, true>(op, ws, sa, ws->cap, ev, chain);
       } else if constexpr (sizeof(T) == 4) {
         if (pc == 1) launch_iteration<T, S, 1, false>(op, ws, sa, ws->cap, ev, chain);
         else if (pc == 2) launch_iteration<T, S, 2, false>(op, ws, sa, ws->cap, ev, chain);
+        else if (pc == 3) launch_iteration<T, S, 3, false>(op, ws, sa, ws->cap, ev, chain);
         else launch_iteration<T, S, 0, false>(op, ws, sa, ws->cap, ev, chain);
       }
     }
@@ -1785,7 +1985,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       BLOCKOA_CUDA(cudaMemsetAsync(ws->wg, 0, sm, st));
       BLOCKOA_CUDA(cudaMemsetAsync(ws->rn2, 0, sv, st));
       BLOCKOA_CUDA(cudaMemsetAsync(ws->ticket, 0, sizeof(int) * 2 * (size_t)nc, st));
-      BLOCKOA_CUDA(cudaMemsetAsync(ws->work, 0, sizeof(int) * 6, st));
+      BLOCKOA_CUDA(cudaMemsetAsync(ws->work, 0, sizeof(int) * 8, st));
     }
     g_launches += 2;
     {
@@ -1798,7 +1998,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
         inner_init_kernel<T, S, 0><<<ws->n_units_small, 256, 0, st>>>(
             ws->units_small, ws->outer_active, ws->R64, ws->inv_sigma, (T *)ws->R, (T *)ws->P,
             (T *)ws->D, dinv);
-      if (pc == 2) {   // P = Z = M^-1 R
+      if (pc >= 2) {   // P = Z = M^-1 R
         long long maxcols = 1;
         for (const ChipDev &cd : op->chips) maxcols = std::max<long long>(maxcols, (long long)cd.nx * cd.ny);
         const int nq = S / (16 / (int)sizeof(T));
@@ -1808,20 +2008,27 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
         zline_init_kernel<T, S><<<zg, 256, 0, st>>>(op->d_chips, nc, ws->outer_active, gco, zinv,
                                                    (const T *)ws->R, (T *)ws->P, (T *)ws->Zb);
         g_launches += 1;
+        if (pc == 3) {   // two-step: P = Z = M^-1 (2 R - A M^-1 R)
+          const UnitSched us_z2{ws->zunits, ws->n_zunits, ws->zchip_unit_end, ws->work + 6};
+          zline2_kernel<T, S, true><<<ws->grid_z2, 256, zline2_smem<T, S>(), st>>>(
+              us_z2, op->d_chips, gco, zinv, (const T *)ws->Zb, (const T *)ws->R, (const T *)ws->Q,
+              (T *)ws->P, sa);
+          g_launches += 1;
+        }
       }
     }
     BLOCKOA_CUDA(cudaGetLastError());
     // Inner block-CG iterations, polled every `check_every` iterations.
     for (;;) {
-      g_launches += (long long)loop_kernels(ch) * check_every;
-      for (int i = 0; i < loop_kernels(ch); ++i) add_launches(op, loop_class(ch, i), check_every);
+      g_launches += (long long)loop_kernels(ch, pc) * check_every;
+      for (int i = 0; i < loop_kernels(ch, pc); ++i) add_launches(op, loop_class(ch, pc, i), check_every);
       BLOCKOA_CUDA(cudaGraphLaunch(ws->graph, st));
       BLOCKOA_CUDA(read_small(ws->h_state, ws->state, sizeof(ChipSolveState) * nc, st));
       BLOCKOA_CUDA(cudaStreamSynchronize(st));
-      for (int i = 0; i < loop_kernels(ch); ++i) {   // live timing of this chunk's first iteration
+      for (int i = 0; i < loop_kernels(ch, pc); ++i) {   // live timing of this chunk's first iteration
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, ws->tev[i], ws->tev[i + 1]) == cudaSuccess)
-          add_time(op, loop_class(ch, i), ms);
+          add_time(op, loop_class(ch, pc, i), ms);
         else
           cudaGetLastError();
       }
@@ -1874,7 +2081,7 @@ extern "C" int blockoa_block_solve(blockoa_operator *op, const double *B, double
   if (!(opts->rtol > 0.0) || opts->maxiter < 0) return BLOCKOA_ERR_INVALID;
   if (opts->precision != BLOCKOA_FP64 && opts->precision != BLOCKOA_MIXED) return BLOCKOA_ERR_INVALID;
   if (opts->precond != BLOCKOA_PRECOND_NONE && opts->precond != BLOCKOA_PRECOND_JACOBI &&
-      opts->precond != BLOCKOA_PRECOND_ZLINE)
+      opts->precond != BLOCKOA_PRECOND_ZLINE && opts->precond != BLOCKOA_PRECOND_ZLINE2)
     return BLOCKOA_ERR_INVALID;
   if (opts->small_solve != BLOCKOA_SMALL_AUTO && opts->small_solve != BLOCKOA_SMALL_FP64_CHOLESKY)
     return BLOCKOA_ERR_INVALID;

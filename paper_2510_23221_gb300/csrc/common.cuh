@@ -48,7 +48,7 @@ static_assert(sizeof(ChipSolveState) % 8 == 0, "chip states are read back in 8-b
 // Kernel classes with live event timing.
 enum KernelClass {
   KC_SPMM_GRAM = 0, KC_ALPHA_SOLVE, KC_UPDATE_GRAM, KC_BETA_SOLVE, KC_P_UPDATE,
-  KC_RESIDUAL64, KC_COMBINE_TC, KC_SPLIT, KC_APPLY, KC_COMBINE_FP64, KC_COUNT
+  KC_RESIDUAL64, KC_COMBINE_TC, KC_SPLIT, KC_APPLY, KC_COMBINE_FP64, KC_ZLINE2, KC_COUNT
 };
 
 struct KernelTimes {

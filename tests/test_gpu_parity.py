@@ -371,28 +371,44 @@ def test_mixed_with_fp64_cholesky_small_solves(precond):
         assert np.all(relcols(Xs[c], ref) < 1e-8)
 
 
+@pytest.mark.parametrize("pc", [bo.PRECOND_ZLINE, bo.PRECOND_ZLINE2])
 @pytest.mark.parametrize("precision", [bo.FP64, bo.MIXED])
-def test_zline_preconditioned_solve(precision):
-    """z-line preconditioning changes the iteration, not the solution: the
-    reference stack at 1e-12 against the oracle, and uneven chips (several
-    layer counts, multi-cell layers, ragged column tiles) against dense solves."""
+def test_zline_preconditioned_solve(precision, pc):
+    """z-line preconditioning (one or two steps) changes the iteration, not
+    the solution: the reference stack at 1e-12 against the oracle, and uneven
+    chips (several layer counts, multi-cell layers, ragged column tiles)
+    against dense solves."""
     w = synth.small_fp64_workload()
     chip = w.chips[0]
     A = orc.assemble(chip)
     B = orc.rhs(chip, w.density[0])
     U_or, _ = orc.block_cg(A, B, rtol=1e-12)
-    (X,), (st,) = _solve([chip], [B], 8, precision, 1e-12, precond=bo.PRECOND_ZLINE)
+    (X,), (st,) = _solve([chip], [B], 8, precision, 1e-12, precond=pc)
     assert st.status == bo.OK and st.relres_max <= 1e-12
     assert np.all(relcols(X, U_or) < 1e-9)
     chips = small_chips() + [synth.random_small_chip(105, 37, 21, 5)]
     rng = np.random.default_rng(80)
     for s in (4, 12):
         Bs = [rng.uniform(0, 1e-2, (c.n, s)) for c in chips]
-        Xs, stats = _solve(chips, Bs, s, precision, 1e-11, precond=bo.PRECOND_ZLINE)
+        Xs, stats = _solve(chips, Bs, s, precision, 1e-11, precond=pc)
         for c, ch in enumerate(chips):
             assert stats[c].status == bo.OK, (s, c, stats[c])
             ref = np.linalg.solve(orc.assemble(ch).toarray(), Bs[c])
             assert np.all(relcols(Xs[c], ref) < 1e-8)
+
+
+@pytest.mark.parametrize("precision", [bo.FP64, bo.MIXED])
+def test_two_step_zline_needs_fewer_iterations(precision):
+    """The second z-line step (directions from M^-1 (2R - A M^-1 R)) cuts
+    the block iterations on a layered chip against one step."""
+    chip = synth.single_chip_workload(48, 40, 8, s=8, M=4).chips[0]
+    rng = np.random.default_rng(12)
+    B = orc.rhs(chip, np.stack([synth.rect_power_map(rng, chip.nx, chip.ny) for _ in range(8)]))
+    (X1,), (s1,) = _solve([chip], [B], 8, precision, 1e-9, precond=bo.PRECOND_ZLINE)
+    (X2,), (s2,) = _solve([chip], [B], 8, precision, 1e-9, precond=bo.PRECOND_ZLINE2)
+    assert s1.status == bo.OK and s2.status == bo.OK
+    assert s2.iters < 0.8 * s1.iters, (s1.iters, s2.iters)
+    assert np.all(relcols(X2, X1) < 1e-7)
 
 
 def test_reassemble_in_place_matches_fresh_assembly():
