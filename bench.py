@@ -3,7 +3,7 @@
 
 One step = the whole hot path on one synthetic chip (128 x 128 x 8 cells,
 8 layers, s = 32 power maps, M = 5000 fields): assemble, right-hand sides,
-z-line-preconditioned mixed-precision block CG to a float64 relative
+two-step z-line-preconditioned mixed-precision block CG to a float64 relative
 residual of 1e-6, bfloat16x3
 tensor-core combination T = U C, operator action q = A T.  Inputs (power
 maps and coefficients) are resident on the device when timing starts; L2 is
@@ -53,7 +53,7 @@ METRIC = "verified sample pairs/s at <=1e-6 rel err, chosen vs plain FP64, one G
 UNIT = "pairs/s"
 RTOL = 1e-6
 PAIR_TOL = 1e-6
-# inner tolerance of each float32 block-CG pass of the chosen (z-line) form
+# inner tolerance of each float32 block-CG pass of the chosen (two-step z-line) form
 # (the library default; at 1e-3 it takes three refinement passes, not two)
 INNER_RTOL = 1e-4
 # convergence polls of the chosen form: every 16 block-CG iterations (one
@@ -235,7 +235,7 @@ def run_ours(args):
     e_pair = torch.empty(M, dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    CHOSEN_PRECOND = bo.PRECOND_ZLINE
+    CHOSEN_PRECOND = bo.PRECOND_ZLINE2   # two-step z-line
     ops = {}   # one long-lived operator per precision, re-discretised every step
 
     def operator(precision):
@@ -246,7 +246,7 @@ def run_ours(args):
     def step(precision, Tb, qb, precond=CHOSEN_PRECOND):
         op = operator(precision)
         bo.build_rhs(op, inputs.density, B, s)
-        chosen = precision == bo.MIXED and precond == bo.PRECOND_ZLINE
+        chosen = precision == bo.MIXED and precond == CHOSEN_PRECOND
         st = bo.block_solve(op, B, U, s, rtol=RTOL, precision=precision, precond=precond,
                             inner_rtol=INNER_RTOL if chosen else 0.0,
                             check_every=CHECK_EVERY if chosen else 0, raise_on_error=False)
@@ -384,7 +384,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
             "config": {"workload": w.name, "cells": n, "s": s, "M": M, "precision": "mixed",
-                       "precond": "zline", "inner_rtol": INNER_RTOL, "check_every": CHECK_EVERY, "plain_fp64_precond": "none",
+                       "precond": "zline2", "inner_rtol": INNER_RTOL, "check_every": CHECK_EVERY, "plain_fp64_precond": "none",
                        "rtol": RTOL, "pair_tol": PAIR_TOL,
                        "l2": "flushed between steps (512 MB write, outside timed events)",
                        "parallelism": f"replicas x{world}"},

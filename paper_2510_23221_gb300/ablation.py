@@ -7,7 +7,7 @@ the per-sample direct method against the basis route.
 Part 1 (iterations): the chip's s power maps are solved with the s columns
 coupled (block CG, one Krylov space) and with the columns independent
 (s scalar CG solves: every off-diagonal Gram entry dropped), at each
-tolerance, in the chosen form (mixed precision, z-line preconditioning)
+tolerance, in the chosen form (mixed precision, two-step z-line preconditioning)
 and in the plain float64 unpreconditioned form.  Reported: block
 iterations, the largest single-column iteration count, and solve times
 (CUDA events, device-resident inputs, warm operator).
@@ -60,7 +60,7 @@ def main():
     B = torch.empty(n * s, dtype=torch.float64, device=dev)
     U = torch.empty_like(B)
     bo.build_rhs(op, inputs.density, B, s)
-    forms = {"chosen": dict(precision=bo.MIXED, precond=bo.PRECOND_ZLINE),
+    forms = {"chosen": dict(precision=bo.MIXED, precond=bo.PRECOND_ZLINE2),
              "plain_fp64": dict(precision=bo.FP64, precond=bo.PRECOND_NONE)}
 
     def timed(fn):

@@ -33,7 +33,7 @@ def main():
     p.add_argument("--s", type=int, default=32)
     p.add_argument("--M", type=int, default=1000)
     p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
-    p.add_argument("--precond", choices=["none", "jacobi", "zline"], default="jacobi")
+    p.add_argument("--precond", choices=["none", "jacobi", "zline", "zline2"], default="jacobi")
     p.add_argument("--small", choices=["auto", "fp64-cholesky"], default="auto")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--reps", type=int, default=10)
@@ -55,7 +55,7 @@ def main():
         dens = pl.upload(w).density
         B = torch.empty(n * s, dtype=torch.float64, device="cuda")
         bo.build_rhs(op, dens, B, s)
-        pc = {"none": bo.PRECOND_NONE, "jacobi": bo.PRECOND_JACOBI, "zline": bo.PRECOND_ZLINE}[a.precond]
+        pc = {"none": bo.PRECOND_NONE, "jacobi": bo.PRECOND_JACOBI, "zline": bo.PRECOND_ZLINE, "zline2": bo.PRECOND_ZLINE2}[a.precond]
 
     def call():
         if a.call == "solve":

@@ -35,7 +35,7 @@ def main():
     p = argparse.ArgumentParser()
     p.add_argument("--workload", choices=["chip128", "batch256", "chip512"], default="batch256")
     p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
-    p.add_argument("--precond", choices=["none", "jacobi", "zline"], default="jacobi")
+    p.add_argument("--precond", choices=["none", "jacobi", "zline", "zline2"], default="jacobi")
     p.add_argument("--chunk", type=int, default=1000, help="fields per combine/apply pass")
     p.add_argument("--M", type=int, default=0, help="override the workload's field count")
     p.add_argument("--maxiter", type=int, default=20000)
@@ -49,7 +49,7 @@ def main():
     else:
         w = synth.large_chip_workload(M=a.M or 10000)
     prec = bo.MIXED if a.precision == "mixed" else bo.FP64
-    pc = {"none": bo.PRECOND_NONE, "jacobi": bo.PRECOND_JACOBI, "zline": bo.PRECOND_ZLINE}[a.precond]
+    pc = {"none": bo.PRECOND_NONE, "jacobi": bo.PRECOND_JACOBI, "zline": bo.PRECOND_ZLINE, "zline2": bo.PRECOND_ZLINE2}[a.precond]
     fdt = torch.float32 if prec == bo.MIXED else torch.float64
     dev = torch.device("cuda")
     s, M = w.s, w.M
