@@ -116,6 +116,38 @@ __device__ __forceinline__ double4 coef_ld(const double *g, long long a) {
   return make_double4(lo.x, lo.y, hi.x, hi.y);
 }
 
+// (A v)_a on the V columns at j0 of a [cell][S] block vector vb, given the
+// cell's own values vc and its grid position.  All six neighbour rows and
+// the three lower-face coefficients are requested before any is used; a
+// neighbour outside the chip is read at the cell itself with a zero
+// coefficient, so its term is exactly zero and the sum is the 7-point
+// stencil in the order +x, -x, +y, -y, +z, -z.
+template <typename T, int S>
+__device__ __forceinline__ void stencil_row(const T *__restrict__ g, const T *__restrict__ vb, long long a,
+                                            const T (&vc)[16 / sizeof(T)], int x, int y, int z, int nx, int ny,
+                                            int nz, long long nxny, int j0, T (&out)[16 / sizeof(T)]) {
+  constexpr int V = 16 / sizeof(T);
+  const bool xp = x + 1 < nx, xm = x > 0, yp = y + 1 < ny, ym = y > 0, zp = z + 1 < nz, zm = z > 0;
+  const long long b[6] = {xp ? a + 1 : a, xm ? a - 1 : a, yp ? a + nx : a,
+                          ym ? a - nx : a, zp ? a + nxny : a, zm ? a - nxny : a};
+  const auto c4 = coef_ld(g, a);
+  const auto cxm = coef_ld(g, b[1]);
+  const auto cym = coef_ld(g, b[3]);
+  const auto czm = coef_ld(g, b[5]);
+  T o[6][V];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) vload<T>(o[i], vb + b[i] * S + j0);
+  const T gg[6] = {xp ? c4.x : T(0), xm ? cxm.x : T(0), yp ? c4.y : T(0),
+                   ym ? cym.y : T(0), zp ? c4.z : T(0), zm ? czm.z : T(0)};
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    T acc = c4.w * vc[v];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) acc += gg[i] * (vc[v] - o[i][v]);
+    out[v] = acc;
+  }
+}
+
 // Load this thread's 4 cells x V columns of a [cell][S] block (zeros past `end`).
 template <typename T, int S>
 __device__ __forceinline__ void load_block(T (&x)[4][16 / sizeof(T)], const T *G, long long c0,
@@ -458,23 +490,7 @@ spmm_gram_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T 
         }
 #pragma unroll
         for (int v = 0; v < V; ++v) qv[k][v] = T(0);
-        if (a < u.end) {
-          const auto c4 = coef_ld(g, a);
-#pragma unroll
-          for (int v = 0; v < V; ++v) qv[k][v] = c4.w * pc[k][v];
-          auto nb = [&](long long b, T gg) {
-            T o[V];
-            vload<T>(o, P + b * S + j0);
-#pragma unroll
-            for (int v = 0; v < V; ++v) qv[k][v] += gg * (pc[k][v] - o[v]);
-          };
-          if (x + 1 < nx) nb(a + 1, c4.x);
-          if (x > 0) nb(a - 1, coef_ld(g, a - 1).x);
-          if (y + 1 < ny) nb(a + nx, c4.y);
-          if (y > 0) nb(a - nx, coef_ld(g, a - nx).y);
-          if (z + 1 < nz) nb(a + nxny, c4.z);
-          if (z > 0) nb(a - nxny, coef_ld(g, a - nxny).z);
-        }
+        if (a < u.end) stencil_row<T, S>(g, P, a, pc[k], x, y, z, nx, ny, nz, nxny, j0, qv[k]);
       }
       store_block<T, S>(Q, qv, base + cl0, u.end, j0);
       put_tile<T, G::LD>(sP, pc, cl0, j0);
@@ -1324,21 +1340,7 @@ zline2_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T *__
             T zc[V], rr[V], az[V];
             vload<T>(zc, Z1 + a * S + j0);
             vload<T>(rr, R + a * S + j0);
-            const auto c4 = coef_ld(g, a);
-#pragma unroll
-            for (int v = 0; v < V; ++v) az[v] = c4.w * zc[v];
-            auto nb = [&](long long b, T gg) {
-              T o[V];
-              vload<T>(o, Z1 + b * S + j0);
-#pragma unroll
-              for (int v = 0; v < V; ++v) az[v] += gg * (zc[v] - o[v]);
-            };
-            if (x + 1 < ch.nx) nb(a + 1, c4.x);
-            if (x > 0) nb(a - 1, coef_ld(g, a - 1).x);
-            if (y + 1 < ch.ny) nb(a + ch.nx, c4.y);
-            if (y > 0) nb(a - ch.nx, coef_ld(g, a - ch.nx).y);
-            if (z + 1 < ch.nz) nb(a + nxny, c4.z);
-            if (z > 0) nb(a - nxny, coef_ld(g, a - nxny).z);
+            stencil_row<T, S>(g, Z1, a, zc, x, y, z, ch.nx, ch.ny, ch.nz, nxny, j0, az);
 #pragma unroll
             for (int v = 0; v < V; ++v) yv[k][v] = T(2) * rr[v] - az[v];
           }
