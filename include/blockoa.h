@@ -199,6 +199,37 @@ int blockoa_block_solve(blockoa_operator *op, const double *B, double *X, int s,
                         blockoa_stream stream);
 
 /*
+ * Launch tuning of the batched block-CG loop (the persistent launches of
+ * blockoa_block_solve): work units are tiles_per_unit block tiles of one
+ * chip for the loop kernels, and ztiles_per_unit column tiles for the
+ * z-line kernels; 0 lets the library derive the size from the tile count.
+ */
+typedef struct {
+  int tiles_per_unit;
+  int ztiles_per_unit;
+  double ms_per_iter;   /* blockoa_autotune: measured time of one block iteration */
+} blockoa_tuning;
+
+/*
+ * Autotune the unit sizes of this operator for s columns in the given
+ * precision and preconditioner form: for each candidate (1, 2, 4, 8, 16, 32
+ * tiles; then, for the z-line forms, 1-32 column tiles) it times block
+ * iterations of a solve on synthetic right-hand sides (the difference of a
+ * 24- and an 8-iteration run, so set-up and refinement cancel), keeps the
+ * fastest in the operator for later solves and reports it.  Synchronous;
+ * uses the library's device pool for its right-hand sides.
+ * Errors: ERR_INVALID, ERR_OOM, ERR_CUDA.
+ */
+int blockoa_autotune(blockoa_operator *op, int s, int precision, int precond, blockoa_tuning *out,
+                     blockoa_stream stream);
+
+/* Set (0 = derive from the tile count) or read the operator's unit sizes;
+ * ms_per_iter is ignored / returned as 0.  Errors: ERR_INVALID (sizes
+ * outside 0..64). */
+int blockoa_set_tuning(blockoa_operator *op, const blockoa_tuning *t);
+int blockoa_get_tuning(const blockoa_operator *op, blockoa_tuning *t);
+
+/*
  * New temperature fields T = U C (Eq. 5, Sec. III-B, with the noise term
  * off and no normalisation: unknowns are excess temperatures, so every
  * combination keeps the homogeneous Robin/adiabatic conditions).

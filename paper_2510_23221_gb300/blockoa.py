@@ -38,7 +38,7 @@ EXPORTED = (
     "blockoa_block_solve", "blockoa_combine", "blockoa_combine_ex", "blockoa_apply_basis", "blockoa_apply_operator", "blockoa_pair_check",
     "blockoa_export_conductances", "blockoa_destroy", "blockoa_status_string",
     "blockoa_last_error", "blockoa_kernel_times", "blockoa_reset_kernel_times",
-    "blockoa_launch_count",
+    "blockoa_launch_count", "blockoa_autotune", "blockoa_set_tuning", "blockoa_get_tuning",
 )
 
 
@@ -48,6 +48,10 @@ class ChipDesc(ct.Structure):
                 ("layer_k", ct.POINTER(ct.c_double)), ("k_cell", ct.POINTER(ct.c_double)),
                 ("dx", ct.c_double), ("dy", ct.c_double), ("h_top", ct.c_double),
                 ("h_bottom", ct.c_double), ("h_side", ct.c_double), ("t_ambient", ct.c_double)]
+
+
+class Tuning(ct.Structure):
+    _fields_ = [("tiles_per_unit", ct.c_int), ("ztiles_per_unit", ct.c_int), ("ms_per_iter", ct.c_double)]
 
 
 class CombineOpts(ct.Structure):
@@ -98,6 +102,9 @@ def _lib():
         lib.blockoa_apply_operator.argtypes = [vp, vp, vp, i, i, vp]
         lib.blockoa_apply_basis.argtypes = [vp, vp, vp, i, vp]
         lib.blockoa_combine_ex.argtypes = [vp, vp, vp, vp, i, i, i, ct.POINTER(CombineOpts), vp]
+        lib.blockoa_autotune.argtypes = [vp, i, i, i, ct.POINTER(Tuning), vp]
+        lib.blockoa_set_tuning.argtypes = [vp, ct.POINTER(Tuning)]
+        lib.blockoa_get_tuning.argtypes = [vp, ct.POINTER(Tuning)]
         lib.blockoa_pair_check.argtypes = [vp, vp, vp, i, i, vp, vp]
         lib.blockoa_export_conductances.argtypes = [vp, i, vp, vp, vp, vp]
         lib.blockoa_destroy.argtypes = [vp]
@@ -214,6 +221,24 @@ def reassemble(op: Operator, chips: Sequence, stream=None) -> Operator:
     _check(_lib().blockoa_reassemble(op.handle, arr, len(chips), _stream(stream)), "reassemble")
     op.chips = list(chips)
     return op
+
+
+def autotune(op: Operator, s: int, precision: int = MIXED, precond: int = PRECOND_NONE, stream=None) -> dict:
+    """blockoa_autotune: time candidate unit sizes, keep the fastest in `op`."""
+    t = Tuning()
+    _check(_lib().blockoa_autotune(op.handle, s, precision, precond, ct.byref(t), _stream(stream)), "autotune")
+    return {"tiles_per_unit": t.tiles_per_unit, "ztiles_per_unit": t.ztiles_per_unit, "ms_per_iter": t.ms_per_iter}
+
+
+def set_tuning(op: Operator, tiles_per_unit: int = 0, ztiles_per_unit: int = 0):
+    t = Tuning(tiles_per_unit=tiles_per_unit, ztiles_per_unit=ztiles_per_unit, ms_per_iter=0.0)
+    _check(_lib().blockoa_set_tuning(op.handle, ct.byref(t)), "set_tuning")
+
+
+def get_tuning(op: Operator) -> dict:
+    t = Tuning()
+    _check(_lib().blockoa_get_tuning(op.handle, ct.byref(t)), "get_tuning")
+    return {"tiles_per_unit": t.tiles_per_unit, "ztiles_per_unit": t.ztiles_per_unit}
 
 
 def operator_size(op: Operator, chip: int):

@@ -1475,6 +1475,7 @@ constexpr int loop_class(bool ch, int pc, int i) {
 
 struct SolveWS {
   int S = 0, prec = -1;
+  int tune_tpu = 0, tune_ztpu = 0;   // the operator's unit sizes this workspace was built with
   long long n = 0;
   int n_chips = 0;
   // float64 block vectors
@@ -1703,7 +1704,8 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
   const int nc = op->n_chips;
   const long long n = op->n_total;
   SolveWS *ws = (SolveWS *)op->solve_ws;
-  if (!ws || ws->S != S || ws->prec != prec || ws->n != n) {
+  if (!ws || ws->S != S || ws->prec != prec || ws->n != n || ws->tune_tpu != op->tune_tpu ||
+      ws->tune_ztpu != op->tune_ztpu) {
     free_solve_ws(ws);
     op->solve_ws = nullptr;
     ws = new SolveWS();
@@ -1763,6 +1765,9 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     for (const ChipDev &cd : op->chips) tiles += (cd.n + G::TC - 1) / G::TC;
     long long tpu = tiles / (16LL * std::max(occ_s, 1) * nsm);
     tpu = std::min<long long>(std::max<long long>(tpu, 1), 8);
+    if (op->tune_tpu > 0) tpu = op->tune_tpu;   // chosen by blockoa_autotune or the caller
+    ws->tune_tpu = op->tune_tpu;
+    ws->tune_ztpu = op->tune_ztpu;
     std::vector<Unit> units = make_units(op, tpu * G::TC);
     ws->n_units = (int)units.size();
     {
@@ -1790,6 +1795,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
         if (cd.nz <= G::TC) ztiles += (long long)cd.ny * ((cd.nx + G::TC / cd.nz - 1) / (G::TC / cd.nz));
       long long ztpu = ztiles / (16LL * std::max(occ_z, 1) * nsm);
       ztpu = std::min<long long>(std::max<long long>(ztpu, 1), 8);
+      if (op->tune_ztpu > 0) ztpu = op->tune_ztpu;
       for (int c = 0; c < nc; ++c) {
         const ChipDev &cd = op->chips[c];
         if (cd.nz > G::TC) continue;   // no z-line units: such chips cannot use PRECOND_ZLINE
@@ -2109,3 +2115,122 @@ extern "C" int blockoa_block_solve(blockoa_operator *op, const double *B, double
     default: return solve_impl<float, 64>(op, B, X, s, opts, stats, st);
   }
 }
+
+
+// ---------------------------------------------------------------- autotuning
+namespace blockoa {
+// Deterministic positive right-hand sides for timing runs.
+__global__ void tune_rhs_kernel(double *B, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x)
+    B[i] = 1.0 + 0.25 * (double)((unsigned long long)(i * 2654435761LL) % 1024ull) / 1024.0;
+}
+}  // namespace blockoa
+
+extern "C" int blockoa_set_tuning(blockoa_operator *op, const blockoa_tuning *t) {
+  if (!op || !t || t->tiles_per_unit < 0 || t->tiles_per_unit > 64 || t->ztiles_per_unit < 0 ||
+      t->ztiles_per_unit > 64)
+    return BLOCKOA_ERR_INVALID;
+  op->tune_tpu = t->tiles_per_unit;
+  op->tune_ztpu = t->ztiles_per_unit;
+  return BLOCKOA_OK;
+}
+
+extern "C" int blockoa_get_tuning(const blockoa_operator *op, blockoa_tuning *t) {
+  if (!op || !t) return BLOCKOA_ERR_INVALID;
+  t->tiles_per_unit = op->tune_tpu;
+  t->ztiles_per_unit = op->tune_ztpu;
+  t->ms_per_iter = 0.0;
+  return BLOCKOA_OK;
+}
+
+extern "C" int blockoa_autotune(blockoa_operator *op, int s, int precision, int precond, blockoa_tuning *out,
+                                blockoa_stream stream) {
+  if (!op || !out || s < 1 || s > 64) return BLOCKOA_ERR_INVALID;
+  if (precision != BLOCKOA_FP64 && precision != BLOCKOA_MIXED) return BLOCKOA_ERR_INVALID;
+  if (precond < BLOCKOA_PRECOND_NONE || precond > BLOCKOA_PRECOND_ZLINE2) return BLOCKOA_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long total = op->n_total * s;
+  void *B = nullptr, *X = nullptr;
+  int rc = pool_alloc(op, &B, sizeof(double) * total, st);
+  if (!rc) rc = pool_alloc(op, &X, sizeof(double) * total, st);
+  auto done = [&](int code) {
+    pool_free(B, st);
+    pool_free(X, st);
+    cudaStreamSynchronize(st);
+    return code;
+  };
+  if (rc) return done(rc);
+  tune_rhs_kernel<<<1024, 256, 0, st>>>((double *)B, total);
+  g_launches += 1;
+  std::vector<blockoa_solve_stats> stats(op->n_chips);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return done(BLOCKOA_ERR_CUDA);
+  }
+  // time of a solve that runs exactly `iters` block iterations (unreachable tolerance)
+  auto run = [&](int iters, float &ms) -> int {
+    blockoa_solve_opts o;
+    memset(&o, 0, sizeof(o));
+    o.rtol = 1e-300;
+    o.maxiter = iters;
+    o.precision = precision;
+    o.precond = precond;
+    o.check_every = 8;
+    int r = blockoa_block_solve(op, (const double *)B, (double *)X, s, &o, stats.data(), stream);   // warm: workspace, graph
+    if (r != BLOCKOA_OK && r != BLOCKOA_ERR_NOT_CONVERGED) return r;
+    cudaEventRecord(e0, st);
+    r = blockoa_block_solve(op, (const double *)B, (double *)X, s, &o, stats.data(), stream);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    return (r == BLOCKOA_OK || r == BLOCKOA_ERR_NOT_CONVERGED) ? BLOCKOA_OK : r;
+  };
+  // per-iteration cost with the set-up and the refinement step cancelled
+  auto per_iter = [&](double &ms_it) -> int {
+    float a = 0.f, b = 0.f;
+    int r = run(8, a);
+    if (!r) r = run(24, b);
+    ms_it = (b - a) / 16.0;
+    return r;
+  };
+  const int saved_tpu = op->tune_tpu, saved_ztpu = op->tune_ztpu;
+  int best_tpu = 0, best_ztpu = 0;
+  double best = 1e30;
+  static const int cands[] = {1, 2, 4, 8, 16, 32};
+  for (int c : cands) {
+    op->tune_tpu = c;
+    op->tune_ztpu = saved_ztpu;
+    double ms = 0.0;
+    if ((rc = per_iter(ms))) break;
+    if (ms < best) { best = ms; best_tpu = c; }
+  }
+  best_ztpu = saved_ztpu;   // the z-line unit size the first search ran with
+  if (!rc && precond >= BLOCKOA_PRECOND_ZLINE) {
+    for (int c : cands) {
+      op->tune_tpu = best_tpu;
+      op->tune_ztpu = c;
+      double ms = 0.0;
+      if ((rc = per_iter(ms))) break;
+      if (ms < best) {
+        best = ms;
+        best_ztpu = c;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) {
+    op->tune_tpu = saved_tpu;
+    op->tune_ztpu = saved_ztpu;
+    return done(rc);
+  }
+  op->tune_tpu = best_tpu;
+  op->tune_ztpu = best_ztpu;
+  out->tiles_per_unit = best_tpu;
+  out->ztiles_per_unit = best_ztpu;
+  out->ms_per_iter = best;
+  return done(BLOCKOA_OK);
+}
+

@@ -118,6 +118,8 @@ struct blockoa_operator {
   void *apply_vec_blocks = nullptr;      // same for the vectorised form
   int n_apply_vec_blocks = 0;
   int *h_flag = nullptr;                 // pinned status word for small device -> host reads
+  int tune_tpu = 0;                      // block-CG unit size in tiles (0: from the tile count)
+  int tune_ztpu = 0;                     // z-line unit size in column tiles (0: from the tile count)
 };
 
 namespace blockoa {

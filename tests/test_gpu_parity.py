@@ -411,6 +411,36 @@ def test_two_step_zline_needs_fewer_iterations(precision):
     assert np.all(relcols(X2, X1) < 1e-7)
 
 
+def test_autotune_and_hand_set_unit_sizes_keep_the_results():
+    """Unit sizes only regroup the work: after blockoa_autotune, and with
+    odd sizes set by hand, solves of an uneven batch still match dense
+    solves; the tuning is kept in the operator."""
+    chips = [synth.random_small_chip(110 + c, 24 + 7 * c, 18 + 3 * c, 3 + c) for c in range(3)]
+    s = 8
+    op = bo.assemble(chips)
+    t = bo.autotune(op, s, bo.MIXED, bo.PRECOND_ZLINE2)
+    assert t["tiles_per_unit"] in (1, 2, 4, 8, 16, 32) and t["ztiles_per_unit"] in (0, 1, 2, 4, 8, 16, 32)
+    assert t["ms_per_iter"] > 0
+    assert bo.get_tuning(op) == {"tiles_per_unit": t["tiles_per_unit"], "ztiles_per_unit": t["ztiles_per_unit"]}
+    rng = np.random.default_rng(21)
+    Bs = [rng.uniform(0, 1e-2, (c.n, s)) for c in chips]
+    dense = [np.linalg.solve(orc.assemble(c).toarray(), b) for c, b in zip(chips, Bs)]
+    for tune in (None, (3, 5)):
+        if tune:
+            bo.set_tuning(op, *tune)
+        B = cuda(np.concatenate([b.ravel() for b in Bs]))
+        X = torch.empty_like(B)
+        stats = bo.block_solve(op, B, X, s, rtol=1e-11, precision=bo.MIXED, precond=bo.PRECOND_ZLINE2)
+        Xh = X.cpu().numpy()
+        for c in range(len(chips)):
+            assert stats[c].status == bo.OK
+            sz = op.sizes[c]
+            got = Xh[sz["off"] * s:(sz["off"] + sz["n"]) * s].reshape(-1, s)
+            assert np.all(relcols(got, dense[c]) < 1e-8), (tune, c)
+    with pytest.raises(bo.BlockoaError):
+        bo.set_tuning(op, -1, 0)
+
+
 def test_reassemble_in_place_matches_fresh_assembly():
     """Re-discretising an operator in place equals a fresh assembly bit for
     bit; a solve on it, reusing the workspace and graph built by a solve on
