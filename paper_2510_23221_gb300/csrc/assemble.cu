@@ -179,7 +179,7 @@ __global__ void assemble_kernel(const Unit *__restrict__ units, const ChipDev *_
       if (y == 0) cb = __dadd_rn(cb, robin_g(__dmul_rn(ph.dx, dz), ph.dy, ka, ph.h_side));
       if (y == ch.ny - 1) cb = __dadd_rn(cb, robin_g(__dmul_rn(ph.dx, dz), ph.dy, ka, ph.h_side));
     }
-    reinterpret_cast<double4 *>(g64)[a] = make_double4(cx, cy, cz, cb);
+    reinterpret_cast<Coef64 *>(g64)[a] = Coef64{cx, cy, cz, cb};
     reinterpret_cast<float4 *>(g32)[a] =
         make_float4((float)cx, (float)cy, (float)cz, (float)cb);
   }
@@ -193,11 +193,11 @@ __global__ void inv_diag_kernel(const Unit *__restrict__ units, const ChipDev *_
   const Unit u = units[blockIdx.x];
   const ChipDev ch = chips[u.chip];
   const long long nxny = (long long)ch.nx * ch.ny;
-  const double4 *g = reinterpret_cast<const double4 *>(g64);
+  const Coef64 *g = reinterpret_cast<const Coef64 *>(g64);
   for (long long a = u.begin + threadIdx.x; a < u.end; a += blockDim.x) {
     const long long loc = a - ch.off;
     const int x = (int)(loc % ch.nx), y = (int)((loc / ch.nx) % ch.ny), z = (int)(loc / nxny);
-    const double4 c = g[a];
+    const Coef64 c = g[a];
     double d = c.x + c.y + c.z + c.w;
     if (x > 0) d += g[a - 1].x;
     if (y > 0) d += g[a - ch.nx].y;
@@ -221,14 +221,14 @@ __global__ void zfactor_kernel(const ChipDev *__restrict__ chips, int n_chips, c
   if (c >= n_chips) return;
   const ChipDev ch = chips[c];
   const long long nxny = (long long)ch.nx * ch.ny;
-  const double4 *g = reinterpret_cast<const double4 *>(g64);
+  const Coef64 *g = reinterpret_cast<const Coef64 *>(g64);
   for (long long col = blockIdx.x * (long long)blockDim.x + threadIdx.x; col < nxny;
        col += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(col % ch.nx), y = (int)(col / ch.nx);
     double den_prev = 1.0;
     for (int z = 0; z < ch.nz; ++z) {
       const long long a = ch.off + z * nxny + col;
-      const double4 cf = g[a];
+      const Coef64 cf = g[a];
       double d = cf.x + cf.y + cf.z + cf.w;
       if (x > 0) d += g[a - 1].x;
       if (y > 0) d += g[a - ch.nx].y;

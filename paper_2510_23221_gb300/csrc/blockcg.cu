@@ -110,10 +110,10 @@ __device__ __forceinline__ void st4(T *tile, const T *s, int row, int cell) {
 __device__ __forceinline__ float4 coef_ld(const float *g, long long a) {
   return __ldg(reinterpret_cast<const float4 *>(g) + a);
 }
-__device__ __forceinline__ double4 coef_ld(const double *g, long long a) {
+__device__ __forceinline__ Coef64 coef_ld(const double *g, long long a) {
   const double2 lo = __ldg(reinterpret_cast<const double2 *>(g) + 2 * a);
   const double2 hi = __ldg(reinterpret_cast<const double2 *>(g) + 2 * a + 1);
-  return make_double4(lo.x, lo.y, hi.x, hi.y);
+  return Coef64{lo.x, lo.y, hi.x, hi.y};
 }
 
 // (A v)_a on the V columns at j0 of a [cell][S] block vector vb, given the
@@ -211,22 +211,22 @@ __device__ __forceinline__ void gram_range(T *acc, const T *A, const T *B, int i
     }
 #pragma unroll
     for (int e = 0; e < 16; ++e) acc[e] += pr[e].x + pr[e].y;
-    return;
-  }
+  } else {
 #pragma unroll 2
-  for (int c = cbeg; c < cbeg + nc; c += 4) {
-    T a[4][4], b[4][4];
+    for (int c = cbeg; c < cbeg + nc; c += 4) {
+      T a[4][4], b[4][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      ld4<T, G::LD>(a[q], A, i0 + q, c);
-      ld4<T, G::LD>(b[q], B, j0 + q, c);
+      for (int q = 0; q < 4; ++q) {
+        ld4<T, G::LD>(a[q], A, i0 + q, c);
+        ld4<T, G::LD>(b[q], B, j0 + q, c);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc[q * 4 + r] += a[q][k] * b[r][k];
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[q * 4 + r] += a[q][k] * b[r][k];
   }
 }
 
@@ -715,8 +715,8 @@ p_update_staged_kernel(const UnitSched us, const ChipSolveState *__restrict__ st
                        const float *__restrict__ Zb) {
   using SG = Stage32<S>;
   constexpr int TC = SG::TC, TPR = S / 4;
-  extern __shared__ __align__(128) unsigned char smem[];
-  float *sB = reinterpret_cast<float *>(smem);
+  extern __shared__ __align__(128) unsigned char smem_staged[];
+  float *sB = reinterpret_cast<float *>(smem_staged);
   float *sP = sB + S * S;                 // NST staged tiles of P
   float *sZ = sP + NST * SG::FLOATS;      // NST staged tiles of Z (R under PCM 0 and 1)
   grid_release_next();
@@ -831,8 +831,8 @@ p_update_tc_kernel(const UnitSched us, ChipSolveState *__restrict__ state, const
   using SG = Stage32<S>;
   static_assert(SG::TC == TCP_M, "one staged tile per MMA tile");
   constexpr uint32_t TCOLS = 32;
-  extern __shared__ __align__(1024) unsigned char smem[];
-  float *stP = reinterpret_cast<float *>(smem);      // [2][TC * S] staged P rows
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  float *stP = reinterpret_cast<float *>(smem_tc);      // [2][TC * S] staged P rows
   float *stZ = stP + 2 * SG::FLOATS;                  // [2][TC * S] staged Z rows, then results
   unsigned char *aHi = reinterpret_cast<unsigned char *>(stZ + 2 * SG::FLOATS);
   unsigned char *aLo = aHi + I::BYTES_A;
@@ -1929,10 +1929,16 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
   std::vector<double> relres(nc, 0.0), prev_relres(nc, INFINITY);
   std::vector<double> sig((size_t)nc * S), isig((size_t)nc * S), tgt((size_t)nc * S);
   for (int step = 0;; ++step) {
-    // True float64 residual R64 = B - A X64 and its column norms.
-    BLOCKOA_CUDA(cudaMemsetAsync(ws->rn64, 0, sizeof(double) * nc * S, st));
-    int rc = launch_residual64(op, ws->B64, ws->X64, ws->R64, S, ws->rn64, st);
-    if (rc) return rc;
+    // True float64 residual R64 = B - A X64 and its column norms (from a
+    // zero start the first one is B itself).
+    if (step == 0 && !o->x0) {
+      BLOCKOA_CUDA(cudaMemcpyAsync(ws->R64, ws->B64, sizeof(double) * (size_t)n * S, cudaMemcpyDeviceToDevice, st));
+      BLOCKOA_CUDA(cudaMemcpyAsync(ws->rn64, ws->bn2, sizeof(double) * nc * S, cudaMemcpyDeviceToDevice, st));
+    } else {
+      BLOCKOA_CUDA(cudaMemsetAsync(ws->rn64, 0, sizeof(double) * nc * S, st));
+      int rc = launch_residual64(op, ws->B64, ws->X64, ws->R64, S, ws->rn64, st);
+      if (rc) return rc;
+    }
     BLOCKOA_CUDA(read_small(ws->h_small, ws->rn64, sizeof(double) * nc * S, st));
     BLOCKOA_CUDA(cudaStreamSynchronize(st));
     int n_active = 0;

@@ -60,6 +60,11 @@ struct KernelTimes {
   std::vector<cudaEvent_t> pend_ev;   // 2 per pending launch
 };
 
+// One cell's four float64 conductances (cx, cy, cz, cb) as stored in g64.
+struct alignas(32) Coef64 {
+  double x, y, z, w;
+};
+
 // Kernel launches issued by the library in this process (graph launches
 // count every kernel node).
 extern std::atomic<long long> g_launches;

@@ -30,10 +30,10 @@ static __device__ __align__(256) double g_pair_scratch[2 * kStaticPairMax];
 
 constexpr int PS_X = 32, PS_Y = 8;
 
-__device__ __forceinline__ double4 ps_coef(const double *g, long long a) {
+__device__ __forceinline__ Coef64 ps_coef(const double *g, long long a) {
   const double2 lo = __ldg(reinterpret_cast<const double2 *>(g) + 2 * a);
   const double2 hi = __ldg(reinterpret_cast<const double2 *>(g) + 2 * a + 1);
-  return make_double4(lo.x, lo.y, hi.x, hi.y);
+  return Coef64{lo.x, lo.y, hi.x, hi.y};
 }
 
 __global__ void ps_clear_kernel(double *acc, int n) {
@@ -62,7 +62,7 @@ ps_check_kernel(const ChipDev *__restrict__ chips, const double *__restrict__ g,
     for (int z = 0; z < ch.nz; ++z) {
       const long long loc = z * nxny + (long long)y * ch.nx + x;
       const long long a = ch.off + loc;
-      const double4 c4 = ps_coef(g, a);
+      const Coef64 c4 = ps_coef(g, a);
       const double c = (double)tf[loc];
       double r = c4.w * c;
       if (x + 1 < ch.nx) r += c4.x * (c - (double)tf[loc + 1]);

@@ -14,15 +14,15 @@ namespace blockoa {
 
 template <typename T> struct Coef4;
 template <> struct Coef4<float> { using type = float4; };
-template <> struct Coef4<double> { using type = double4; };
+template <> struct Coef4<double> { using type = Coef64; };
 
 __device__ __forceinline__ float4 load_coef_(const float *g, long long a) {
   return __ldg(reinterpret_cast<const float4 *>(g) + a);
 }
-__device__ __forceinline__ double4 load_coef_(const double *g, long long a) {
+__device__ __forceinline__ Coef64 load_coef_(const double *g, long long a) {
   const double2 lo = __ldg(reinterpret_cast<const double2 *>(g) + 2 * a);
   const double2 hi = __ldg(reinterpret_cast<const double2 *>(g) + 2 * a + 1);
-  return make_double4(lo.x, lo.y, hi.x, hi.y);
+  return Coef64{lo.x, lo.y, hi.x, hi.y};
 }
 template <typename T>
 __device__ __forceinline__ typename Coef4<T>::type load_coef(const T *g, long long a) {
@@ -456,7 +456,7 @@ pair_check_kernel(const FieldTile *__restrict__ tiles, const ChipDev *__restrict
     for (int z = 0; z < ch.nz; ++z) {
       const long long loc = z * nxny + (long long)y * ch.nx + x;
       const long long a = ch.off + loc;
-      const double4 c4 = load_coef<double>(g, a);
+      const Coef64 c4 = load_coef<double>(g, a);
       const double c = (double)tf[loc];
       double r = c4.w * c;
       if (x + 1 < ch.nx) r += c4.x * (c - (double)tf[loc + 1]);
@@ -551,7 +551,7 @@ residual64_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ ch
     const int x = (int)(loc % ch.nx);
     const int y = (int)((loc / ch.nx) % ch.ny);
     const int z = (int)(loc / nxny);
-    const double4 c4 = load_coef<double>(g, a);
+    const Coef64 c4 = load_coef<double>(g, a);
     const double2 c = *reinterpret_cast<const double2 *>(X + a * S + j);
     double r0 = c4.w * c.x, r1 = c4.w * c.y;
     auto nb = [&](long long b, double gg) {
@@ -600,7 +600,7 @@ apply_block64_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__
     const int x = (int)(loc % ch.nx);
     const int y = (int)((loc / ch.nx) % ch.ny);
     const int z = (int)(loc / nxny);
-    const double4 c4 = load_coef<double>(g, a);
+    const Coef64 c4 = load_coef<double>(g, a);
     const double c = U[a * s + j];
     double r = c4.w * c;
     if (x + 1 < ch.nx) r += c4.x * (c - U[(a + 1) * s + j]);
