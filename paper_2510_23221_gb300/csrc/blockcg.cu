@@ -1833,7 +1833,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     ws->grid_spmm = (int)std::min<long long>(ws->n_units, (long long)std::max(occ_s, 1) * nsm);
     ws->grid_update = (int)std::min<long long>(ws->n_units, (long long)std::max(occ_u, 1) * nsm);
     ws->grid_pupd = (int)std::min<long long>(ws->n_units, (long long)std::max(occ_p, 1) * nsm);
-    std::vector<Unit> us = make_units(op, 2048);
+    std::vector<Unit> us = make_units(op, 256);   // element-wise set-up kernels: ~512 CTAs on a 131K-cell chip
     ws->n_units_small = (int)us.size();
     BLOCKOA_CUDA(ws_alloc(ws, &ws->units_small, sizeof(Unit) * us.size()));
     BLOCKOA_CUDA(cudaMemcpy(ws->units_small, us.data(), sizeof(Unit) * us.size(), cudaMemcpyHostToDevice));

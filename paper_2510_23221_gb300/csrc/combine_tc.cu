@@ -1,9 +1,9 @@
 // T = U C on the tensor cores (Eq. 5, Sec. III-B), bfloat16x3 with float32
 // accumulation in tensor memory (tcgen05, sm_103a).
 //
-// The float64 basis U is split into three bfloat16 planes
-//   hi = bf16(u),  mid = bf16(u - hi),  lo = bf16(u - hi - mid)
-// (relative residual below 2^-24 |u|), C is bfloat16-exact, and
+// The float64 basis U is rounded to float32 and split into three bfloat16
+// planes  hi = bf16(u),  mid = bf16(u - hi),  lo = bf16(u - hi - mid)
+// (relative residual below 2^-23 |u|), C is bfloat16-exact, and
 //   T = [lo | mid | hi] [C; C; C]
 // is one GEMM with K = 3 S' (S' = s rounded up to 16), the small planes first
 // so that they enter the float32 accumulator before the large ones.
@@ -67,11 +67,15 @@ __global__ void split_u_kernel(const TcTile *__restrict__ tiles, int n_tiles,
       const int plane = k / Sp, j = k % Sp;   // 0 = lo, 1 = mid, 2 = hi
       double u = 0.0;
       if (r < tile.ncells && j < s) u = U[(tile.cell0 + r) * s + j];
-      const __nv_bfloat16 hi = __double2bfloat16(u);
-      const double r1 = u - (double)__bfloat162float(hi);
-      const __nv_bfloat16 mid = __double2bfloat16(r1);
-      const double r2 = r1 - (double)__bfloat162float(mid);
-      const __nv_bfloat16 lo = __double2bfloat16(r2);
+      // one rounding to float32 (2^-24 relative), then an exact split in
+      // float32: each residual is representable, so hi + mid + lo carries
+      // the float value to its last bits without float64 arithmetic
+      const float uf = (float)u;
+      const __nv_bfloat16 hi = __float2bfloat16(uf);
+      const float r1 = uf - __bfloat162float(hi);
+      const __nv_bfloat16 mid = __float2bfloat16(r1);
+      const float r2 = r1 - __bfloat162float(mid);
+      const __nv_bfloat16 lo = __float2bfloat16(r2);
       v[q] = plane == 2 ? hi : (plane == 1 ? mid : lo);
     }
     char *dst = reinterpret_cast<char *>(img) + tile.img * (long long)TC_M * K * 2 + tc_img_off(r, k0, K);
