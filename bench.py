@@ -53,9 +53,11 @@ METRIC = "verified sample pairs/s at <=1e-6 rel err, chosen vs plain FP64, one G
 UNIT = "pairs/s"
 RTOL = 1e-6
 PAIR_TOL = 1e-6
-# inner tolerance of each float32 block-CG pass of the chosen (two-step z-line) form
-# (the library default; at 1e-3 it takes three refinement passes, not two)
-INNER_RTOL = 1e-4
+# inner tolerance of the first float32 block-CG pass of the chosen (two-step
+# z-line) form; the second pass is asked only for what the 1e-6 target still
+# needs.  Measured on this chip: 1e-3 -> 89 iterations, 16.0 ms per solve;
+# 1e-4 (the library default) -> 102 iterations, 17.1 ms; both two passes.
+INNER_RTOL = 1e-3
 # convergence polls of the chosen form: every 16 block-CG iterations (one
 # CUDA graph of 16 iterations per poll; fewer host round trips)
 CHECK_EVERY = 16
