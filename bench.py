@@ -154,15 +154,28 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- our arm
-def algorithmic(kernel: str, n: int, s: int, M: int):
-    """(bound, algorithmic units per launch, unit) of a kernel on an n-cell chip."""
+def algorithmic(kernel: str, n: int, s: int, M: int, precond: str = "zline2"):
+    """(bound, algorithmic units per launch, unit) of a kernel on an n-cell chip.
+
+    Flop counts per cell (S = the padded block width, an FMA counted as 2):
+    the 7-point stencil is 13 S, a tridiagonal z-line solve 5 S (forward
+    elimination 3, back substitution 2), an S x S Gram or block update 2 S^2."""
     S = 8 if s <= 8 else 16 if s <= 16 else 32 if s <= 32 else 64
     Sp = (s + 15) // 16 * 16
+    if precond == "zline2":
+        # X and R updates, Z1 = M^-1 R and ||R_j||^2; W = Q^T Z is in zline_second
+        update = n * (4 * S * S + 5 * S + 2 * S)
+    elif precond == "zline":
+        update = n * (6 * S * S + 5 * S + 2 * S)
+    else:
+        # X and R updates, W = Q^T (D^-1 R), column norms
+        update = n * (6 * S * S + 3 * S)
     table = {
-        # float32 SIMT: stencil 13 flop per cell-column + two S x S Grams
+        # float32 SIMT: stencil + two S x S Grams (P^T Q, Q^T Q)
         "spmm_gram": ("alu", n * (13 * S + 4 * S * S), "flop"),
-        # X and R updates (2 S^2 each) + W = Q^T R (2 S^2) + column norms
-        "update_gram": ("alu", n * (6 * S * S + 2 * S), "flop"),
+        "update_gram": ("alu", update, "flop"),
+        # Y = 2 R - A Z1 (stencil + 2 S), z-line solve, W = Q^T Z
+        "zline_second": ("alu", n * (13 * S + 2 * S + 5 * S + 2 * S * S), "flop"),
         "p_update": ("alu", n * 2 * S * S, "flop"),
         # operator action: read T, write q (float32)
         "apply_fields": ("hbm", 8 * n * M, "byte"),
@@ -173,7 +186,7 @@ def algorithmic(kernel: str, n: int, s: int, M: int):
     return table.get(kernel)
 
 
-def roofline(kt: dict, n: int, s: int, M: int, peaks: dict):
+def roofline(kt: dict, n: int, s: int, M: int, peaks: dict, precond: str = "zline2"):
     """Roofline entry of the dominant kernel from live event timings.
 
     Loop kernels are timed on one iteration per convergence poll; a kernel's
@@ -183,7 +196,7 @@ def roofline(kt: dict, n: int, s: int, M: int, peaks: dict):
     ranked = sorted(((est[name], ms, name, cnt) for name, (ms, cnt, nall) in kt.items() if cnt > 0),
                     reverse=True)
     for _, ms, name, cnt in ranked:
-        a = algorithmic(name, n, s, M)
+        a = algorithmic(name, n, s, M, precond)
         if a is None:
             continue
         bound, units, kind = a
@@ -372,7 +385,7 @@ def run_ours(args):
     pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pp):
         peaks = json.load(open(pp))
-    roof = roofline(kt_sum, n, s, M, peaks)
+    roof = roofline(kt_sum, n, s, M, peaks, precond="zline2")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -1,0 +1,61 @@
+"""Host logic of the benchmark's roofline entry: which kernel is dominant,
+how its achieved rate follows from the algorithmic work and the live event
+timings, and which peak it is divided by.  No GPU: kernel timings are given
+as the (timed ms, timed launches, all launches) triples the library reports."""
+import pytest
+
+import bench
+
+N, S, M = 128 * 128 * 8, 32, 5000
+PEAKS = {"hbm_gbs": 6788.3}
+
+
+def test_dominant_kernel_is_ranked_by_estimated_share_not_timed_ms():
+    # spmm_gram: 10 ms over 100 timed launches of 1600 -> 160 ms estimated;
+    # apply_fields: 50 ms over its only 50 launches -> 50 ms.
+    kt = {"spmm_gram": (10.0, 100, 1600), "apply_fields": (50.0, 50, 50)}
+    r = bench.roofline(kt, N, S, M, PEAKS)
+    assert r["kernel"] == "spmm_gram"
+    assert r["share_of_kernel_time"] == pytest.approx(160.0 / 210.0, abs=1e-3)
+    assert r["launches"] == 1600 and r["timed_launches"] == 100
+
+
+def test_alu_kernel_rate_and_fraction():
+    kt = {"spmm_gram": (6.0, 100, 100)}   # 60 us per launch
+    r = bench.roofline(kt, N, S, M, PEAKS)
+    flop = N * (13 * 32 + 4 * 32 * 32)
+    achieved = flop / 60e-6 / 1e12
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(achieved, abs=1e-3)
+    assert r["peak"] == pytest.approx(152 * 128 * 2 * 2.070 / 1000, abs=0.1)
+    assert r["frac"] == pytest.approx(achieved / bench.FP32_PEAK_TFLOPS, abs=1e-4)
+    assert r["avg_launch_us"] == pytest.approx(60.0)
+
+
+def test_hbm_kernel_uses_the_measured_copy_peak():
+    kt = {"apply_fields": (1.0, 1, 1)}   # 1 ms: read T and write q, float32
+    r = bench.roofline(kt, N, S, M, PEAKS)
+    gbs = 8 * N * M / 1e-3 / 1e9
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(gbs, abs=1e-2)
+    assert r["peak"] == pytest.approx(6788.3)
+    assert r["frac"] == pytest.approx(gbs / 6788.3, abs=1e-4)
+    assert "measured" in r["peak_source"]
+
+
+def test_kernels_without_a_cost_model_or_timed_launch_are_skipped():
+    # the small solves have no per-cell cost model; a kernel never timed has no rate
+    kt = {"alpha_solve": (900.0, 10, 10), "p_update": (0.0, 0, 500), "update_gram": (3.0, 10, 10)}
+    assert bench.roofline(kt, N, S, M, PEAKS)["kernel"] == "update_gram"
+    assert bench.roofline({"alpha_solve": (1.0, 1, 1)}, N, S, M, PEAKS) is None
+
+
+def test_cost_model_follows_the_preconditioner():
+    # the two-step z-line form moves W = Q^T Z from the update kernel to the second step
+    z2 = bench.algorithmic("update_gram", N, S, M, "zline2")[1]
+    z1 = bench.algorithmic("update_gram", N, S, M, "zline")[1]
+    assert z1 - z2 == N * 2 * S * S
+    second = bench.algorithmic("zline_second", N, S, M, "zline2")[1]
+    assert second == N * (13 * S + 2 * S + 5 * S + 2 * S * S)
+    # the padded width: s = 20 is computed as S = 32
+    assert bench.algorithmic("p_update", N, 20, M)[1] == N * 2 * 32 * 32
