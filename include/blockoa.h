@@ -174,6 +174,22 @@ int blockoa_build_rhs(const blockoa_operator *op, const double *density, double 
                       blockoa_stream stream);
 
 /*
+ * Right-hand sides b of Eq. 2 from a volumetric heat source q (the q of
+ * Eq. 1, per unit volume), for sources anywhere in the stack -- e.g. the
+ * core and cache device layers of a 3-D IC (Sec. V-A):
+ * b_j(a) = qv_j(a) * dx * dy * dz(a), dz(a) the thickness of cell a's layer
+ * (the volume dx dy dz is formed first, then the product, in float64).
+ * qv: device float64 [chip][s][nz][ny][nx] (W/m^3), chips concatenated;
+ *     owned by the caller, only read.
+ * B: device float64 block vector [n_total][s] (written in full).
+ * Asynchronous on `stream`.  s = 0 is a no-op.
+ * Errors: ERR_INVALID (op NULL, s < 0, qv or B NULL with s > 0), ERR_OOM,
+ * ERR_CUDA.
+ */
+int blockoa_build_rhs_volume(const blockoa_operator *op, const double *qv, double *B, int s,
+                             blockoa_stream stream);
+
+/*
  * Block conjugate gradient on A_c X_c = B_c for every chip c at once
  * (Eq. 3-4, Sec. III-A): all s columns of a chip share one Krylov space.
  * Each iteration: Q = A P; Gamma = P^T Q; Jacobi-scaled pivoted Cholesky of
@@ -365,7 +381,7 @@ const char *blockoa_last_error(void);
  * inputs of one chip shape (e.g. normalised log k, power density and cell
  * coordinates) to a predicted basis solution, used as the initial guess of
  * block CG (blockoa_solve_opts.x0).  The paper trains neural operators on
- * data the method generates (Sec. IV); the network follows the FNO
+ * data the method generates (Sec. V-C); the network follows the FNO
  * literature:
  *   v0 = P x + bP;  u_l = K_l(v_l) + W_l v_l + b_l,  v_{l+1} = gelu(u_l)
  *   (no gelu after the last layer);  y = Q2 gelu(Q1 v_L + c1) + c2,

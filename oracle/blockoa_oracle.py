@@ -15,6 +15,8 @@ against the paper:
                        -div(k grad T) (harmonic face conductances).
 * ``rhs``           -- right-hand sides b of Eq. 2: cell power in W from a
                        top-layer power density in W/m^2.
+* ``rhs_volume``    -- the same from a volumetric source in W/m^3 anywhere
+                       in the stack (the device layers of Sec. V-A's 3-D IC).
 * ``block_cg``      -- block conjugate gradient on A X = B for all columns of
                        one chip at once (Eq. 4, Sec. III-A), O'Leary form with
                        Jacobi-scaled pivoted-Cholesky deflation of the s x s
@@ -130,6 +132,22 @@ def rhs(chip, density) -> np.ndarray:
     area = float(chip.dx) * float(chip.dy)
     top = chip.nx * chip.ny
     B[:top, :] = (density.reshape(s, top) * area).T
+    return B
+
+
+def rhs_volume(chip, qv) -> np.ndarray:
+    """B [n][s]: volumetric source qv (W/m^3, [s][nz][ny][nx]) times the cell
+    volume dx * dy * dz of each cell's layer (the q of Eq. 1 integrated over
+    the cell, Eq. 2).  Plain loop over z-rows."""
+    qv = np.asarray(qv, np.float64)
+    s = qv.shape[0]
+    nxny = chip.nx * chip.ny
+    dz = chip.cell_dz()
+    q = qv.reshape(s, chip.nz, nxny)
+    B = np.zeros((chip.n, s))
+    for z in range(chip.nz):
+        vol = (float(chip.dx) * float(chip.dy)) * float(dz[z])
+        B[z * nxny:(z + 1) * nxny, :] = (q[:, z, :] * vol).T
     return B
 
 

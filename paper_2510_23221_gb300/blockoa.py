@@ -35,6 +35,7 @@ SMALL_FP64_CHOLESKY = 1
 
 EXPORTED = (
     "blockoa_assemble", "blockoa_reassemble", "blockoa_operator_size", "blockoa_operator_total", "blockoa_build_rhs",
+    "blockoa_build_rhs_volume",
     "blockoa_block_solve", "blockoa_combine", "blockoa_combine_ex", "blockoa_apply_basis", "blockoa_apply_operator", "blockoa_pair_check",
     "blockoa_export_conductances", "blockoa_destroy", "blockoa_status_string",
     "blockoa_last_error", "blockoa_kernel_times", "blockoa_reset_kernel_times",
@@ -96,6 +97,7 @@ def _lib():
                                               ct.POINTER(i), ct.POINTER(i), ct.POINTER(i)]
         lib.blockoa_operator_total.argtypes = [vp, ct.POINTER(ct.c_int64), ct.POINTER(i)]
         lib.blockoa_build_rhs.argtypes = [vp, vp, vp, i, vp]
+        lib.blockoa_build_rhs_volume.argtypes = [vp, vp, vp, i, vp]
         lib.blockoa_block_solve.argtypes = [vp, vp, vp, i, ct.POINTER(SolveOpts),
                                             ct.POINTER(SolveStats), vp]
         lib.blockoa_combine.argtypes = [vp, vp, vp, vp, i, i, i, vp]
@@ -253,6 +255,14 @@ def build_rhs(op: Operator, density, B, s: int, stream=None):
     import torch
     _check(_lib().blockoa_build_rhs(op.handle, _ptr(density, torch.float64, "density"),
                                     _ptr(B, torch.float64, "B"), s, _stream(stream)), "build_rhs")
+
+
+def build_rhs_volume(op: Operator, qv, B, s: int, stream=None):
+    """B[a][j] = qv[j][a] * dx dy dz(a): volumetric sources (W/m^3) of every cell."""
+    import torch
+    _check(_lib().blockoa_build_rhs_volume(op.handle, _ptr(qv, torch.float64, "qv"),
+                                           _ptr(B, torch.float64, "B"), s, _stream(stream)),
+           "build_rhs_volume")
 
 
 @dataclass

@@ -309,6 +309,24 @@ __global__ void build_rhs_kernel(const Unit *__restrict__ units, const ChipDev *
   }
 }
 
+// Volumetric sources: B[a][j] = qv_j(a) * V(a), V = dx dy dz of the cell's
+// z-row (per-z-row volumes computed on the host, indexed by ChipDev::lz).
+__global__ void build_rhs_volume_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chips,
+                                        const long long *__restrict__ q_off, const double *__restrict__ vol,
+                                        const double *__restrict__ qv, double *__restrict__ B, int s) {
+  const Unit u = units[blockIdx.x];
+  const ChipDev ch = chips[u.chip];
+  const long long nxny = (long long)ch.nx * ch.ny;
+  const long long base = q_off[u.chip];
+  const long long total = (u.end - u.begin) * s;
+  for (long long t = threadIdx.x; t < total; t += blockDim.x) {
+    const long long a = u.begin + t / s;
+    const int j = (int)(t % s);
+    const long long loc = a - ch.off;
+    B[a * s + j] = __dmul_rn(qv[base + (long long)j * ch.n + loc], vol[ch.lz + loc / nxny]);
+  }
+}
+
 }  // namespace blockoa
 
 using namespace blockoa;
@@ -476,6 +494,7 @@ extern "C" int blockoa_assemble(const blockoa_chip_desc *chips, int n_chips,
   op->n_zrows = (long long)t.zk.size();
   op->cell_area.resize(n_chips);
   for (int c = 0; c < n_chips; ++c) op->cell_area[c] = chips[c].dx * chips[c].dy;
+  op->zrow_dz = t.zdz;
   auto fail = [&](int code) {
     blockoa_destroy(op);
     return code;
@@ -522,6 +541,7 @@ extern "C" int blockoa_reassemble(blockoa_operator *op, const blockoa_chip_desc 
   }
   op->chips = t.tab;   // the layered flag may change with the conductivity description
   for (int c = 0; c < n_chips; ++c) op->cell_area[c] = chips[c].dx * chips[c].dy;
+  op->zrow_dz = t.zdz;
   return run_assembly(op, t, (cudaStream_t)stream);
 }
 
@@ -574,6 +594,43 @@ extern "C" int blockoa_build_rhs(const blockoa_operator *op, const double *densi
   pool_free(d_units, st);
   pool_free(d_rc, st);
   return cuda_status(e, "build_rhs");
+}
+
+extern "C" int blockoa_build_rhs_volume(const blockoa_operator *op, const double *qv, double *B, int s,
+                                        blockoa_stream stream) {
+  if (!op || s < 0) return BLOCKOA_ERR_INVALID;
+  if (s == 0) return BLOCKOA_OK;
+  if (!qv || !B) return BLOCKOA_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<long long> qoff(op->n_chips);
+  std::vector<double> vol(op->n_zrows);
+  long long off = 0;
+  for (int c = 0; c < op->n_chips; ++c) {
+    const ChipDev &ch = op->chips[c];
+    qoff[c] = off;
+    off += (long long)s * ch.n;
+    for (int z = 0; z < ch.nz; ++z) vol[ch.lz + z] = op->cell_area[c] * op->zrow_dz[ch.lz + z];
+  }
+  std::vector<Unit> units = make_units(op, 2048);
+  blockoa_operator *mop = const_cast<blockoa_operator *>(op);
+  void *d_units = nullptr, *d_off = nullptr, *d_vol = nullptr;
+  int rc = pool_alloc(mop, &d_units, sizeof(Unit) * units.size(), st);
+  if (!rc) rc = pool_alloc(mop, &d_off, sizeof(long long) * qoff.size(), st);
+  if (!rc) rc = pool_alloc(mop, &d_vol, sizeof(double) * vol.size(), st);
+  if (rc) { pool_free(d_units, st); pool_free(d_off, st); pool_free(d_vol, st); return rc; }
+  cudaError_t e = cudaMemcpyAsync(d_units, units.data(), sizeof(Unit) * units.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, qoff.data(), sizeof(long long) * qoff.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_vol, vol.data(), sizeof(double) * vol.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    g_launches += 1;
+    build_rhs_volume_kernel<<<(unsigned)units.size(), 256, 0, st>>>(
+        (const Unit *)d_units, op->d_chips, (const long long *)d_off, (const double *)d_vol, qv, B, s);
+    e = cudaGetLastError();
+  }
+  pool_free(d_units, st);
+  pool_free(d_off, st);
+  pool_free(d_vol, st);
+  return cuda_status(e, "build_rhs_volume");
 }
 
 extern "C" int blockoa_export_conductances(const blockoa_operator *op, int chip, double *gx,

@@ -106,6 +106,7 @@ struct blockoa_operator {
   long long n_zrows = 0;                 // z-rows of all chips (layer table records)
   std::vector<blockoa::ChipDev> chips;   // host copy
   std::vector<double> cell_area;         // dx * dy per chip (m^2)
+  std::vector<double> zrow_dz;           // [n_zrows] cell thickness of every z-row (m)
   blockoa::ChipDev *d_chips = nullptr;   // device copy
   double *g64 = nullptr;                 // [n_total][4]: cx, cy, cz, cb (float64)
   float *g32 = nullptr;                  // [n_total][4]: float32 copies

@@ -7,6 +7,11 @@ Workloads (seeded, see synth.py):
   chip128  -- one 128x128x8 chip, s = 32, M = 5000 (the benchmark chip)
   batch256 -- 256 uneven chips (sides 64..256, 4-12 layers), s = 16, M = 20
   chip512  -- one 512x512x16 chip, s = 64, M = 10,000 streamed in chunks
+  paper3dic -- the 3-D IC of the paper's experiments (Sec. V-A) in its
+              ablation setting (Sec. V-E): 5 floorplans of 92x92x12 cells
+              (copper TSV columns, sources in the core and both cache
+              layers), s = 50, M = 1000 per chip, Dirichlet faces (or
+              --boundary robin / mixed), noise epsilon of amplitude 0.01
 
 One pass: assemble, right-hand sides, block CG to the workload's relative
 residual (1e-6), then per chunk of fields the combination T = U C and the
@@ -33,7 +38,11 @@ def main():
     from . import build, synth
 
     p = argparse.ArgumentParser()
-    p.add_argument("--workload", choices=["chip128", "batch256", "chip512"], default="batch256")
+    p.add_argument("--workload", choices=["chip128", "batch256", "chip512", "paper3dic"], default="batch256")
+    p.add_argument("--boundary", choices=list(synth.PAPER_BOUNDARIES), default="dirichlet",
+                   help="boundary scenario of the paper3dic workload")
+    p.add_argument("--noise-amp", type=float, default=None,
+                   help="noise epsilon of the combination (default 0.01 for paper3dic, else 0)")
     p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     p.add_argument("--precond", choices=["none", "jacobi", "zline", "zline2"], default="jacobi")
     p.add_argument("--chunk", type=int, default=1000, help="fields per combine/apply pass")
@@ -47,8 +56,11 @@ def main():
         w = synth.single_chip_workload(M=a.M or 5000)
     elif a.workload == "batch256":
         w = synth.batched_workload(M=a.M or 20)
-    else:
+    elif a.workload == "chip512":
         w = synth.large_chip_workload(M=a.M or 10000)
+    else:
+        w = synth.paper_3dic_workload(M=a.M or 1000, boundary=a.boundary)
+    amp = a.noise_amp if a.noise_amp is not None else (0.01 if a.workload == "paper3dic" else 0.0)
     prec = bo.MIXED if a.precision == "mixed" else bo.FP64
     pc = {"none": bo.PRECOND_NONE, "jacobi": bo.PRECOND_JACOBI, "zline": bo.PRECOND_ZLINE, "zline2": bo.PRECOND_ZLINE2}[a.precond]
     fdt = torch.float32 if prec == bo.MIXED else torch.float64
@@ -80,7 +92,10 @@ def main():
     n = op.n_total
     B = torch.empty(n * s, dtype=torch.float64, device=dev)
     U = torch.empty_like(B)
-    bo.build_rhs(op, dens, B, s)
+    if w.sources is not None:
+        bo.build_rhs_volume(op, dens, B, s)
+    else:
+        bo.build_rhs(op, dens, B, s)
     ev[1].record(stream)
     stats = bo.block_solve(op, B, U, s, rtol=w.rtol, maxiter=a.maxiter, precision=prec, precond=pc,
                            raise_on_error=False)
@@ -95,7 +110,9 @@ def main():
         Mc = min(M, (qi + 1) * chunk) - qi * chunk
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        bo.combine(op, U, C_chunks[qi], T, s, Mc, prec)
+        # noise counters restart per chunk: field index within the chunk, so
+        # chunks use disjoint seeds
+        bo.combine(op, U, C_chunks[qi], T, s, Mc, prec, noise_seed=1 + qi, noise_amp=amp)
         e1.record(stream)
         bo.apply_operator(op, T, q_, Mc, prec)
         e2.record(stream)
@@ -115,7 +132,7 @@ def main():
     kt = bo.kernel_times(op)
     out = {
         "workload": w.name, "chips": op.n_chips, "cells": n, "s": s, "M": M, "chunk": chunk,
-        "precision": a.precision, "precond": a.precond,
+        "precision": a.precision, "precond": a.precond, "noise_amp": amp,
         "ms": {"assemble_rhs": round(setup_ms, 3), "solve": round(solve_ms, 3),
                "combine": round(sum(comb_ms), 3), "apply": round(sum(apply_ms), 3),
                "total": round(total_ms, 3)},

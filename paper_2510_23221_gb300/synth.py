@@ -21,6 +21,19 @@ Recipe (all distributions seeded through ``numpy.random.default_rng``):
 * combination coefficients C ~ N(0, 1), rounded to the nearest bfloat16
   value (round-half-even) so that every consumer sees the same exact operand.
 
+The 3-D IC of the paper's experiments (Sec. V-A) is also available
+(``paper_3dic_chip``, ``paper_3dic_sources``, ``paper_3dic_workload``):
+10 mm x 10 mm x 0.51 mm; three 0.15 mm silicon device layers (core on top,
+then two L2-cache layers), each above a 0.02 mm TIM layer; k = 150 (silicon),
+40 (TIM), 413 (copper TSVs) W/m/K; 156 core blocks (6 at 3-6 W/mm^2, 150 at
+0.5-1 W/mm^2) and two caches per L2 layer (0.02-0.04 W/mm^2); Dirichlet
+(all faces at 50 C), Robin (h = 3e4 on every face) or mixed (Robin top and
+bottom, held sides).  The paper's floorplans are hand-made and not
+published; here the core blocks tile the die in a 12 x 13 grid, each cache
+is half of its layer, TSV bundles are square copper columns through the
+stack at seeded sites, and a device layer's areal power density is spread
+evenly over its thickness.
+
 Seeds: chip j of workload c uses ``1_000_000 * c + j``.
 """
 from __future__ import annotations
@@ -87,6 +100,10 @@ class Workload:
     M: int
     rtol: float
     extra: dict = field(default_factory=dict)
+    # per chip float64 [s][nz][ny][nx], W/m^3: volumetric sources anywhere in
+    # the stack; when set, the right-hand sides come from these (and
+    # ``density`` is unused)
+    sources: Optional[List[np.ndarray]] = None
 
 
 def round_to_bf16(x: np.ndarray) -> np.ndarray:
@@ -224,3 +241,110 @@ def random_small_chip(seed: int, nx: int, ny: int, n_layers: int,
                 layer_dz=CELL_DZ * rng.uniform(0.5, 2.0, n_layers),
                 layer_k=_log_uniform(rng, 1.0, 400.0, n_layers),
                 h_top=h_top, h_bottom=h_bottom, h_side=h_side)
+
+
+# ---------------------------------------------------------------- the paper's 3-D IC (Sec. V-A)
+PAPER_3DIC = {
+    "die_m": (10e-3, 10e-3, 0.51e-3),
+    "device_layers": 3,
+    "device_dz_m": 0.15e-3,
+    "tim_dz_m": 0.02e-3,
+    "k_silicon": 150.0,
+    "k_copper": 413.0,
+    "k_tim": 40.0,
+    "core_blocks": 156,
+    "hot_blocks": 6,
+    "hot_w_per_mm2": (3.0, 6.0),
+    "cool_w_per_mm2": (0.5, 1.0),
+    "caches_per_l2_layer": 2,
+    "l2_w_per_mm2": (0.02, 0.04),
+    "h_robin": 3e4,
+    "t_held_k": 323.15,
+}
+CORE_GRID = (12, 13)          # core blocks along x and y (12 x 13 = 156)
+PAPER_BOUNDARIES = ("dirichlet", "robin", "mixed")
+
+
+def paper_3dic_chip(seed: int, nx: int = 92, ny: int = 92, boundary: str = "dirichlet",
+                    device_cells: int = 3, tsv_bundles: int = 4, tsv_side: int = 2) -> Chip:
+    """The paper's six-layer 3-D IC stack on an nx x ny x (3 (device_cells + 1))
+    grid.  TSV bundles (``tsv_bundles`` squares of ``tsv_side`` cells, seeded
+    sites) are copper through every layer, so the chip carries a per-cell k."""
+    P = PAPER_3DIC
+    if boundary not in PAPER_BOUNDARIES:
+        raise ValueError(f"boundary must be one of {PAPER_BOUNDARIES}")
+    nd = P["device_layers"]
+    layer_nz = np.array([device_cells, 1] * nd, np.int32)
+    layer_dz = np.array([P["device_dz_m"] / device_cells, P["tim_dz_m"]] * nd)
+    layer_k = np.array([P["k_silicon"], P["k_tim"]] * nd)
+    h = {"dirichlet": (np.inf, np.inf, np.inf),
+         "robin": (P["h_robin"], P["h_robin"], P["h_robin"]),
+         "mixed": (P["h_robin"], P["h_robin"], np.inf)}[boundary]
+    chip = Chip(nx=nx, ny=ny, layer_nz=layer_nz, layer_dz=layer_dz, layer_k=layer_k,
+                dx=P["die_m"][0] / nx, dy=P["die_m"][1] / ny,
+                h_top=h[0], h_bottom=h[1], h_side=h[2], t_ambient=P["t_held_k"])
+    if tsv_bundles > 0:
+        rng = np.random.default_rng(seed)
+        k = chip.cell_k()
+        side = min(tsv_side, nx, ny)
+        for _ in range(tsv_bundles):
+            x0 = int(rng.integers(0, nx - side + 1))
+            y0 = int(rng.integers(0, ny - side + 1))
+            k[:, y0:y0 + side, x0:x0 + side] = P["k_copper"]
+        chip.k_cell = k
+    return chip
+
+
+def _block_edges(n: int, parts: int) -> np.ndarray:
+    return np.rint(np.linspace(0.0, n, parts + 1)).astype(np.int64)
+
+
+def paper_3dic_sources(rng, chip: Chip, s: int) -> np.ndarray:
+    """s floorplan power draws as volumetric sources, float64 [s][nz][ny][nx]
+    (W/m^3): per draw, 6 of the 156 core blocks are hot (3-6 W/mm^2), the rest
+    0.5-1 W/mm^2, and each of the two caches of both L2 layers 0.02-0.04
+    W/mm^2 (all uniform); areal density / device-layer thickness."""
+    P = PAPER_3DIC
+    nd = P["device_layers"]
+    dev_cells = int(chip.layer_nz[0])
+    t_dev = P["device_dz_m"]
+    gx, gy = CORE_GRID
+    ex, ey = _block_edges(chip.nx, gx), _block_edges(chip.ny, gy)
+    half = chip.nx // 2
+    out = np.zeros((s, chip.nz, chip.ny, chip.nx))
+    for j in range(s):
+        core = np.zeros((chip.ny, chip.nx))
+        hot = set(rng.choice(gx * gy, P["hot_blocks"], replace=False).tolist())
+        for b in range(gx * gy):
+            bx, by = b % gx, b // gx
+            lo, hi = P["hot_w_per_mm2"] if b in hot else P["cool_w_per_mm2"]
+            core[ey[by]:ey[by + 1], ex[bx]:ex[bx + 1]] = rng.uniform(lo, hi) * 1e6
+        layers = [core]
+        for _ in range(nd - 1):
+            l2 = np.zeros((chip.ny, chip.nx))
+            for c, (x0, x1) in enumerate(((0, half), (half, chip.nx))[:P["caches_per_l2_layer"]]):
+                l2[:, x0:x1] = rng.uniform(*P["l2_w_per_mm2"]) * 1e6
+            layers.append(l2)
+        for d, areal in enumerate(layers):
+            z0 = d * (dev_cells + 1)            # first z-row of device layer d
+            out[j, z0:z0 + dev_cells] = areal / t_dev
+    return out
+
+
+def paper_3dic_workload(n_chips: int = 5, nx: int = 92, ny: int = 92, s: int = 50, M: int = 1000,
+                        boundary: str = "dirichlet", cfg: int = 6, rtol: float = 1e-6) -> Workload:
+    """N_k = n_chips floorplans of the 3-D IC (own TSV sites and power draws),
+    N_basis = s sources each, M fields per chip: the paper's ablation setting
+    (Sec. V-E: N_basis 50, N_k 5, N_data 5000, n ~ 1e5, Dirichlet) at the
+    defaults (92 x 92 x 12 = 101,568 cells per chip)."""
+    chips, srcs, Cs = [], [], []
+    for j in range(n_chips):
+        seed = 1_000_000 * cfg + j
+        chip = paper_3dic_chip(seed, nx, ny, boundary)
+        rng = np.random.default_rng(seed + 500_000)
+        chips.append(chip)
+        srcs.append(paper_3dic_sources(rng, chip, s))
+        Cs.append(coefficients(rng, s, M))
+    empty = [np.zeros((s, c.ny, c.nx)) for c in chips]
+    return Workload(f"paper3dic_{boundary}_{n_chips}x{nx}x{ny}x{chips[0].nz}_s{s}_M{M}", chips, empty, Cs,
+                    s=s, M=M, rtol=rtol, sources=srcs)

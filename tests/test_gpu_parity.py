@@ -556,6 +556,71 @@ def test_invalid_calls_return_invalid():
         bo.apply_operator(op, T, T, 1, bo.FP64)
 
 
+# ---------------------------------------------------------------- the paper's 3-D IC (Sec. V-A)
+def test_build_rhs_volume_exact():
+    """Volumetric sources on two chips of different stacks: bit-exact."""
+    chips = [synth.paper_3dic_chip(3, nx=13, ny=14, device_cells=2),
+             synth.random_small_chip(4, 9, 7, 3, layer_nz=[2, 1, 2])]
+    rng = np.random.default_rng(8)
+    s = 5
+    qvs = [synth.paper_3dic_sources(rng, chips[0], s),
+           rng.uniform(0.0, 1e9, (s, chips[1].nz, chips[1].ny, chips[1].nx))]
+    op = bo.assemble(chips)
+    B = torch.empty(op.n_total * s, dtype=torch.float64, device="cuda")
+    bo.build_rhs_volume(op, cuda(np.concatenate([q.ravel() for q in qvs])), B, s)
+    Bh = B.cpu().numpy()
+    for c, chip in enumerate(chips):
+        sz = op.sizes[c]
+        assert np.array_equal(Bh[sz["off"] * s:(sz["off"] + sz["n"]) * s].reshape(-1, s),
+                              orc.rhs_volume(chip, qvs[c]))
+
+
+@pytest.mark.parametrize("precision", [bo.FP64, bo.MIXED])
+@pytest.mark.parametrize("boundary", synth.PAPER_BOUNDARIES)
+def test_paper_3dic_pipeline(boundary, precision):
+    """Two floorplans of the six-layer 3-D IC (copper TSV columns, sources in
+    the core and both cache layers) batched in one operator, under each of
+    the paper's boundary scenarios: sources, basis, T = U C + epsilon (Eq. 5,
+    amplitude 0.01 as in the paper's experiments) and q = A T against the
+    oracle, and the pairs' own consistency."""
+    chips = [synth.paper_3dic_chip(40 + i, nx=24, ny=20, boundary=boundary, device_cells=2) for i in range(2)]
+    s, M, seed, amp = 8, 16, 77, 0.01
+    rng = np.random.default_rng(41)
+    qvs = [synth.paper_3dic_sources(rng, c, s) for c in chips]
+    Cs = [synth.coefficients(rng, s, M) for c in chips]
+    op = bo.assemble(chips)
+    fdt = torch.float64 if precision == bo.FP64 else torch.float32
+    B = torch.empty(op.n_total * s, dtype=torch.float64, device="cuda")
+    bo.build_rhs_volume(op, cuda(np.concatenate([q.ravel() for q in qvs])), B, s)
+    U = torch.empty_like(B)
+    pc = bo.PRECOND_ZLINE2 if precision == bo.MIXED else bo.PRECOND_NONE
+    stats = bo.block_solve(op, B, U, s, rtol=1e-12, precision=precision, precond=pc)
+    assert all(st.status == bo.OK and st.relres_max <= 1e-12 for st in stats)
+    T = torch.empty(M * op.n_total, dtype=fdt, device="cuda")
+    q = torch.empty_like(T)
+    bo.combine(op, U, cuda(np.concatenate([c.ravel() for c in Cs])), T, s, M, precision,
+               noise_seed=seed, noise_amp=amp)
+    bo.apply_operator(op, T, q, M, precision)
+    e_pair = torch.empty(op.n_chips * M, dtype=torch.float64, device="cuda")
+    bo.pair_check(op, T, q, M, precision, e_pair)
+    Bh, Uh = B.cpu().numpy(), U.cpu().numpy()
+    Th, qh = T.cpu().numpy().astype(np.float64), q.cpu().numpy().astype(np.float64)
+    tol_u, tol_f, tol_q = (1e-10, 1e-10, 1e-13) if precision == bo.FP64 else (1e-9, 1e-6, 2e-6)
+    for c, chip in enumerate(chips):
+        off, n = op.sizes[c]["off"], chip.n
+        A = orc.assemble(chip)
+        B_or = orc.rhs_volume(chip, qvs[c])
+        assert np.array_equal(Bh[off * s:(off + n) * s].reshape(n, s), B_or)
+        U_or, info = orc.block_cg(A, B_or, rtol=1e-12)
+        assert np.all(relcols(Uh[off * s:(off + n) * s].reshape(n, s), U_or) < tol_u)
+        T_or = orc.combine(U_or, Cs[c]) + orc.noise(seed, np.arange(off, off + n), M, amp)
+        Tc = Th[off * M:(off + n) * M].reshape(M, n)
+        assert np.all(relcols(Tc, T_or, axis=1) < tol_f)
+        q_or = orc.apply_operator(A, Tc)          # q of the stored fields
+        assert np.all(relcols(qh[off * M:(off + n) * M].reshape(M, n), q_or, axis=1) < tol_q)
+    assert float(e_pair.max()) <= (1e-10 if precision == bo.FP64 else 1e-6)
+
+
 def test_empty_sizes_are_noops():
     chip = synth.random_small_chip(4, 4, 4, 2)
     op = bo.assemble([chip])

@@ -25,6 +25,9 @@ def _run_pins():
         ("ladder_y", lambda: pins.test_lateral_ladder_closed_form("y", 4e4)),
         ("ladder_x_held", lambda: pins.test_lateral_ladder_closed_form("x", np.inf)),
         ("rhs", pins.test_rhs_total_power_and_placement),
+        ("rhs_volume_unit", pins.test_rhs_volume_unit_sources),
+        ("rhs_volume_total", pins.test_rhs_volume_paper_stack_total_power),
+        ("rhs_volume_chain", pins.test_rhs_volume_chain_closed_form),
         ("finite_termination", pins.test_finite_termination),
         ("textbook_cg", pins.test_single_column_equals_textbook_cg),
         ("deflation", pins.test_deflation_duplicate_and_zero_columns),
@@ -45,7 +48,7 @@ def _run_pins():
 
 
 REAL = {name: getattr(orc, name) for name in
-        ("rhs", "block_cg", "face_conductances", "_gram_solve", "_series")}
+        ("rhs", "rhs_volume", "block_cg", "face_conductances", "_gram_solve", "_series")}
 REAL_ROBIN = orc._robin
 
 
@@ -76,6 +79,25 @@ def _mut_rhs_bottom_layer(chip, density):
     out = np.zeros_like(B)
     out[chip.n - top:] = B[:top]
     return out
+
+
+def _mut_rhs_volume_no_dz(chip, qv):
+    # cell volume taken as dx * dy (the layer thickness dropped)
+    B = REAL["rhs_volume"](chip, qv)
+    return B / np.repeat(chip.cell_dz(), chip.nx * chip.ny)[:, None]
+
+
+def _mut_rhs_volume_top_dz(chip, qv):
+    # every row given the top row's thickness
+    B = REAL["rhs_volume"](chip, qv)
+    dz = np.repeat(chip.cell_dz(), chip.nx * chip.ny)[:, None]
+    return B / dz * chip.cell_dz()[0]
+
+
+def _mut_rhs_volume_rows_flipped(chip, qv):
+    # z numbered from the bottom
+    qv = np.asarray(qv)[:, ::-1].copy()
+    return REAL["rhs_volume"](chip, qv)
 
 
 def _mut_combine_no_transpose(U, C):
@@ -122,6 +144,9 @@ MUTANTS = {
     "robin_held_as_adiabatic": ("_robin", _mut_robin_held_as_adiabatic),
     "rhs_bottom_layer": ("rhs", _mut_rhs_bottom_layer),
     "combine_no_transpose": ("combine", _mut_combine_no_transpose),
+    "rhs_volume_no_dz": ("rhs_volume", _mut_rhs_volume_no_dz),
+    "rhs_volume_top_dz": ("rhs_volume", _mut_rhs_volume_top_dz),
+    "rhs_volume_rows_flipped": ("rhs_volume", _mut_rhs_volume_rows_flipped),
     "beta_sign": ("block_cg", _make_bcg_mutant("beta_sign")),
     "alpha_scale": ("block_cg", _make_bcg_mutant("alpha_scale")),
     "gz_wrong_index": ("face_conductances", _mut_gz_wrong_index),

@@ -190,6 +190,71 @@ def test_rhs_total_power_and_placement():
     assert B[3 * 6 + 2, 1] == dens[1, 3, 2] * (chip.dx * chip.dy)
 
 
+def test_rhs_volume_unit_sources():
+    """A volumetric source of P / V_a in one cell a (V_a = dx dy times the
+    thickness of a's layer, taken from the layer table) is P watts in cell a
+    and nothing elsewhere, for cells in layers of different thickness."""
+    chip = synth.random_small_chip(9, 4, 3, 4, layer_nz=[2, 1, 3, 1])
+    nxny = chip.nx * chip.ny
+    layer_of_row = np.repeat(np.arange(4), chip.layer_nz)
+    cells = [(0, 1, 2), (2, 0, 3), (3, 2, 1), (6, 1, 0)]   # (z, y, x)
+    P = 0.125
+    qv = np.zeros((len(cells), chip.nz, chip.ny, chip.nx))
+    for j, (z, y, x) in enumerate(cells):
+        qv[j, z, y, x] = P / (chip.dx * chip.dy * chip.layer_dz[layer_of_row[z]])
+    B = orc.rhs_volume(chip, qv)
+    assert B.shape == (chip.n, len(cells))
+    for j, (z, y, x) in enumerate(cells):
+        a = z * nxny + y * chip.nx + x
+        assert B[a, j] == pytest.approx(P, rel=1e-15)
+        assert np.count_nonzero(B[:, j]) == 1
+
+
+def test_rhs_volume_paper_stack_total_power():
+    """On the 3-D IC stack every draw's total power is the sum over device
+    layers of areal density times cell area (the TIM layers carry none)."""
+    chip = synth.paper_3dic_chip(3, nx=13, ny=14, device_cells=2)
+    qv = synth.paper_3dic_sources(np.random.default_rng(3), chip, 2)
+    B = orc.rhs_volume(chip, qv)
+    t_dev = synth.PAPER_3DIC["device_dz_m"]
+    first_rows = [0, 3, 6]                      # first z-row of each device layer
+    areal = qv[:, first_rows] * t_dev           # W/m^2 per device layer
+    expect = areal.sum(axis=(1, 2, 3)) * chip.dx * chip.dy
+    assert np.allclose(B.sum(axis=0), expect, rtol=1e-13)
+    tim_rows = [2, 5, 8]
+    nxny = chip.nx * chip.ny
+    for z in tim_rows:
+        assert np.all(B[z * nxny:(z + 1) * nxny] == 0)
+
+
+def test_rhs_volume_chain_closed_form():
+    """Laterally uniform sources in all three device layers of the 3-D IC
+    stack, Robin top, insulated elsewhere: the heat of every cell leaves
+    through the top, so the flux through the face below row z is the power
+    of the rows beneath it, and the solution is the series resistor chain
+    (half-cell resistances dz / (2 k S), convection 1 / (h S))."""
+    chip = synth.paper_3dic_chip(0, nx=3, ny=2, device_cells=2, tsv_bundles=0)
+    chip.h_top, chip.h_bottom, chip.h_side = 2e4, 0.0, 0.0
+    S = chip.dx * chip.dy
+    qrow = np.zeros(chip.nz)
+    qrow[[0, 1]] = 4e9
+    qrow[[3, 4]] = 2e8
+    qrow[[6, 7]] = 1.5e8
+    qv = np.broadcast_to(qrow[None, :, None, None], (1, chip.nz, chip.ny, chip.nx)).copy()
+    B = orc.rhs_volume(chip, qv)
+    U, info = orc.block_cg(orc.assemble(chip), B, rtol=1e-15, maxiter=400)
+    theta = U[:, 0].reshape(chip.nz, chip.ny, chip.nx)
+    dz = np.repeat(chip.layer_dz, chip.layer_nz)
+    k = np.repeat(chip.layer_k, chip.layer_nz)
+    p = qrow * S * dz                          # W per cell of row z
+    below = np.cumsum(p[::-1])[::-1]            # power of rows z .. bottom
+    expect = np.empty(chip.nz)
+    expect[0] = below[0] * (dz[0] / (2 * k[0] * S) + 1.0 / (chip.h_top * S))
+    for z in range(chip.nz - 1):
+        expect[z + 1] = expect[z] + below[z + 1] * (dz[z] / (2 * k[z] * S) + dz[z + 1] / (2 * k[z + 1] * S))
+    assert np.allclose(theta, expect[:, None, None], rtol=1e-12, atol=0)
+
+
 # ---------------------------------------------------------------- block CG
 @pytest.mark.parametrize("chip", _chips())
 def test_block_cg_matches_dense_direct(chip):
