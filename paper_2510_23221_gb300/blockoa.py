@@ -147,8 +147,12 @@ def _stream(stream) -> Optional[int]:
     return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
 
 
-def _ptr(t, dtype=None, name="tensor"):
-    """Raw device pointer of a contiguous CUDA tensor (None passes NULL)."""
+def _ptr(t, dtype=None, name="tensor", need: int = 0):
+    """Raw device pointer of a contiguous CUDA tensor (None passes NULL).
+
+    ``need`` is the number of elements the call reads or writes through the
+    pointer: a smaller tensor is refused here, before any launch, since the
+    library sees only the pointer."""
     if t is None:
         return None
     import torch
@@ -158,6 +162,8 @@ def _ptr(t, dtype=None, name="tensor"):
         raise ValueError(f"{name} must be contiguous")
     if dtype is not None and t.dtype != dtype:
         raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if t.numel() < need:
+        raise ValueError(f"{name} holds {t.numel()} elements, the call needs {need}")
     return t.data_ptr()
 
 
@@ -253,15 +259,16 @@ def operator_size(op: Operator, chip: int):
 
 def build_rhs(op: Operator, density, B, s: int, stream=None):
     import torch
-    _check(_lib().blockoa_build_rhs(op.handle, _ptr(density, torch.float64, "density"),
-                                    _ptr(B, torch.float64, "B"), s, _stream(stream)), "build_rhs")
+    top = sum(z["nx"] * z["ny"] for z in op.sizes)
+    _check(_lib().blockoa_build_rhs(op.handle, _ptr(density, torch.float64, "density", s * top),
+                                    _ptr(B, torch.float64, "B", op.n_total * s), s, _stream(stream)), "build_rhs")
 
 
 def build_rhs_volume(op: Operator, qv, B, s: int, stream=None):
     """B[a][j] = qv[j][a] * dx dy dz(a): volumetric sources (W/m^3) of every cell."""
     import torch
-    _check(_lib().blockoa_build_rhs_volume(op.handle, _ptr(qv, torch.float64, "qv"),
-                                           _ptr(B, torch.float64, "B"), s, _stream(stream)),
+    _check(_lib().blockoa_build_rhs_volume(op.handle, _ptr(qv, torch.float64, "qv", s * op.n_total),
+                                           _ptr(B, torch.float64, "B", op.n_total * s), s, _stream(stream)),
            "build_rhs_volume")
 
 
@@ -282,11 +289,11 @@ def block_solve(op: Operator, B, X, s: int, rtol: float = 1e-12, maxiter: int = 
     import torch
     o = SolveOpts(rtol=rtol, maxiter=maxiter, precision=precision, inner_rtol=inner_rtol,
                   max_refine=max_refine, deflate_tol=deflate_tol,
-                  x0=_ptr(x0, torch.float64, "x0"), check_every=check_every, precond=precond,
+                  x0=_ptr(x0, torch.float64, "x0", op.n_total * s), check_every=check_every, precond=precond,
                   small_solve=small_solve, independent=int(bool(independent)))
     st = (SolveStats * op.n_chips)()
-    code = _lib().blockoa_block_solve(op.handle, _ptr(B, torch.float64, "B"),
-                                      _ptr(X, torch.float64, "X"), s, ct.byref(o), st,
+    code = _lib().blockoa_block_solve(op.handle, _ptr(B, torch.float64, "B", op.n_total * s),
+                                      _ptr(X, torch.float64, "X", op.n_total * s), s, ct.byref(o), st,
                                       _stream(stream))
     stats = [Stats(x.status, x.iters, x.refine_steps, x.deflated_cols, x.relres_max) for x in st]
     if raise_on_error:
@@ -300,35 +307,39 @@ def combine(op: Operator, U, C, T, s: int, M: int, dtype: int, stream=None, nois
     (blockoa_combine_ex: uniform in [-noise_amp, noise_amp) K from Philox)."""
     import torch
     tdt = torch.float64 if dtype == FP64 else torch.float32
+    pU = _ptr(U, torch.float64, "U", op.n_total * s)
+    pC = _ptr(C, torch.float64, "C", op.n_chips * s * M)
+    pT = _ptr(T, tdt, "T", op.n_total * M)
     if noise_amp == 0.0:
-        _check(_lib().blockoa_combine(op.handle, _ptr(U, torch.float64, "U"), _ptr(C, torch.float64, "C"),
-                                      _ptr(T, tdt, "T"), s, M, dtype, _stream(stream)), "combine")
+        _check(_lib().blockoa_combine(op.handle, pU, pC, pT, s, M, dtype, _stream(stream)), "combine")
         return
     o = CombineOpts(noise_seed=int(noise_seed) & ((1 << 64) - 1), noise_amp=float(noise_amp))
-    _check(_lib().blockoa_combine_ex(op.handle, _ptr(U, torch.float64, "U"), _ptr(C, torch.float64, "C"),
-                                     _ptr(T, tdt, "T"), s, M, dtype, ct.byref(o), _stream(stream)),
+    _check(_lib().blockoa_combine_ex(op.handle, pU, pC, pT, s, M, dtype, ct.byref(o), _stream(stream)),
            "combine_ex")
 
 
 def apply_operator(op: Operator, T, q, M: int, dtype: int, stream=None):
     import torch
     tdt = torch.float64 if dtype == FP64 else torch.float32
-    _check(_lib().blockoa_apply_operator(op.handle, _ptr(T, tdt, "T"), _ptr(q, tdt, "q"), M, dtype,
+    _check(_lib().blockoa_apply_operator(op.handle, _ptr(T, tdt, "T", op.n_total * M),
+                                         _ptr(q, tdt, "q", op.n_total * M), M, dtype,
                                          _stream(stream)), "apply_operator")
 
 
 def apply_basis(op: Operator, U, AU, s: int, stream=None):
     """AU = A U on a float64 [n][s] block (blockoa_apply_basis)."""
     import torch
-    _check(_lib().blockoa_apply_basis(op.handle, _ptr(U, torch.float64, "U"), _ptr(AU, torch.float64, "AU"), s,
+    _check(_lib().blockoa_apply_basis(op.handle, _ptr(U, torch.float64, "U", op.n_total * s),
+                                      _ptr(AU, torch.float64, "AU", op.n_total * s), s,
                                       _stream(stream)), "apply_basis")
 
 
 def pair_check(op: Operator, T, q, M: int, dtype: int, e_pair, stream=None):
     import torch
     tdt = torch.float64 if dtype == FP64 else torch.float32
-    _check(_lib().blockoa_pair_check(op.handle, _ptr(T, tdt, "T"), _ptr(q, tdt, "q"), M, dtype,
-                                     _ptr(e_pair, torch.float64, "e_pair"), _stream(stream)),
+    _check(_lib().blockoa_pair_check(op.handle, _ptr(T, tdt, "T", op.n_total * M),
+                                     _ptr(q, tdt, "q", op.n_total * M), M, dtype,
+                                     _ptr(e_pair, torch.float64, "e_pair", op.n_chips * M), _stream(stream)),
            "pair_check")
 
 

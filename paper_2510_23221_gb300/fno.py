@@ -104,22 +104,27 @@ class Fno:
         except Exception:
             pass
 
+    def _cells(self, batch: int) -> int:
+        return batch * self.shape.nx * self.shape.ny * self.shape.nz
+
     def forward(self, x, y, batch: int, keep: bool = False, stream=None):
         import torch
-        bo._check(_lib().blockoa_fno_forward(self.handle, bo._ptr(x, torch.float32, "x"),
-                                             bo._ptr(y, torch.float32, "y"), batch, int(keep),
+        n = self._cells(batch)
+        bo._check(_lib().blockoa_fno_forward(self.handle, bo._ptr(x, torch.float32, "x", n * self.shape.c_in),
+                                             bo._ptr(y, torch.float32, "y", n), batch, int(keep),
                                              bo._stream(stream)), "fno_forward")
 
     def mse(self, y, target, batch: int, dy, loss, stream=None):
         import torch
-        bo._check(_lib().blockoa_fno_mse(self.handle, bo._ptr(y, torch.float32, "y"),
-                                         bo._ptr(target, torch.float32, "target"), batch,
-                                         bo._ptr(dy, torch.float32, "dy"), bo._ptr(loss, torch.float32, "loss"),
+        n = self._cells(batch)
+        bo._check(_lib().blockoa_fno_mse(self.handle, bo._ptr(y, torch.float32, "y", n),
+                                         bo._ptr(target, torch.float32, "target", n), batch,
+                                         bo._ptr(dy, torch.float32, "dy", n), bo._ptr(loss, torch.float32, "loss", 1),
                                          bo._stream(stream)), "fno_mse")
 
     def backward(self, dy, batch: int, stream=None):
         import torch
-        bo._check(_lib().blockoa_fno_backward(self.handle, bo._ptr(dy, torch.float32, "dy"), batch,
+        bo._check(_lib().blockoa_fno_backward(self.handle, bo._ptr(dy, torch.float32, "dy", self._cells(batch)), batch,
                                               bo._stream(stream)), "fno_backward")
 
     def zero_grad(self, stream=None):

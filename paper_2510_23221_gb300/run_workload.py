@@ -68,9 +68,11 @@ def main():
     s, M = w.s, w.M
     chunk = min(a.chunk, M)
     n_chunks = (M + chunk - 1) // chunk
-    # inputs resident: densities, and C split into per-chunk [chip][s][chunk] blocks
+    # inputs resident: densities (or volumetric sources), and C split into
+    # per-chunk [chip][s][chunk] blocks
+    src = w.sources if w.sources is not None else w.density
     dens = torch.from_numpy(np.concatenate([np.ascontiguousarray(d, np.float64).ravel()
-                                            for d in w.density])).to(dev)
+                                            for d in src])).to(dev)
     C_chunks = []
     for q in range(n_chunks):
         m0, m1 = q * chunk, min(M, (q + 1) * chunk)

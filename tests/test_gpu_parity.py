@@ -621,6 +621,36 @@ def test_paper_3dic_pipeline(boundary, precision):
     assert float(e_pair.max()) <= (1e-10 if precision == bo.FP64 else 1e-6)
 
 
+def test_short_buffers_are_refused_before_launch():
+    """The library sees only pointers: the binding refuses a tensor smaller
+    than the call reads or writes, before anything is launched."""
+    chips = [synth.paper_3dic_chip(9, nx=10, ny=9, device_cells=1), synth.random_small_chip(9, 7, 5, 3)]
+    op = bo.assemble(chips)
+    s, M = 5, 3
+    n = op.n_total
+    B = torch.zeros(n * s, dtype=torch.float64, device="cuda")
+    top = sum(c.nx * c.ny for c in chips)
+    with pytest.raises(ValueError):
+        bo.build_rhs_volume(op, torch.zeros(top * s, dtype=torch.float64, device="cuda"), B, s)
+    with pytest.raises(ValueError):
+        bo.build_rhs(op, torch.zeros(top * s - 1, dtype=torch.float64, device="cuda"), B, s)
+    with pytest.raises(ValueError):
+        bo.block_solve(op, B, B[: n * s - 1], s)
+    T = torch.zeros(n * M, dtype=torch.float32, device="cuda")
+    C = torch.zeros(len(chips) * s * M, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        bo.combine(op, B, C[:-1], T, s, M, bo.MIXED)
+    with pytest.raises(ValueError):
+        bo.apply_operator(op, T, T[:-1].clone(), M, bo.MIXED)
+    with pytest.raises(ValueError):
+        bo.pair_check(op, T, T.clone(), M, bo.MIXED, torch.zeros(len(chips) * M - 1, dtype=torch.float64,
+                                                                device="cuda"))
+    # the right sizes go through
+    bo.build_rhs_volume(op, torch.ones(n * s, dtype=torch.float64, device="cuda"), B, s)
+    torch.cuda.synchronize()
+    assert float(B.min()) > 0
+
+
 def test_empty_sizes_are_noops():
     chip = synth.random_small_chip(4, 4, 4, 2)
     op = bo.assemble([chip])
