@@ -108,3 +108,59 @@ def test_oracle_on_the_paper_boundaries(boundary):
     assert np.allclose(orc.boundary_loss(chip, theta), B.sum(axis=0), rtol=1e-10)
     U, info = orc.block_cg(A, B, rtol=1e-12)
     assert np.allclose(U, theta, rtol=1e-9, atol=1e-9 * np.abs(theta).max())
+
+
+def _stack_continuous(zc, tops, k, g, h):
+    """Exact theta(z) of -(k theta')' = g(z) through a stack of layers (z down
+    from the cooled top, layer i on [tops[i], tops[i+1]) with constant k[i],
+    g[i]), insulated bottom, h theta = k theta' at z = 0.  F(z), the heat
+    crossing depth z upwards, is the source beneath it; theta is F(0)/h plus
+    the integral of F/k from the top."""
+    L = tops[-1]
+
+    def F(z):
+        return sum(g[i] * max(0.0, tops[i + 1] - max(z, tops[i])) for i in range(len(k)))
+
+    out = np.empty(len(zc))
+    for m, z in enumerate(zc):
+        th = F(0.0) / h
+        for i in range(len(k)):
+            a, b = tops[i], min(tops[i + 1], z)
+            if b <= a:
+                break
+            # F is linear on [a, b] inside one layer: trapezoid is exact
+            th += (b - a) * (F(a) + F(b)) / (2.0 * k[i])
+        out[m] = th
+    assert L > 0
+    return out
+
+
+def test_oracle_converges_to_the_stack_solution_with_three_heated_layers():
+    """The paper's six-layer stack with a volumetric source in each device
+    layer, convective top, insulated elsewhere: refining every layer along z
+    converges to the continuous solution at second order."""
+    h = 3e4
+    q = [4e9, 3e8, 2e8]                       # W/m^3 in the core and the two cache layers
+    errs = []
+    for r in (1, 2, 4, 8):
+        chip = synth.paper_3dic_chip(0, nx=2, ny=2, device_cells=3 * r, tsv_bundles=0)
+        chip.layer_nz = np.array([3 * r, r] * 3, np.int32)
+        chip.layer_dz = np.array([P["device_dz_m"] / (3 * r), P["tim_dz_m"] / r] * 3)
+        chip.h_top, chip.h_bottom, chip.h_side = h, 0.0, 0.0
+        dz = chip.cell_dz()
+        qrow = np.zeros(chip.nz)
+        z0 = 0
+        for d in range(3):
+            qrow[z0:z0 + 3 * r] = q[d]
+            z0 += 4 * r
+        qv = np.broadcast_to(qrow[None, :, None, None], (1, chip.nz, chip.ny, chip.nx)).copy()
+        B = orc.rhs_volume(chip, qv)
+        theta = np.linalg.solve(orc.assemble(chip).toarray(), B)[:, 0].reshape(chip.nz, 2, 2)[:, 0, 0]
+        tops = np.concatenate([[0.0], np.cumsum(chip.layer_dz * chip.layer_nz)])
+        zc = np.cumsum(dz) - dz / 2
+        g = [q[0], 0.0, q[1], 0.0, q[2], 0.0]
+        exact = _stack_continuous(zc, tops, chip.layer_k, g, h)
+        errs.append(np.abs(theta - exact).max() / np.abs(exact).max())
+    rates = [np.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert errs[-1] < 1e-4, errs
+    assert all(rt > 1.8 for rt in rates), (errs, rates)
