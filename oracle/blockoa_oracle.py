@@ -27,6 +27,8 @@ against the paper:
 * ``noise``         -- the epsilon term of Eq. 5: uniform noise per cell and
                        field from ``philox4x64_10``, a counter-based generator
                        written from its published definition.
+* ``noise_gaussian``-- the Gaussian variant of that noise (Box-Muller from a
+                       second Philox stream); no library counterpart yet.
 * ``apply_operator``-- operator action q = A T (Eq. 6, Sec. III-C).
 * ``pair_errors``   -- relative L2 errors of generated pairs.
 
@@ -306,6 +308,28 @@ def noise(seed, cells, M, amp) -> np.ndarray:
                 m = 4 * g + j
                 if m < M:
                     out[m, i] = amp * (2.0 * ((w[j] >> 11) * 2.0 ** -53) - 1.0)
+    return out
+
+
+def noise_gaussian(seed, cells, M, sigma) -> np.ndarray:
+    """Zero-mean Gaussian epsilon [M][len(cells)] of standard deviation sigma
+    (the Gaussian variant of the noise experiments, Sec. V-D): for global
+    cell a and field m, words 2 (m % 2) and 2 (m % 2) + 1 of Philox4x64-10 at
+    counter (a, m // 2, 1, 0) and key (seed, 0) give u1 = ((w1 >> 11) + 1/2)
+    2^-53 in (0, 1) and u2 = (w2 >> 11) 2^-53, and epsilon = sigma
+    sqrt(-2 ln u1) cos(2 pi u2) (Box and Muller, 1958).  The third counter word
+    keeps this stream apart from the uniform one.  Plain loops: small cases
+    only."""
+    out = np.empty((M, len(cells)))
+    for i, a in enumerate(cells):
+        for g in range((M + 1) // 2):
+            w = philox4x64_10((int(a), g, 1, 0), (seed, 0))
+            for j in range(2):
+                m = 2 * g + j
+                if m < M:
+                    u1 = ((w[2 * j] >> 11) + 0.5) * 2.0 ** -53
+                    u2 = (w[2 * j + 1] >> 11) * 2.0 ** -53
+                    out[m, i] = sigma * np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
     return out
 
 

@@ -429,6 +429,26 @@ def test_noise_is_uniform_bounded_and_reproducible():
     assert np.allclose(e[12:16, 0], [amp * (2 * ((x >> 11) * 2.0 ** -53) - 1) for x in w], rtol=0, atol=0)
 
 
+def test_gaussian_noise_is_normal_reproducible_and_apart_from_the_uniform_stream():
+    from scipy import stats
+    sigma, M = 0.02, 32
+    cells = np.arange(500, 1100)
+    e = orc.noise_gaussian(91, cells, M, sigma)
+    assert e.shape == (M, len(cells)) and np.all(np.isfinite(e))
+    x = e.ravel() / sigma
+    N = x.size
+    assert abs(x.mean()) < 5 / np.sqrt(N) and abs(x.std() - 1) < 5 / np.sqrt(2 * N)
+    assert stats.kstest(x, "norm").pvalue > 1e-3                 # the normal law, not just two moments
+    assert abs(stats.kurtosis(x)) < 0.1
+    assert np.array_equal(e[:, 7:11], orc.noise_gaussian(91, cells[7:11], M, sigma))
+    u = orc.noise(91, cells, M, 1.0)                             # same seed, uniform stream
+    assert abs(np.corrcoef(u.ravel(), x)[0, 1]) < 5 / np.sqrt(N)
+    # one generator block per two fields: Box-Muller of words (0, 1) and (2, 3)
+    w = orc.philox4x64_10((int(cells[3]), 5, 1, 0), (91, 0))
+    u1, u2 = ((w[2] >> 11) + 0.5) * 2.0 ** -53, (w[3] >> 11) * 2.0 ** -53
+    assert e[11, 3] == sigma * np.sqrt(-2 * np.log(u1)) * np.cos(2 * np.pi * u2)
+
+
 def test_bf16_rounding_matches_torch():
     x = np.random.default_rng(5).standard_normal(4096)
     ours = synth.round_to_bf16(x)
