@@ -134,8 +134,18 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.f.close()
+        with open(self.path) as f:
+            out = self.summarize(f)
+        os.unlink(self.path)
+        return out
+
+    @staticmethod
+    def summarize(lines):
+        """Median SM clock, maximum SM clock and the throttle reasons seen
+        in nvidia-smi rows of FIELDS (csv, no header, no units); None when
+        no row parses."""
         rows = []
-        for line in open(self.path):
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -143,7 +153,6 @@ class ClockSampler:
                 rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
             except ValueError:
                 continue
-        os.unlink(self.path)
         if not rows:
             return None
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]

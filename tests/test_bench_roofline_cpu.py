@@ -59,3 +59,18 @@ def test_cost_model_follows_the_preconditioner():
     assert second == N * (13 * S + 2 * S + 5 * S + 2 * S * S)
     # the padded width: s = 20 is computed as S = 32
     assert bench.algorithmic("p_update", N, 20, M)[1] == N * 2 * 32 * 32
+
+
+def test_clock_rows_summary():
+    lines = [
+        "0, 1965, 2070, 1012.34, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "0, 1890, 2070, 1388.10, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n",
+        "0, 1920, 2070, 1290.00, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "0, [N/A], 2070, [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]\n",   # unparsable sample: skipped
+        "garbage\n",
+    ]
+    out = bench.ClockSampler.summarize(lines)
+    assert out == {"sm_mhz": 1920.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert bench.ClockSampler.summarize(["x, y\n"]) is None
+    hw = bench.ClockSampler.summarize(["0, 900, 2070, 700, 0x8, Active, Active, Not Active, Not Active\n"])
+    assert hw["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
