@@ -34,6 +34,8 @@ def _run_pins():
         ("combine_apply", pins.test_combine_and_apply_brute_force),
         ("linearity", pins.test_linearity_and_pair_consistency),
         ("pivoted_cholesky", pins.test_pivoted_cholesky_against_library),
+        ("philox", pins.test_philox_matches_library_generator),
+        ("noise", pins.test_noise_is_uniform_bounded_and_reproducible),
     ]
     for chip in pins._chips():
         checks.append(("spd", lambda c=chip: pins.test_operator_symmetric_bitwise_and_spd(c)))
@@ -48,7 +50,8 @@ def _run_pins():
 
 
 REAL = {name: getattr(orc, name) for name in
-        ("rhs", "rhs_volume", "block_cg", "face_conductances", "_gram_solve", "_series")}
+        ("rhs", "rhs_volume", "block_cg", "face_conductances", "_gram_solve", "_series",
+         "scaled_pivoted_cholesky", "noise")}
 REAL_ROBIN = orc._robin
 
 
@@ -100,6 +103,51 @@ def _mut_rhs_volume_rows_flipped(chip, qv):
     return REAL["rhs_volume"](chip, qv)
 
 
+def _mut_rhs_no_area(chip, density):
+    # power density deposited as if it were power per cell
+    return REAL["rhs"](chip, density) / (chip.dx * chip.dy)
+
+
+def _mut_cholesky_no_pivoting(G, tol):
+    # columns taken in index order instead of largest remaining pivot first
+    s = G.shape[0]
+    diag = np.diag(G).copy()
+    usable = np.isfinite(diag) & (diag > 0)
+    d = np.zeros(s)
+    d[usable] = 1.0 / np.sqrt(diag[usable])
+    W = d[:, None] * G * d[None, :]
+    remaining = [j for j in range(s) if usable[j]]
+    kept, cols = [], []
+    while remaining:
+        piv = remaining[0]
+        w = W[piv, piv]
+        if not (w > tol):
+            break
+        col = np.zeros(s)
+        col[remaining] = W[remaining, piv] / np.sqrt(w)
+        rem = np.ix_(remaining, remaining)
+        W[rem] -= np.outer(col[remaining], col[remaining])
+        kept.append(piv)
+        cols.append(col)
+        remaining.remove(piv)
+    if not kept:
+        return [], np.zeros((0, 0)), d
+    return kept, np.stack(cols, axis=1)[kept, :], d
+
+
+def _mut_noise_wrong_word(seed, cells, M, amp):
+    # word index taken from the block number instead of the field
+    out = np.empty((M, len(cells)))
+    for i, a in enumerate(cells):
+        for g in range((M + 3) // 4):
+            w = orc.philox4x64_10((int(a), g, 0, 0), (seed, 0))
+            for j in range(4):
+                m = 4 * g + j
+                if m < M:
+                    out[m, i] = amp * (2.0 * ((w[g % 4] >> 11) * 2.0 ** -53) - 1.0)
+    return out
+
+
 def _mut_combine_no_transpose(U, C):
     return np.asarray(U, np.float64) @ np.asarray(C, np.float64)
 
@@ -144,6 +192,9 @@ MUTANTS = {
     "robin_held_as_adiabatic": ("_robin", _mut_robin_held_as_adiabatic),
     "rhs_bottom_layer": ("rhs", _mut_rhs_bottom_layer),
     "combine_no_transpose": ("combine", _mut_combine_no_transpose),
+    "rhs_no_area": ("rhs", _mut_rhs_no_area),
+    "cholesky_no_pivoting": ("scaled_pivoted_cholesky", _mut_cholesky_no_pivoting),
+    "noise_wrong_word": ("noise", _mut_noise_wrong_word),
     "rhs_volume_no_dz": ("rhs_volume", _mut_rhs_volume_no_dz),
     "rhs_volume_top_dz": ("rhs_volume", _mut_rhs_volume_top_dz),
     "rhs_volume_rows_flipped": ("rhs_volume", _mut_rhs_volume_rows_flipped),
