@@ -258,27 +258,53 @@ int blockoa_combine(blockoa_operator *op, const double *U, const double *C, void
                     int M, int dtype, blockoa_stream stream);
 
 /*
- * Options of blockoa_combine_ex: the noise term epsilon of Eq. 5 (Sec.
- * III-B).  With noise_amp > 0 every field value gets
- *   T[m][a] += noise_amp * (2 u - 1),  u = (w >> 11) * 2^-53 in [0, 1),
+ * Options of blockoa_combine_ex: the noise term epsilon and the normalised
+ * weights of Eq. 5 (Sec. III-B).
+ *
+ * Noise.  BLOCKOA_NOISE_UNIFORM with noise_amp > 0 adds to every field value
+ *   noise_amp * (2 u - 1),  u = (w >> 11) * 2^-53 in [0, 1),
  * w = word (m % 4) of Philox4x64-10 (Salmon et al., SC 2011) with counter
  * (a, m / 4, 0, 0) and key (noise_seed, 0), a the cell's index in the
  * operator's concatenated numbering: a uniform perturbation in
  * [-noise_amp, noise_amp) K that any kernel can reproduce.  MIXED (float32
  * fields) takes u from the top 24 bits of w, u = (w >> 40) * 2^-24, in
- * float32 (within noise_amp * 2^-23 of the float64 value).  The operator
- * action of the stored (noisy) T stays exact, so pairs (T, A T) remain
- * consistent.
+ * float32 (within noise_amp * 2^-23 of the float64 value).
+ * BLOCKOA_NOISE_GAUSSIAN adds zero-mean Gaussian noise of standard
+ * deviation noise_amp (the Gaussian noise of the noise study, Sec. V-D) by
+ * Box-Muller (1958): words w1 = 2 (m % 2) and w2 = 2 (m % 2) + 1 of
+ * Philox4x64-10 at counter (a, m / 2, 1, 0), key (noise_seed, 0), give
+ * u1 = ((w1 >> 11) + 1/2) 2^-53, u2 = (w2 >> 11) 2^-53 and
+ * epsilon = noise_amp sqrt(-2 ln u1) cos(2 pi u2); float32 fields evaluate
+ * it in float32 from u1, u2 rounded once to float32.
+ * Either way the operator action of the stored (noisy) T stays exact, so
+ * pairs (T, A T) remain consistent.
+ *
+ * Normalised weights.  normalize = 1 combines with Eq. 5's weights
+ * alpha_jm = C_jm / sum_i C_im (each field's weights sum to one), evaluated
+ * as (U C)_m / sum_i C_im, with noise (if any) added afterwards.  Fields are
+ * still excess temperatures: since the weights sum to one, the absolute
+ * field is t_ambient + T_m, which keeps every boundary condition of the
+ * basis (Robin ambient, held faces).  A field whose weights nearly cancel,
+ * |sum_i C_im| <= normalize_min * sum_i |C_im| (normalize_min <= 0: 1e-6),
+ * makes the call return ERR_INVALID (blockoa_last_error() says so); the
+ * check synchronises the stream.
  */
 typedef struct {
   uint64_t noise_seed;  /* Philox key word 0 */
-  double noise_amp;     /* K, >= 0; 0 = no noise */
+  double noise_amp;     /* K, >= 0; 0 = no noise (half-width, or standard deviation) */
+  int noise_kind;       /* BLOCKOA_NOISE_UNIFORM or BLOCKOA_NOISE_GAUSSIAN */
+  int normalize;        /* 0: weights C as given; 1: Eq. 5's normalised weights */
+  double normalize_min; /* guard on |sum_i C_im| / sum_i |C_im|; <= 0: 1e-6; < 1 */
 } blockoa_combine_opts;
 
+enum { BLOCKOA_NOISE_UNIFORM = 0, BLOCKOA_NOISE_GAUSSIAN = 1 };
+
 /*
- * blockoa_combine with options (NULL opts: no noise, same as
- * blockoa_combine).  Errors: as blockoa_combine, and ERR_INVALID for a
- * negative or non-finite noise_amp.
+ * blockoa_combine with options (NULL opts: no noise, weights as given, same
+ * as blockoa_combine).  Errors: as blockoa_combine, and ERR_INVALID for a
+ * negative or non-finite noise_amp, an unknown noise_kind or normalize
+ * value, normalize_min >= 1, or (normalize = 1) a field whose weights sum
+ * to ~0.
  */
 int blockoa_combine_ex(blockoa_operator *op, const double *U, const double *C, void *T, int s,
                        int M, int dtype, const blockoa_combine_opts *opts, blockoa_stream stream);
@@ -321,19 +347,25 @@ int blockoa_pair_check(const blockoa_operator *op, const void *T, const void *q,
 
 /*
  * blockoa_pair_check without any device allocation.  The paper has no
- * counterpart; this serves callers that cannot allocate during the call:
- * code running inside an open CUDA stream capture (a cudaMalloc would break
- * the capture), serving processes whose device memory is reserved up front
- * by their own pool, and fixed-budget deployments that forbid allocation
- * after start-up.  Same arguments, layout and result as blockoa_pair_check.
+ * counterpart.  blockoa_pair_check takes a small accumulator and a launch
+ * table from the library's device pool on every call; this variant is for
+ * callers that cannot allocate while they run: serving processes whose
+ * device memory is reserved up front by their own pool (a stray allocation
+ * competes with that budget and can fail or fragment it), deployments with
+ * a fixed memory budget that forbid allocation after start-up, and loops
+ * that must not stall on cudaMalloc / cudaFree, which can synchronise the
+ * device.  Same arguments, layout and result as blockoa_pair_check.
  * Its accumulators live in a fixed library-owned device array of
- * 2 * BLOCKOA_STATIC_PAIR_MAX float64 values (512 KB per GPU that loads the
- * library, held until the process exits); n_chips * M above
+ * 2 * BLOCKOA_STATIC_PAIR_MAX float64 values (512 KB on every GPU that
+ * loads the library, held until the process exits); n_chips * M above
  * BLOCKOA_STATIC_PAIR_MAX returns ERR_INVALID before anything is launched
- * (blockoa_last_error() says why).  The first call on a device looks up that
- * array's device address, so make it before any stream capture.  All calls
- * on a device share the array and each clears it on its stream first: calls
- * that overlap on the GPU race and must be serialised by the caller.
+ * (blockoa_last_error() says why).  The first call on a device looks up
+ * that array's device address (once per device, with that device
+ * current), so make the first call before any stream capture.  All calls
+ * on a device share the array, which keeps the last call's contents; each
+ * call clears it on its stream first, so calls that overlap on the GPU
+ * (different streams, or concurrent host threads) race and must be
+ * serialised by the caller.
  */
 int blockoa_pair_check_static(const blockoa_operator *op, const void *T, const void *q, int M,
                               int dtype, double *e_pair, blockoa_stream stream);

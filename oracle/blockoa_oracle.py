@@ -24,11 +24,14 @@ against the paper:
 * ``combine``       -- new temperature fields T = U C (Eq. 5 without the
                        normalisation and noise terms; unknowns are excess
                        temperature, so any C keeps the boundary conditions).
+* ``combine_normalized`` -- the same with Eq. 5's normalised weights
+                       alpha_im = mu_im / sum_j mu_jm (each field's weights
+                       sum to one).
 * ``noise``         -- the epsilon term of Eq. 5: uniform noise per cell and
                        field from ``philox4x64_10``, a counter-based generator
                        written from its published definition.
 * ``noise_gaussian``-- the Gaussian variant of that noise (Box-Muller from a
-                       second Philox stream); no library counterpart yet.
+                       second Philox stream).
 * ``apply_operator``-- operator action q = A T (Eq. 6, Sec. III-C).
 * ``pair_errors``   -- relative L2 errors of generated pairs.
 
@@ -269,6 +272,15 @@ def block_cg(A, B, X0=None, rtol=1e-12, maxiter=10000, deflate_tol=1e-14,
 def combine(U, C) -> np.ndarray:
     """T [M][n]: field m is sum_i C[i, m] U[:, i]."""
     return (np.asarray(U, np.float64) @ np.asarray(C, np.float64)).T.copy()
+
+
+def combine_normalized(U, C) -> np.ndarray:
+    """T [M][n] with the normalised weights of Eq. 5: for field m the weights
+    are alpha_im = C[i, m] / sum_j C[j, m], and field m is
+    sum_i alpha_im U[:, i]."""
+    C = np.asarray(C, np.float64)
+    alpha = C / C.sum(axis=0, keepdims=True)
+    return combine(U, alpha)
 
 
 # ---------------------------------------------------------------- noise (Eq. 5's epsilon)

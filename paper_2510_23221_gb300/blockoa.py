@@ -40,7 +40,11 @@ EXPORTED = (
     "blockoa_export_conductances", "blockoa_destroy", "blockoa_status_string",
     "blockoa_last_error", "blockoa_kernel_times", "blockoa_reset_kernel_times",
     "blockoa_launch_count", "blockoa_autotune", "blockoa_set_tuning", "blockoa_get_tuning",
+    "blockoa_pair_check_static",
 )
+
+# Largest n_chips * M accepted by blockoa_pair_check_static (its fixed device array).
+STATIC_PAIR_MAX = 32768
 
 
 class ChipDesc(ct.Structure):
@@ -56,7 +60,12 @@ class Tuning(ct.Structure):
 
 
 class CombineOpts(ct.Structure):
-    _fields_ = [("noise_seed", ct.c_uint64), ("noise_amp", ct.c_double)]
+    _fields_ = [("noise_seed", ct.c_uint64), ("noise_amp", ct.c_double), ("noise_kind", ct.c_int),
+                ("normalize", ct.c_int), ("normalize_min", ct.c_double)]
+
+
+NOISE_UNIFORM = 0
+NOISE_GAUSSIAN = 1
 
 
 class SolveOpts(ct.Structure):
@@ -108,6 +117,7 @@ def _lib():
         lib.blockoa_set_tuning.argtypes = [vp, ct.POINTER(Tuning)]
         lib.blockoa_get_tuning.argtypes = [vp, ct.POINTER(Tuning)]
         lib.blockoa_pair_check.argtypes = [vp, vp, vp, i, i, vp, vp]
+        lib.blockoa_pair_check_static.argtypes = [vp, vp, vp, i, i, vp, vp]
         lib.blockoa_export_conductances.argtypes = [vp, i, vp, vp, vp, vp]
         lib.blockoa_destroy.argtypes = [vp]
         lib.blockoa_destroy.restype = None
@@ -302,18 +312,23 @@ def block_solve(op: Operator, B, X, s: int, rtol: float = 1e-12, maxiter: int = 
 
 
 def combine(op: Operator, U, C, T, s: int, M: int, dtype: int, stream=None, noise_seed: int = 0,
-            noise_amp: float = 0.0):
+            noise_amp: float = 0.0, noise_kind: int = NOISE_UNIFORM, normalize: bool = False,
+            normalize_min: float = 0.0):
     """T = U C; with noise_amp > 0, plus the epsilon term of Eq. 5
-    (blockoa_combine_ex: uniform in [-noise_amp, noise_amp) K from Philox)."""
+    (blockoa_combine_ex: uniform in [-noise_amp, noise_amp) K, or Gaussian of
+    standard deviation noise_amp, from Philox); with normalize, Eq. 5's
+    weights C_jm / sum_i C_im."""
     import torch
     tdt = torch.float64 if dtype == FP64 else torch.float32
     pU = _ptr(U, torch.float64, "U", op.n_total * s)
     pC = _ptr(C, torch.float64, "C", op.n_chips * s * M)
     pT = _ptr(T, tdt, "T", op.n_total * M)
-    if noise_amp == 0.0:
+    if noise_amp == 0.0 and not normalize:
         _check(_lib().blockoa_combine(op.handle, pU, pC, pT, s, M, dtype, _stream(stream)), "combine")
         return
-    o = CombineOpts(noise_seed=int(noise_seed) & ((1 << 64) - 1), noise_amp=float(noise_amp))
+    o = CombineOpts(noise_seed=int(noise_seed) & ((1 << 64) - 1), noise_amp=float(noise_amp),
+                    noise_kind=int(noise_kind), normalize=int(bool(normalize)),
+                    normalize_min=float(normalize_min))
     _check(_lib().blockoa_combine_ex(op.handle, pU, pC, pT, s, M, dtype, ct.byref(o), _stream(stream)),
            "combine_ex")
 
@@ -341,6 +356,18 @@ def pair_check(op: Operator, T, q, M: int, dtype: int, e_pair, stream=None):
                                      _ptr(q, tdt, "q", op.n_total * M), M, dtype,
                                      _ptr(e_pair, torch.float64, "e_pair", op.n_chips * M), _stream(stream)),
            "pair_check")
+
+
+def pair_check_static(op: Operator, T, q, M: int, dtype: int, e_pair, stream=None):
+    """blockoa_pair_check without device allocation (its accumulators live in
+    a fixed library array; n_chips * M <= STATIC_PAIR_MAX)."""
+    import torch
+    tdt = torch.float64 if dtype == FP64 else torch.float32
+    _check(_lib().blockoa_pair_check_static(op.handle, _ptr(T, tdt, "T", op.n_total * M),
+                                            _ptr(q, tdt, "q", op.n_total * M), M, dtype,
+                                            _ptr(e_pair, torch.float64, "e_pair", op.n_chips * M),
+                                            _stream(stream)),
+           "pair_check_static")
 
 
 def export_conductances(op: Operator, chip: int):

@@ -25,7 +25,8 @@ template <typename T, int S>
 __global__ void __launch_bounds__(CT_CELLS)
 combine_simt_kernel(const CombTile *__restrict__ tiles, const ChipDev *__restrict__ chips,
                     const double *__restrict__ U, const double *__restrict__ C,
-                    T *__restrict__ Tout, int s, int M, const NoiseSpec nz) {
+                    T *__restrict__ Tout, int s, int M, const CombineEpi epi) {
+  const NoiseSpec &nz = epi.nz;
   __shared__ T sC[S][CT_FIELDS];
   const CombTile tile = tiles[blockIdx.x];
   const ChipDev ch = chips[tile.chip];
@@ -43,21 +44,48 @@ combine_simt_kernel(const CombTile *__restrict__ tiles, const ChipDev *__restric
 #pragma unroll
   for (int j = 0; j < S; ++j) u[j] = j < s ? (T)U[a * s + j] : T(0);
   T *out = Tout + ch.off * (long long)M + (a - ch.off);
+  const double *inv = epi.inv_sum ? epi.inv_sum + (long long)tile.chip * M + m0 : nullptr;
   for (int f0 = 0; f0 < nf; f0 += 4) {   // m0 is a multiple of 4: one noise block per 4 fields
     double eps[4] = {0.0, 0.0, 0.0, 0.0};
-    if (nz.amp > 0.0) noise4(nz, a, (m0 + f0) / 4, eps);
+    if (nz.amp > 0.0 && nz.kind == NOISE_UNIFORM) {
+      noise4(nz, a, (m0 + f0) / 4, eps);
+    } else if (nz.amp > 0.0) {   // Gaussian: two blocks of two fields
+      gauss2(nz, a, (m0 + f0) / 2, eps);
+      gauss2(nz, a, (m0 + f0) / 2 + 1, eps + 2);
+    }
     for (int f = f0; f < f0 + 4 && f < nf; ++f) {
       T acc = T(0);
 #pragma unroll
       for (int j = 0; j < S; ++j) acc += u[j] * sC[j][f];
+      if (inv) acc *= (T)inv[f];   // normalised weights of Eq. 5
       out[(long long)(m0 + f) * ch.n] = acc + (T)eps[f - f0];
     }
   }
 }
 
+// Normalised weights of Eq. 5, alpha_jm = C_jm / sum_i C_im, applied as
+// (U C)_m / sum_i C_im: inv[chip * M + m] = 1 / sum_i C_im (sum in float64,
+// i ascending).  A field whose |sum| <= min_rel * sum |C_im| sets *bad.
+__global__ void comb_inv_sum_kernel(const double *__restrict__ C, int n_chips, int s, int M,
+                                    double min_rel, double *__restrict__ inv, int *__restrict__ bad) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)n_chips * M) return;
+  const long long chip = i / M, m = i % M;
+  const double *c = C + chip * s * (long long)M + m;
+  double sum = 0.0, mag = 0.0;
+  for (int j = 0; j < s; ++j) {
+    const double v = c[(long long)j * M];
+    sum += v;
+    mag += fabs(v);
+  }
+  const bool ok = mag > 0.0 && fabs(sum) > min_rel * mag && isfinite(sum);
+  inv[i] = ok ? 1.0 / sum : 0.0;
+  if (!ok) atomicExch(bad, 1);
+}
+
 int launch_combine(blockoa_operator *op, const double *U, const double *C, void *Tout, int s, int M,
-                   int dtype, const NoiseSpec &nz, cudaStream_t st) {
-  if (dtype == BLOCKOA_MIXED) return launch_combine_tc(op, U, C, (float *)Tout, s, M, nz, st);
+                   int dtype, const CombineEpi &epi, cudaStream_t st) {
+  if (dtype == BLOCKOA_MIXED) return launch_combine_tc(op, U, C, (float *)Tout, s, M, epi, st);
   std::vector<CombTile> tiles;
   for (int c = 0; c < op->n_chips; ++c)
     for (long long b = 0; b < op->chips[c].n; b += CT_CELLS)
@@ -72,7 +100,7 @@ int launch_combine(blockoa_operator *op, const double *U, const double *C, void 
     const CombTile *dt = (const CombTile *)d_tiles;
     const int S = s <= 8 ? 8 : s <= 16 ? 16 : s <= 32 ? 32 : 64;
 #define BLOCKOA_COMB(TT, SS) \
-  combine_simt_kernel<TT, SS><<<grid, CT_CELLS, 0, st>>>(dt, op->d_chips, U, C, (TT *)Tout, s, M, nz)
+  combine_simt_kernel<TT, SS><<<grid, CT_CELLS, 0, st>>>(dt, op->d_chips, U, C, (TT *)Tout, s, M, epi)
     cudaEvent_t ev;
     time_begin(op, st, &ev);
     g_launches += 1;
@@ -100,16 +128,53 @@ extern "C" int blockoa_combine_ex(blockoa_operator *op, const double *U, const d
                                   int s, int M, int dtype, const blockoa_combine_opts *opts,
                                   blockoa_stream stream) {
   if (!op || s < 1 || s > 64 || M < 0 || !valid_dtype(dtype)) return BLOCKOA_ERR_INVALID;
-  NoiseSpec nz;
+  CombineEpi epi;
+  bool normalize = false;
+  double min_rel = 1e-6;
   if (opts) {
     if (!(opts->noise_amp >= 0.0) || !std::isfinite(opts->noise_amp)) return BLOCKOA_ERR_INVALID;
-    nz.seed = (unsigned long long)opts->noise_seed;
-    nz.amp = opts->noise_amp;
+    if (opts->noise_kind != BLOCKOA_NOISE_UNIFORM && opts->noise_kind != BLOCKOA_NOISE_GAUSSIAN)
+      return BLOCKOA_ERR_INVALID;
+    if (opts->normalize != 0 && opts->normalize != 1) return BLOCKOA_ERR_INVALID;
+    if (!std::isfinite(opts->normalize_min) || opts->normalize_min >= 1.0) return BLOCKOA_ERR_INVALID;
+    epi.nz.seed = (unsigned long long)opts->noise_seed;
+    epi.nz.amp = opts->noise_amp;
+    epi.nz.kind = opts->noise_kind;
+    normalize = opts->normalize == 1;
+    if (opts->normalize_min > 0.0) min_rel = opts->normalize_min;
   }
   if (M == 0) return BLOCKOA_OK;
   if (!U || !C || !T) return BLOCKOA_ERR_INVALID;
   if (dtype == BLOCKOA_FP64 && (M + CT_FIELDS - 1) / CT_FIELDS > 65535) return BLOCKOA_ERR_INVALID;
-  return launch_combine(op, U, C, T, s, M, dtype, nz, (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!normalize) return launch_combine(op, U, C, T, s, M, dtype, epi, st);
+  // the weights' column sums first; a field whose sum is ~0 fails the call
+  const long long np = (long long)op->n_chips * M;
+  void *inv = nullptr, *bad = nullptr;
+  int rc = pool_alloc(op, &inv, sizeof(double) * (size_t)np, st);
+  if (!rc) rc = pool_alloc(op, &bad, 8, st);
+  auto done = [&](int code) { pool_free(inv, st); pool_free(bad, st); return code; };
+  if (rc) return done(rc);
+  cudaError_t e = cudaMemsetAsync(bad, 0, 8, st);
+  if (e == cudaSuccess) {
+    g_launches += 1;
+    comb_inv_sum_kernel<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(C, op->n_chips, s, M, min_rel,
+                                                                      (double *)inv, (int *)bad);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    op->h_flag[0] = 0;
+    e = read_small(op->h_flag, bad, 8, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return done(cuda_status(e, "combine: normalised weights"));
+  if (op->h_flag[0]) {
+    set_last_error(cudaErrorInvalidValue,
+                   "blockoa_combine_ex: a field's coefficients sum to ~0 (normalize_min)");
+    return done(BLOCKOA_ERR_INVALID);
+  }
+  epi.inv_sum = (const double *)inv;
+  return done(launch_combine(op, U, C, T, s, M, dtype, epi, st));
 }
 
 extern "C" int blockoa_combine(blockoa_operator *op, const double *U, const double *C, void *T,

@@ -116,7 +116,8 @@ __global__ void __launch_bounds__(TC_THREADS)
 combine_tc_kernel(const TcTile *__restrict__ tiles, const ChipDev *__restrict__ chips,
                   const __nv_bfloat16 *__restrict__ uimg, const __nv_bfloat16 *__restrict__ cimg,
                   float *__restrict__ Tout, int M, int Kdim, int n_chunks, int *__restrict__ err,
-                  const NoiseSpec nz) {
+                  const CombineEpi epi) {
+  const NoiseSpec &nz = epi.nz;
   extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t a_bytes = TC_M * Kdim * 2, b_bytes = TC_N * Kdim * 2;
   unsigned char *sA = smem;
@@ -194,13 +195,27 @@ combine_tc_kernel(const TcTile *__restrict__ tiles, const ChipDev *__restrict__ 
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       const int fb = f0 + cc * 32;
       if (valid) {
-        if (nz.amp > 0.0) {   // epsilon of Eq. 5, 4 fields per generator block (fb is a multiple of 32)
+        if (epi.inv_sum) {   // normalised weights of Eq. 5: (U C)_m / sum_j C_jm
+          const double *inv = epi.inv_sum + (long long)tile.chip * M + fb;
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (fb + i < M) r[i] = __float_as_uint(__uint_as_float(r[i]) * (float)__ldg(inv + i));
+        }
+        if (nz.amp > 0.0 && nz.kind == NOISE_UNIFORM) {   // epsilon of Eq. 5, 4 fields per block (fb % 32 == 0)
 #pragma unroll   // constant indices keep r[] in registers
           for (int g = 0; g < 8; ++g) {
             float eps[4];
             noise4f(nz, tile.cell0 + cell, (fb + 4 * g) / 4, eps);
 #pragma unroll
             for (int i = 0; i < 4; ++i) r[4 * g + i] = __float_as_uint(__uint_as_float(r[4 * g + i]) + eps[i]);
+          }
+        } else if (nz.amp > 0.0) {   // Gaussian epsilon, 2 fields per generator block
+#pragma unroll
+          for (int g = 0; g < 16; ++g) {
+            float eps[2];
+            gauss2f(nz, tile.cell0 + cell, (fb + 2 * g) / 2, eps);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) r[2 * g + i] = __float_as_uint(__uint_as_float(r[2 * g + i]) + eps[i]);
           }
         }
 #pragma unroll
@@ -223,7 +238,7 @@ combine_tc_kernel(const TcTile *__restrict__ tiles, const ChipDev *__restrict__ 
 }
 
 int launch_combine_tc(blockoa_operator *op, const double *U, const double *C, float *Tout, int s,
-                      int M, const NoiseSpec &nz, cudaStream_t st) {
+                      int M, const CombineEpi &epi, cudaStream_t st) {
   const int Sp = tc_kpad(s), K = 3 * Sp;
   const int n_chunks = (M + TC_N - 1) / TC_N;
   std::vector<TcTile> tiles;
@@ -269,7 +284,7 @@ int launch_combine_tc(blockoa_operator *op, const double *U, const double *C, fl
     time_begin(op, st, &ev1);
     combine_tc_kernel<<<(unsigned)tiles.size(), TC_THREADS, smem, st>>>(
         (const TcTile *)d_tiles, op->d_chips, (const __nv_bfloat16 *)uimg,
-        (const __nv_bfloat16 *)cimg, Tout, M, K, n_chunks, (int *)err, nz);
+        (const __nv_bfloat16 *)cimg, Tout, M, K, n_chunks, (int *)err, epi);
     e = cudaGetLastError();
     time_end(op, st, KC_COMBINE_TC, ev1);
   }

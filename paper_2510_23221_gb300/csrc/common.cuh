@@ -179,14 +179,14 @@ int launch_apply_block64(const blockoa_operator *op, const double *U, double *AU
 // blockcg.cu
 void free_solve_ws(void *ws);
 
-struct NoiseSpec;   // noise.cuh
+struct CombineEpi;   // noise.cuh
 
 // combine_tc.cu (bfloat16x3 on tcgen05; fields in float32)
 int launch_combine_tc(blockoa_operator *op, const double *U, const double *C, float *T, int s,
-                      int M, const NoiseSpec &nz, cudaStream_t st);
+                      int M, const CombineEpi &epi, cudaStream_t st);
 
 // combine.cu
 int launch_combine(blockoa_operator *op, const double *U, const double *C, void *T, int s, int M,
-                   int dtype, const NoiseSpec &nz, cudaStream_t st);
+                   int dtype, const CombineEpi &epi, cudaStream_t st);
 
 }  // namespace blockoa

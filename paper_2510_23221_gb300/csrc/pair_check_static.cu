@@ -2,11 +2,11 @@
 // paper): the same float64 check as blockoa_pair_check, for callers that
 // must not allocate device memory during the call.
 //
-// Who needs it: code that runs while a CUDA stream capture is open (a
-// cudaMalloc inside a capture breaks it), serving processes whose memory is
-// reserved up front by their own pool (a stray cudaMalloc competes with that
-// budget and can fail or fragment it), and fixed-budget deployments that
-// forbid allocation after start-up.  blockoa_pair_check allocates a small
+// Who needs it: serving processes whose device memory is reserved up front
+// by their own pool (a stray cudaMalloc competes with that budget and can
+// fail or fragment it), fixed-budget deployments that forbid allocation
+// after start-up, and loops that must not stall on cudaMalloc / cudaFree,
+// which can synchronise the device.  blockoa_pair_check allocates a small
 // accumulator and a launch table from the library's stream-ordered pool on
 // every call; this variant uses a fixed file-scope device array instead.
 //

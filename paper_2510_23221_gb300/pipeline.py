@@ -13,6 +13,15 @@ import numpy as np
 
 from . import blockoa as bo
 
+# Solve options of the chosen form on the 128x128x8 benchmark chip: mixed
+# precision (float32 block CG inside float64 refinement), two-step z-line
+# preconditioning, the first float32 pass asked for a 1e-3 residual
+# reduction (later passes only for what the target still needs), a
+# convergence poll every 16 iterations, and the s x s Gram systems factored
+# by float64 pivoted Cholesky.
+CHOSEN_SOLVE = dict(precision=bo.MIXED, precond=bo.PRECOND_ZLINE2, inner_rtol=1e-3,
+                    check_every=16, small_solve=bo.SMALL_FP64_CHOLESKY)
+
 
 @dataclass
 class DeviceInputs:

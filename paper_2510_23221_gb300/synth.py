@@ -197,10 +197,13 @@ def single_chip_workload(nx=128, ny=128, n_layers=8, s=32, M=5000,
 
 
 def batched_workload(n_chips: int = 256, s: int = 16, M: int = 20,
-                     sides=(64, 96, 128, 192, 256), cfg=3, rtol=1e-6) -> Workload:
-    """Uneven chips: square side from ``sides``, 4-12 layers, h in [1e3, 1e5]."""
+                     sides=(64, 96, 128, 192, 256), cfg=3, rtol=1e-6, which=None) -> Workload:
+    """Uneven chips: square side from ``sides``, 4-12 layers, h in [1e3, 1e5].
+
+    Chip j draws from its own seed, so ``which`` (a list of chip indices)
+    selects exactly those chips of the n_chips-chip batch."""
     chips, dens, Cs = [], [], []
-    for j in range(n_chips):
+    for j in (range(n_chips) if which is None else which):
         rng = np.random.default_rng(1_000_000 * cfg + j)
         side = int(rng.choice(np.asarray(sides)))
         nl = int(rng.integers(4, 13))
@@ -209,7 +212,8 @@ def batched_workload(n_chips: int = 256, s: int = 16, M: int = 20,
         chips.append(chip)
         dens.append(power_maps(rng, side, side, s, mix=True))
         Cs.append(coefficients(rng, s, M))
-    return Workload(f"batch{n_chips}_s{s}_M{M}", chips, dens, Cs, s=s, M=M, rtol=rtol)
+    name = f"batch{n_chips}_s{s}_M{M}" if which is None else f"batch{n_chips}_subset{len(chips)}_s{s}_M{M}"
+    return Workload(name, chips, dens, Cs, s=s, M=M, rtol=rtol)
 
 
 FNO_TRAIN_SEED0 = 10_000_000      # training chips of the warm-start network

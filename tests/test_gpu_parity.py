@@ -240,6 +240,78 @@ def test_combine_with_noise(precision):
                    T, s, M, precision, noise_seed=seed, noise_amp=-1.0)
 
 
+@pytest.mark.parametrize("precision", [bo.FP64, bo.MIXED])
+def test_gaussian_noise_matches_oracle(precision):
+    """The Gaussian epsilon (Sec. V-D's noise study) against the oracle's
+    noise_gaussian: with a zero basis the fields are the noise itself, so the
+    two are compared element by element (float64: a few roundings of
+    sigma-sized numbers; float32: evaluated in float32 from u1, u2 rounded
+    once, |eps| <= 8.6 sigma, so within 1e-5 sigma); with a random basis the
+    noisy field against U C + epsilon at the combination's own tolerance."""
+    chips = [synth.random_small_chip(17, 19, 11, 3), synth.random_small_chip(18, 7, 13, 2)]
+    s, M, seed, sigma = 8, 41, 4242, 0.05
+    rng = np.random.default_rng(16)
+    op = bo.assemble(chips)
+    fdt = torch.float64 if precision == bo.FP64 else torch.float32
+    Cs = [synth.coefficients(rng, s, M) for _ in chips]
+    Cd = cuda(np.concatenate([c.ravel() for c in Cs]))
+    T = torch.empty(M * op.n_total, dtype=fdt, device="cuda")
+    bo.combine(op, torch.zeros(op.n_total * s, dtype=torch.float64, device="cuda"), Cd, T, s, M, precision,
+               noise_seed=seed, noise_amp=sigma, noise_kind=bo.NOISE_GAUSSIAN)
+    Th = T.cpu().numpy().astype(np.float64)
+    atol = 1e-13 * sigma if precision == bo.FP64 else 1e-5 * sigma
+    for c, chip in enumerate(chips):
+        off = op.sizes[c]["off"]
+        ref = orc.noise_gaussian(seed, np.arange(off, off + chip.n), M, sigma)
+        got = Th[off * M:(off + chip.n) * M].reshape(M, chip.n)
+        assert np.max(np.abs(got - ref)) <= atol, np.max(np.abs(got - ref))
+    Us = [rng.standard_normal((c.n, s)) for c in chips]
+    bo.combine(op, cuda(np.concatenate([u.ravel() for u in Us])), Cd, T, s, M, precision,
+               noise_seed=seed, noise_amp=sigma, noise_kind=bo.NOISE_GAUSSIAN)
+    Th = T.cpu().numpy().astype(np.float64)
+    tol = 1e-14 if precision == bo.FP64 else 1e-6
+    for c, chip in enumerate(chips):
+        off = op.sizes[c]["off"]
+        ref = orc.combine(Us[c], Cs[c]) + orc.noise_gaussian(seed, np.arange(off, off + chip.n), M, sigma)
+        got = Th[off * M:(off + chip.n) * M].reshape(M, chip.n)
+        assert np.all(relcols(got, ref, axis=1) < tol)
+
+
+@pytest.mark.parametrize("precision", [bo.FP64, bo.MIXED])
+def test_normalised_weights_match_oracle(precision):
+    """Eq. 5's normalised weights alpha_im = C_im / sum_j C_jm against the
+    oracle's combine_normalized (with and without uniform noise added
+    afterwards), and the guard on weights that sum to ~0."""
+    chips = [synth.random_small_chip(27, 23, 9, 3), synth.random_small_chip(28, 8, 8, 4)]
+    s, M = 12, 300
+    rng = np.random.default_rng(26)
+    op = bo.assemble(chips)
+    fdt = torch.float64 if precision == bo.FP64 else torch.float32
+    Us = [rng.standard_normal((c.n, s)) for c in chips]
+    Cs = [synth.coefficients(rng, s, M) + 0.0 for _ in chips]
+    Ud = cuda(np.concatenate([u.ravel() for u in Us]))
+    Cd = cuda(np.concatenate([c.ravel() for c in Cs]))
+    T = torch.empty(M * op.n_total, dtype=fdt, device="cuda")
+    tol = 1e-13 if precision == bo.FP64 else 2e-6
+    for amp in (0.0, 0.01):
+        bo.combine(op, Ud, Cd, T, s, M, precision, normalize=True, noise_seed=9, noise_amp=amp)
+        Th = T.cpu().numpy().astype(np.float64)
+        for c, chip in enumerate(chips):
+            off = op.sizes[c]["off"]
+            ref = orc.combine_normalized(Us[c], Cs[c])
+            if amp:
+                ref = ref + orc.noise(9, np.arange(off, off + chip.n), M, amp)
+            got = Th[off * M:(off + chip.n) * M].reshape(M, chip.n)
+            assert np.all(relcols(got, ref, axis=1) < tol), relcols(got, ref, axis=1).max()
+    # a field whose weights cancel exactly is refused
+    Cbad = [c.copy() for c in Cs]
+    Cbad[1][:, 7] = 0.0
+    Cbad[1][0, 7], Cbad[1][1, 7] = 1.5, -1.5
+    with pytest.raises(bo.BlockoaError) as ei:
+        bo.combine(op, Ud, cuda(np.concatenate([c.ravel() for c in Cbad])), T, s, M, precision, normalize=True)
+    assert ei.value.code == bo.ERR_INVALID
+
+
 def test_apply_basis_rejects_bad_arguments():
     op = bo.assemble([synth.random_small_chip(8, 5, 4, 2)])
     with pytest.raises(bo.BlockoaError):

@@ -36,6 +36,7 @@ def _run_pins():
         ("pivoted_cholesky", pins.test_pivoted_cholesky_against_library),
         ("philox", pins.test_philox_matches_library_generator),
         ("noise", pins.test_noise_is_uniform_bounded_and_reproducible),
+        ("normalised_weights", pins.test_normalised_weights_of_eq5),
     ]
     for chip in pins._chips():
         checks.append(("spd", lambda c=chip: pins.test_operator_symmetric_bitwise_and_spd(c)))
@@ -51,7 +52,7 @@ def _run_pins():
 
 REAL = {name: getattr(orc, name) for name in
         ("rhs", "rhs_volume", "block_cg", "face_conductances", "_gram_solve", "_series",
-         "scaled_pivoted_cholesky", "noise")}
+         "scaled_pivoted_cholesky", "noise", "combine_normalized")}
 REAL_ROBIN = orc._robin
 
 
@@ -148,6 +149,18 @@ def _mut_noise_wrong_word(seed, cells, M, amp):
     return out
 
 
+def _mut_normalize_by_basis_sums(U, C):
+    # weights divided by the sums over fields (the wrong axis)
+    C = np.asarray(C, np.float64)
+    return orc.combine(U, C / C.sum(axis=1, keepdims=True))
+
+
+def _mut_normalize_by_magnitude(U, C):
+    # weights divided by sum |mu| instead of sum mu
+    C = np.asarray(C, np.float64)
+    return orc.combine(U, C / np.abs(C).sum(axis=0, keepdims=True))
+
+
 def _mut_combine_no_transpose(U, C):
     return np.asarray(U, np.float64) @ np.asarray(C, np.float64)
 
@@ -201,6 +214,8 @@ MUTANTS = {
     "beta_sign": ("block_cg", _make_bcg_mutant("beta_sign")),
     "alpha_scale": ("block_cg", _make_bcg_mutant("alpha_scale")),
     "gz_wrong_index": ("face_conductances", _mut_gz_wrong_index),
+    "normalize_by_basis_sums": ("combine_normalized", _mut_normalize_by_basis_sums),
+    "normalize_by_magnitude": ("combine_normalized", _mut_normalize_by_magnitude),
 }
 
 

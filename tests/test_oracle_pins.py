@@ -449,6 +449,29 @@ def test_gaussian_noise_is_normal_reproducible_and_apart_from_the_uniform_stream
     assert e[11, 3] == sigma * np.sqrt(-2 * np.log(u1)) * np.cos(2 * np.pi * u2)
 
 
+def test_normalised_weights_of_eq5():
+    """Eq. 5's weights sum to one per field: (i) a basis whose columns are all
+    the same field v combines to v for every field, whatever the
+    coefficients (a normalisation by the wrong axis or by sum |mu| breaks
+    this); (ii) scaling one field's coefficients leaves that field -- and
+    every other field -- unchanged; (iii) weights that already sum to one
+    give the plain combination."""
+    rng = np.random.default_rng(12)
+    n, s, M = 40, 6, 9
+    v = rng.standard_normal(n)
+    C = rng.standard_normal((s, M)) + 0.3
+    T = orc.combine_normalized(np.repeat(v[:, None], s, axis=1), C)
+    assert np.allclose(T, np.broadcast_to(v, (M, n)), rtol=1e-12, atol=1e-12)
+    U = rng.standard_normal((n, s))
+    T0 = orc.combine_normalized(U, C)
+    C2 = C.copy()
+    C2[:, 4] *= -3.5
+    assert np.allclose(orc.combine_normalized(U, C2), T0, rtol=1e-12, atol=1e-12)
+    A = C / C.sum(axis=0, keepdims=True)
+    assert np.allclose(orc.combine_normalized(U, A), orc.combine(U, A), rtol=1e-12, atol=1e-12)
+    assert not np.allclose(T0, orc.combine(U, C))
+
+
 def test_bf16_rounding_matches_torch():
     x = np.random.default_rng(5).standard_normal(4096)
     ours = synth.round_to_bf16(x)

@@ -1,10 +1,13 @@
 """The allocation-free pair check agrees with the allocating one.
 
 blockoa_pair_check_static is for callers that cannot allocate device memory
-during a call (inside an open stream capture, or under a memory budget
-reserved up front).  It keeps its accumulators in a fixed device array
+while they run (memory reserved up front by their own pool, a fixed budget
+that forbids allocation after start-up, or a loop that must not stall on
+cudaMalloc / cudaFree).  It keeps its accumulators in a fixed device array
 shared by all calls, so two calls in a row must both give the same result
-as blockoa_pair_check: the second call proves the array is cleared.
+as blockoa_pair_check: the second call proves the array is cleared.  After
+a first call (which looks up the array's address and loads the kernels),
+the device's free memory must not shrink across further calls.
 """
 import ctypes as ct
 
@@ -50,12 +53,18 @@ def test_static_pair_check_matches_allocating_check_twice(dtype):
     expect = ref.cpu().numpy()
     assert np.all(expect > 1e-8)
     stream = torch.cuda.current_stream().cuda_stream
+    first = torch.full_like(ref, float("nan"))
+    assert fn(op.handle, T.data_ptr(), q.data_ptr(), M, dtype, first.data_ptr(), stream) == bo.OK
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
     for _ in range(2):
         out = torch.full_like(ref, float("nan"))
         rc = fn(op.handle, T.data_ptr(), q.data_ptr(), M, dtype, out.data_ptr(), stream)
         assert rc == bo.OK, bo.status_string(rc)
         torch.cuda.synchronize()
         np.testing.assert_allclose(out.cpu().numpy(), expect, rtol=1e-12, atol=0)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free_before
 
 
 def test_static_pair_check_rejects_sizes_beyond_its_array():
