@@ -215,6 +215,19 @@ int blockoa_block_solve(blockoa_operator *op, const double *B, double *X, int s,
                         blockoa_stream stream);
 
 /*
+ * Test support (no counterpart in the paper): arm a one-shot injection for
+ * the next blockoa_block_solve on this operator.  Before the convergence
+ * poll number after_polls (0 = before the first block of iterations) of
+ * the first inner solve, chip `chip`'s device state is overwritten with
+ * `status` and marked inactive -- the state a bounded device-side wait
+ * leaves when it gives up (status ERR_TIMEOUT) -- so that the propagation
+ * of such a status can be exercised without faulting or hanging a GPU.
+ * The other chips are unaffected.  Errors: ERR_INVALID (chip out of range,
+ * status not an error code, negative after_polls).
+ */
+int blockoa_inject_chip_status(blockoa_operator *op, int chip, int status, int after_polls);
+
+/*
  * Launch tuning of the batched block-CG loop (the persistent launches of
  * blockoa_block_solve): work units are tiles_per_unit block tiles of one
  * chip for the loop kernels, and ztiles_per_unit column tiles for the
@@ -323,6 +336,19 @@ int blockoa_combine_ex(blockoa_operator *op, const double *U, const double *C, v
  */
 int blockoa_apply_basis(const blockoa_operator *op, const double *U, double *AU, int s,
                         blockoa_stream stream);
+
+/*
+ * Relative residual of a candidate solution of A X = B, per chip and column:
+ * ratio[c * s + j] = ||B_j - A_c X_j|| / ||B_j|| (float64 operator action in
+ * difference form, float64 sums; 0 for a zero column of B with a zero
+ * residual, +inf for a zero column with a nonzero residual).  This is the
+ * learned warm start's fallback test: block CG starts from X only if every
+ * ratio of the chip is below the threshold.  B, X: device float64
+ * [n_total][s]; ratio: device float64 [n_chips * s].  1 <= s <= 64.
+ * Errors: ERR_INVALID (NULL pointers, s out of range), ERR_OOM, ERR_CUDA.
+ */
+int blockoa_residual_ratio(const blockoa_operator *op, const double *B, const double *X, int s,
+                           double *ratio, blockoa_stream stream);
 
 /*
  * Operator action q = A T (Eq. 6, Sec. III-C) on M fields of every chip.
@@ -474,6 +500,18 @@ int blockoa_fno_zero_grad(blockoa_fno *net, blockoa_stream stream);
  * parameters from the accumulated gradients; refreshes the bfloat16 copies. */
 int blockoa_fno_adam_step(blockoa_fno *net, float lr, float beta1, float beta2, float eps, int t,
                           blockoa_stream stream);
+
+/*
+ * The warm start's basis from network outputs: sample j of chip c of `op`
+ * (y: device float32 [chip][s][n_c], i.e. y[off_c * s + j * n_c + a], the
+ * layout of blockoa_fno_forward's output for the s samples of each chip)
+ * times scale[c * s + j] (device float64 [n_chips * s]: the sample's input
+ * normalisation undone) into X[(off_c + a) * s + j] (device float64
+ * [n_total][s], the layout of blockoa_solve_opts.x0).
+ * Errors: ERR_INVALID (NULL pointers, s < 1), ERR_OOM, ERR_CUDA.
+ */
+int blockoa_fno_basis(const blockoa_operator *op, const float *y, const double *scale, int s, double *X,
+                      blockoa_stream stream);
 
 /* Copy the float32 parameters or gradients to a host array.  Synchronous. */
 int blockoa_fno_get_params(const blockoa_fno *net, float *params);

@@ -40,7 +40,7 @@ EXPORTED = (
     "blockoa_export_conductances", "blockoa_destroy", "blockoa_status_string",
     "blockoa_last_error", "blockoa_kernel_times", "blockoa_reset_kernel_times",
     "blockoa_launch_count", "blockoa_autotune", "blockoa_set_tuning", "blockoa_get_tuning",
-    "blockoa_pair_check_static",
+    "blockoa_pair_check_static", "blockoa_residual_ratio", "blockoa_inject_chip_status",
 )
 
 # Largest n_chips * M accepted by blockoa_pair_check_static (its fixed device array).
@@ -118,6 +118,8 @@ def _lib():
         lib.blockoa_get_tuning.argtypes = [vp, ct.POINTER(Tuning)]
         lib.blockoa_pair_check.argtypes = [vp, vp, vp, i, i, vp, vp]
         lib.blockoa_pair_check_static.argtypes = [vp, vp, vp, i, i, vp, vp]
+        lib.blockoa_residual_ratio.argtypes = [vp, vp, vp, i, vp, vp]
+        lib.blockoa_inject_chip_status.argtypes = [vp, i, i, i]
         lib.blockoa_export_conductances.argtypes = [vp, i, vp, vp, vp, vp]
         lib.blockoa_destroy.argtypes = [vp]
         lib.blockoa_destroy.restype = None
@@ -356,6 +358,22 @@ def pair_check(op: Operator, T, q, M: int, dtype: int, e_pair, stream=None):
                                      _ptr(q, tdt, "q", op.n_total * M), M, dtype,
                                      _ptr(e_pair, torch.float64, "e_pair", op.n_chips * M), _stream(stream)),
            "pair_check")
+
+
+def inject_chip_status(op: Operator, chip: int, status: int, after_polls: int = 1):
+    """Test support: the next solve finds chip `chip` with `status` (inactive)
+    before poll `after_polls` (blockoa_inject_chip_status)."""
+    _check(_lib().blockoa_inject_chip_status(op.handle, chip, status, after_polls), "inject_chip_status")
+
+
+def residual_ratio(op: Operator, B, X, s: int, ratio, stream=None):
+    """ratio[c * s + j] = ||B_j - A X_j|| / ||B_j|| per chip and column
+    (blockoa_residual_ratio, float64)."""
+    import torch
+    _check(_lib().blockoa_residual_ratio(op.handle, _ptr(B, torch.float64, "B", op.n_total * s),
+                                         _ptr(X, torch.float64, "X", op.n_total * s), s,
+                                         _ptr(ratio, torch.float64, "ratio", op.n_chips * s), _stream(stream)),
+           "residual_ratio")
 
 
 def pair_check_static(op: Operator, T, q, M: int, dtype: int, e_pair, stream=None):

@@ -1651,7 +1651,7 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
   launched();
   if constexpr (CH) {
     mark();
-    launch_chained(chol_alpha_kernel<T, S>, ws->n_chips * S, 256, chol_smem_bytes<S>(), st, chain, sa);
+    launch_chained(chol_alpha_kernel<T, S>, ws->n_chips * S, kCholThreads, chol_smem_bytes<S>(), st, chain, sa);
     launched();
   }
   mark();
@@ -1676,7 +1676,7 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
   launched();
   if constexpr (CH) {
     mark();
-    launch_chained(chol_beta_kernel<T, S>, ws->n_chips * S, 32, 0, st, chain, sa);
+    launch_chained(chol_beta_kernel<T, S>, ws->n_chips * S, kCholThreads, 0, st, chain, sa);
     launched();
   }
   mark();
@@ -2033,7 +2033,18 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     }
     BLOCKOA_CUDA(cudaGetLastError());
     // Inner block-CG iterations, polled every `check_every` iterations.
-    for (;;) {
+    for (int poll = 0;; ++poll) {
+      if (op->inject_chip >= 0 && op->inject_chip < nc && poll == op->inject_after) {
+        // test support: the chip's device state as a device-side wait that
+        // gave up would leave it (status set, chip inactive), between polls
+        ChipSolveState &cs = ws->h_state[op->inject_chip];
+        memset(&cs, 0, sizeof(cs));
+        cs.status = op->inject_status;
+        cs.active = 0;
+        BLOCKOA_CUDA(cudaMemcpyAsync(ws->state + op->inject_chip, &cs, sizeof(cs), cudaMemcpyHostToDevice, st));
+        BLOCKOA_CUDA(cudaStreamSynchronize(st));
+        op->inject_chip = -1;
+      }
       g_launches += (long long)loop_kernels(ch, pc) * check_every;
       for (int i = 0; i < loop_kernels(ch, pc); ++i) add_launches(op, loop_class(ch, pc, i), check_every);
       BLOCKOA_CUDA(cudaGraphLaunch(ws->graph, st));
@@ -2122,6 +2133,16 @@ extern "C" int blockoa_block_solve(blockoa_operator *op, const double *B, double
   }
 }
 
+
+extern "C" int blockoa_inject_chip_status(blockoa_operator *op, int chip, int status, int after_polls) {
+  if (!op || chip < 0 || chip >= op->n_chips || after_polls < 0 || status <= BLOCKOA_OK ||
+      status > BLOCKOA_ERR_OOM)
+    return BLOCKOA_ERR_INVALID;
+  op->inject_chip = chip;
+  op->inject_status = status;
+  op->inject_after = after_polls;
+  return BLOCKOA_OK;
+}
 
 // ---------------------------------------------------------------- autotuning
 namespace blockoa {

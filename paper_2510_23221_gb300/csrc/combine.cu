@@ -188,6 +188,12 @@ extern "C" int blockoa_apply_basis(const blockoa_operator *op, const double *U, 
   return launch_apply_block64(op, U, AU, s, (cudaStream_t)stream);
 }
 
+extern "C" int blockoa_residual_ratio(const blockoa_operator *op, const double *B, const double *X, int s,
+                                      double *ratio, blockoa_stream stream) {
+  if (!op || s < 1 || s > 64 || !B || !X || !ratio) return BLOCKOA_ERR_INVALID;
+  return launch_residual_ratio(op, B, X, s, ratio, (cudaStream_t)stream);
+}
+
 extern "C" int blockoa_apply_operator(const blockoa_operator *op, const void *T, void *q, int M,
                                       int dtype, blockoa_stream stream) {
   if (!op || M < 0 || !valid_dtype(dtype)) return BLOCKOA_ERR_INVALID;

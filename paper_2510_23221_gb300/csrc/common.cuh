@@ -126,6 +126,8 @@ struct blockoa_operator {
   int *h_flag = nullptr;                 // pinned status word for small device -> host reads
   int tune_tpu = 0;                      // block-CG unit size in tiles (0: from the tile count)
   int tune_ztpu = 0;                     // z-line unit size in column tiles (0: from the tile count)
+  // one-shot status injection for tests (blockoa_inject_chip_status)
+  int inject_chip = -1, inject_status = 0, inject_after = 0;
 };
 
 namespace blockoa {
@@ -173,6 +175,9 @@ int launch_pair_check(const blockoa_operator *op, const void *T, const void *q, 
 // per-chip column norms ||R_j||^2 into rn2 [chip][S] (must be zeroed).
 int launch_residual64(const blockoa_operator *op, const double *B, const double *X, double *R,
                       int S, double *rn2, cudaStream_t st);
+// ratio[chip][j] = ||B_j - A X_j|| / ||B_j|| for float64 blocks [n_total][s], s <= 64.
+int launch_residual_ratio(const blockoa_operator *op, const double *B, const double *X, int s,
+                          double *ratio, cudaStream_t st);
 // AU = A U, float64 block of s columns [n][s] (blockoa_apply_basis).
 int launch_apply_block64(const blockoa_operator *op, const double *U, double *AU, int s, cudaStream_t st);
 

@@ -443,10 +443,46 @@ void pw_grad(blockoa_fno *net, const float *x, const float *dy, long long rows, 
   g_launches += 1;
 }
 
+// Prediction of the basis from the network's per-sample outputs: sample j
+// of chip c, y[off_c * s + j * n_c + a], scaled by scale[c * s + j] into the
+// block vector X[(off_c + a) * s + j] (float64).
+__global__ void fno_basis_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chips,
+                                 const float *__restrict__ y, const double *__restrict__ scale, int s,
+                                 double *__restrict__ X) {
+  const Unit u = units[blockIdx.x];
+  const ChipDev ch = chips[u.chip];
+  const long long total = (u.end - u.begin) * s;
+  for (long long i = threadIdx.x; i < total; i += blockDim.x) {
+    const long long a = u.begin + i / s;
+    const int j = (int)(i % s);
+    const float v = y[ch.off * s + (long long)j * ch.n + (a - ch.off)];
+    X[a * s + j] = (double)v * scale[(long long)u.chip * s + j];
+  }
+}
+
 }  // namespace
 }  // namespace blockoa
 
 using namespace blockoa;
+
+extern "C" int blockoa_fno_basis(const blockoa_operator *op, const float *y, const double *scale, int s,
+                                 double *X, blockoa_stream stream) {
+  if (!op || s < 1 || s > 4096 || !y || !scale || !X) return BLOCKOA_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<Unit> units = make_units(op, 512);
+  blockoa_operator *mop = const_cast<blockoa_operator *>(op);
+  void *d_units = nullptr;
+  int rc = pool_alloc(mop, &d_units, sizeof(Unit) * units.size(), st);
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(d_units, units.data(), sizeof(Unit) * units.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    g_launches += 1;
+    fno_basis_kernel<<<(unsigned)units.size(), 256, 0, st>>>((const Unit *)d_units, op->d_chips, y, scale, s, X);
+    e = cudaGetLastError();
+  }
+  pool_free(d_units, st);
+  return cuda_status(e, "blockoa_fno_basis");
+}
 
 extern "C" int blockoa_fno_param_count(const blockoa_fno_shape *shape, int64_t *count) {
   if (!shape_ok(shape) || !count) return BLOCKOA_ERR_INVALID;

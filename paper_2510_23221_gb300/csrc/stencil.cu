@@ -631,6 +631,86 @@ int launch_apply_block64(const blockoa_operator *op, const double *U, double *AU
   return cuda_status(e, "apply_block64");
 }
 
+// Relative residual of a candidate block solution, per chip and column:
+// acc[chip][j][0] += ||B_j - A X_j||^2 and acc[chip][j][1] += ||B_j||^2 over
+// the cells of a unit (one thread per (cell, column) entry, float64 stencil
+// in difference form, column sums in shared memory, one atomic per column
+// and CTA).  s <= 64.
+__global__ void __launch_bounds__(256)
+residual_ratio_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chips,
+                      const double *__restrict__ g, const double *__restrict__ B,
+                      const double *__restrict__ X, int s, double *__restrict__ acc) {
+  __shared__ double sn[64], sd[64];
+  for (int j = threadIdx.x; j < 64; j += blockDim.x) { sn[j] = 0.0; sd[j] = 0.0; }
+  __syncthreads();
+  const Unit u = units[blockIdx.x];
+  const ChipDev ch = chips[u.chip];
+  const long long nxny = (long long)ch.nx * ch.ny;
+  const long long total = (u.end - u.begin) * s;
+  for (long long i = threadIdx.x; i < total; i += blockDim.x) {
+    const long long a = u.begin + i / s;
+    const int j = (int)(i % s);
+    const long long loc = a - ch.off;
+    const int x = (int)(loc % ch.nx);
+    const int y = (int)((loc / ch.nx) % ch.ny);
+    const int z = (int)(loc / nxny);
+    const Coef64 c4 = load_coef<double>(g, a);
+    const double c = X[a * s + j];
+    double r = c4.w * c;
+    if (x + 1 < ch.nx) r += c4.x * (c - X[(a + 1) * s + j]);
+    if (x > 0) r += load_coef<double>(g, a - 1).x * (c - X[(a - 1) * s + j]);
+    if (y + 1 < ch.ny) r += c4.y * (c - X[(a + ch.nx) * s + j]);
+    if (y > 0) r += load_coef<double>(g, a - ch.nx).y * (c - X[(a - ch.nx) * s + j]);
+    if (z + 1 < ch.nz) r += c4.z * (c - X[(a + nxny) * s + j]);
+    if (z > 0) r += load_coef<double>(g, a - nxny).z * (c - X[(a - nxny) * s + j]);
+    const double b = B[a * s + j];
+    const double e = b - r;
+    atomicAdd(&sn[j], e * e);
+    atomicAdd(&sd[j], b * b);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < s; j += blockDim.x) {
+    atomicAdd(&acc[((long long)u.chip * s + j) * 2], sn[j]);
+    atomicAdd(&acc[((long long)u.chip * s + j) * 2 + 1], sd[j]);
+  }
+}
+
+// ratio = sqrt(num / den); a zero right-hand side gives 0 when the residual
+// is zero too, +inf otherwise.
+__global__ void residual_ratio_finish_kernel(const double *__restrict__ acc, double *__restrict__ ratio, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double num = acc[2 * i], den = acc[2 * i + 1];
+  ratio[i] = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+}
+
+int launch_residual_ratio(const blockoa_operator *op, const double *B, const double *X, int s,
+                          double *ratio, cudaStream_t st) {
+  std::vector<Unit> units = make_units(op, 256);
+  blockoa_operator *mop = const_cast<blockoa_operator *>(op);
+  const int n = op->n_chips * s;
+  void *d_units = nullptr, *acc = nullptr;
+  int rc = pool_alloc(mop, &d_units, sizeof(Unit) * units.size(), st);
+  if (!rc) rc = pool_alloc(mop, &acc, sizeof(double) * 2 * (size_t)n, st);
+  if (rc) {
+    pool_free(d_units, st);
+    return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(d_units, units.data(), sizeof(Unit) * units.size(),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, sizeof(double) * 2 * (size_t)n, st);
+  if (e == cudaSuccess) {
+    g_launches += 2;
+    residual_ratio_kernel<<<(unsigned)units.size(), 256, 0, st>>>((const Unit *)d_units, op->d_chips, op->g64,
+                                                                  B, X, s, (double *)acc);
+    residual_ratio_finish_kernel<<<(n + 255) / 256, 256, 0, st>>>((const double *)acc, ratio, n);
+    e = cudaGetLastError();
+  }
+  pool_free(d_units, st);
+  pool_free(acc, st);
+  return cuda_status(e, "residual_ratio");
+}
+
 int launch_residual64(const blockoa_operator *op, const double *B, const double *X, double *R,
                       int S, double *rn2, cudaStream_t st) {
   std::vector<Unit> units = make_units(op, 1024);

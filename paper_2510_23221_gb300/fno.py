@@ -16,7 +16,7 @@ from . import blockoa as bo
 FNO_EXPORTED = (
     "blockoa_fno_param_count", "blockoa_fno_create", "blockoa_fno_forward", "blockoa_fno_mse",
     "blockoa_fno_backward", "blockoa_fno_zero_grad", "blockoa_fno_adam_step",
-    "blockoa_fno_get_params", "blockoa_fno_get_grads", "blockoa_fno_destroy",
+    "blockoa_fno_get_params", "blockoa_fno_get_grads", "blockoa_fno_destroy", "blockoa_fno_basis",
 )
 
 
@@ -62,6 +62,7 @@ def _lib():
         lib.blockoa_fno_adam_step.argtypes = [vp, f, f, f, f, i, vp]
         lib.blockoa_fno_get_params.argtypes = [vp, vp]
         lib.blockoa_fno_get_grads.argtypes = [vp, vp]
+        lib.blockoa_fno_basis.argtypes = [vp, vp, vp, i, vp, vp]
         lib.blockoa_fno_destroy.argtypes = [vp]
         lib.blockoa_fno_destroy.restype = None
         for name in FNO_EXPORTED:
@@ -144,6 +145,16 @@ class Fno:
         out = np.empty(self.n_params, np.float32)
         bo._check(_lib().blockoa_fno_get_grads(self.handle, out.ctypes.data_as(ct.c_void_p)), "fno_get_grads")
         return out
+
+
+def basis(op: bo.Operator, y, scale, s: int, X, stream=None):
+    """blockoa_fno_basis: network outputs y [chip][s][n_c] (float32) times
+    scale [chip * s] (float64) into the block vector X [n_total][s]."""
+    import torch
+    bo._check(_lib().blockoa_fno_basis(op.handle, bo._ptr(y, torch.float32, "y", op.n_total * s),
+                                       bo._ptr(scale, torch.float64, "scale", op.n_chips * s), s,
+                                       bo._ptr(X, torch.float64, "X", op.n_total * s), bo._stream(stream)),
+              "fno_basis")
 
 
 def pack(params: dict, layers: int) -> np.ndarray:

@@ -77,6 +77,8 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.blockoa_apply_operator(None, None, None, 4, bo.FP64, None) == bo.ERR_INVALID
     assert lib.blockoa_pair_check(None, None, None, 4, bo.FP64, None, None) == bo.ERR_INVALID
     assert lib.blockoa_pair_check_static(None, None, None, 4, bo.FP64, None, None) == bo.ERR_INVALID
+    assert lib.blockoa_residual_ratio(None, None, None, 4, None, None) == bo.ERR_INVALID
+    assert lib.blockoa_inject_chip_status(None, 0, bo.ERR_TIMEOUT, 0) == bo.ERR_INVALID
     assert lib.blockoa_build_rhs(None, None, None, 4, None) == bo.ERR_INVALID
     assert lib.blockoa_build_rhs_volume(None, None, None, 4, None) == bo.ERR_INVALID
     assert lib.blockoa_export_conductances(None, 0, None, None, None, None) == bo.ERR_INVALID

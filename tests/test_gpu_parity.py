@@ -312,6 +312,52 @@ def test_normalised_weights_match_oracle(precision):
     assert ei.value.code == bo.ERR_INVALID
 
 
+def test_residual_ratio_matches_oracle():
+    """The warm start's fallback test, ||B_j - A X_j|| / ||B_j|| per chip and
+    column, against the oracle's operator; a zero column of B reads 0 when
+    X is zero there and +inf otherwise."""
+    chips = [synth.random_small_chip(37, 19, 13, 4), synth.random_small_chip(38, 9, 30, 2, h_side=2e3)]
+    s = 11
+    rng = np.random.default_rng(36)
+    op = bo.assemble(chips)
+    Bs = [rng.standard_normal((c.n, s)) for c in chips]
+    Xs = [rng.standard_normal((c.n, s)) for c in chips]
+    Bs[1][:, 4] = 0.0
+    Xs[1][:, 4] = 0.0
+    Bs[0][:, 7] = 0.0
+    r = torch.empty(op.n_chips * s, dtype=torch.float64, device="cuda")
+    bo.residual_ratio(op, cuda(np.concatenate([b.ravel() for b in Bs])),
+                      cuda(np.concatenate([x.ravel() for x in Xs])), s, r)
+    got = r.cpu().numpy().reshape(op.n_chips, s)
+    for c, chip in enumerate(chips):
+        A = orc.assemble(chip)
+        num = np.linalg.norm(Bs[c] - A @ Xs[c], axis=0)
+        den = np.linalg.norm(Bs[c], axis=0)
+        for j in range(s):
+            if den[j] > 0:
+                assert abs(got[c, j] - num[j] / den[j]) <= 1e-12 * num[j] / den[j]
+            else:
+                assert got[c, j] == (0.0 if num[j] == 0 else np.inf)
+
+
+def test_fno_basis_scales_and_transposes():
+    from paper_2510_23221_gb300 import fno
+    chips = [synth.random_small_chip(47, 6, 5, 3), synth.random_small_chip(48, 4, 7, 2)]
+    s = 5
+    rng = np.random.default_rng(46)
+    op = bo.assemble(chips)
+    y = rng.standard_normal(op.n_total * s).astype(np.float32)
+    scale = rng.uniform(0.5, 2.0, op.n_chips * s)
+    X = torch.empty(op.n_total * s, dtype=torch.float64, device="cuda")
+    fno.basis(op, cuda(y), cuda(scale), s, X)
+    got = X.cpu().numpy()
+    for c in range(op.n_chips):
+        off, n = op.sizes[c]["off"], op.sizes[c]["n"]
+        yc = y[off * s:(off + n) * s].reshape(s, n).astype(np.float64)
+        ref = (yc * scale[c * s:(c + 1) * s, None]).T
+        assert np.array_equal(got[off * s:(off + n) * s].reshape(n, s), ref)
+
+
 def test_apply_basis_rejects_bad_arguments():
     op = bo.assemble([synth.random_small_chip(8, 5, 4, 2)])
     with pytest.raises(bo.BlockoaError):
@@ -605,6 +651,36 @@ def test_statuses_not_converged_and_breakdown():
     assert stats[1].status == bo.ERR_BREAKDOWN
     ref = np.linalg.solve(orc.assemble(chips[0]).toarray(), Bs[0])
     assert np.all(relcols(Xs[0], ref) < 1e-8)
+
+
+@pytest.mark.parametrize("precision", [bo.FP64, bo.MIXED])
+def test_timeout_status_of_one_chip_is_reported_and_others_converge(precision):
+    """A chip whose device state reads ERR_TIMEOUT between polls (what the
+    P update's bounded wait leaves when it gives up; injected here from the
+    host, nothing on the GPU waits or faults) is reported with that status,
+    and the other chips of the operator still converge to the dense
+    solution."""
+    chips = [small_chips()[i] for i in (1, 2, 3)]
+    rng = np.random.default_rng(71)
+    Bs = [rng.uniform(0, 1e-2, (c.n, 4)) for c in chips]
+    op = bo.assemble(chips)
+    B = cuda(np.concatenate([b.ravel() for b in Bs]))
+    X = torch.empty_like(B)
+    bo.inject_chip_status(op, 1, bo.ERR_TIMEOUT, after_polls=1)
+    st = bo.block_solve(op, B, X, 4, rtol=1e-10, precision=precision, check_every=2, raise_on_error=False)
+    assert st[1].status == bo.ERR_TIMEOUT
+    Xh = X.cpu().numpy()
+    for c in (0, 2):
+        assert st[c].status == bo.OK and st[c].relres_max <= 1e-10, st[c]
+        sz = op.sizes[c]
+        got = Xh[sz["off"] * 4:(sz["off"] + sz["n"]) * 4].reshape(-1, 4)
+        ref = np.linalg.solve(orc.assemble(chips[c]).toarray(), Bs[c])
+        assert np.all(relcols(got, ref) < 1e-8)
+    with pytest.raises(bo.BlockoaError):
+        bo.inject_chip_status(op, 7, bo.ERR_TIMEOUT)
+    # armed once: the next solve is clean
+    st = bo.block_solve(op, B, X, 4, rtol=1e-10, precision=precision, check_every=2)
+    assert all(x.status == bo.OK for x in st)
 
 
 def test_invalid_calls_return_invalid():
