@@ -78,10 +78,13 @@ def parse_args(argv=None):
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--plain-steps", type=int, default=1)
     p.add_argument("--e2e-steps", type=int, default=8)
+    p.add_argument("--copy-streams", type=int, default=4)
     p.add_argument("--cpu-seconds", type=float, default=25.0)
     p.add_argument("--no-cpu-baseline", action="store_true",
                    help="skip the CPU leg (oracle timing and oracle-side verification)")
-    p.add_argument("--no-suite", action="store_true", help="skip the other workloads (c1, c3, c5)")
+    p.add_argument("--no-suite", action="store_true", help="skip the other workloads (c1, c3, c4, c5)")
+    p.add_argument("--cpu-full", action="store_true",
+                   help="reference arm: every step is the whole oracle pipeline on the workload (no scaling)")
     return p.parse_args(argv)
 
 
@@ -437,7 +440,7 @@ def run_ours(args):
                  torch.empty(n * M, dtype=torch.float32, pin_memory=True)) for _ in range(K)]
         dens_d = torch.empty_like(inputs.density)
         C_d = torch.empty_like(inputs.C)
-        ps = pl.PairStreamer(operator(bo.MIXED), s, M, bo.MIXED)
+        ps = pl.PairStreamer(operator(bo.MIXED), s, M, bo.MIXED, copy_streams=args.copy_streams)
         kw = dict(CHOSEN, rtol=RTOL, raise_on_error=False)
         kw.pop("precision")
         for k in range(K):   # warm-up: every pinned output buffer written once (first touch)
@@ -458,6 +461,7 @@ def run_ours(args):
                "h2d_bytes_per_step": int(dens_h.nbytes + C_h.nbytes),
                "d2h_bytes_per_step": d2h,
                "d2h_GBps_effective": round(K * d2h / (e2e_ms / 1e3) / 1e9, 1),
+               "copy_streams": args.copy_streams,
                "overlap": "pairs of step k copied to host while step k+1 computes"}
         del ps, outs
 
@@ -629,6 +633,78 @@ def run_suite(peaks, flush):
     e5 = one(w5, pl.CHOSEN_SOLVE, 1000)
     e5["form"] = "chosen form, 10 chunks of 1000 fields"
     out["c5"] = e5
+    out["c4"] = warm_start_entry(peaks)
+    return out
+
+
+def fno_flops(shape) -> float:
+    """Floating-point operations of one forward pass of the network for one
+    sample (an FMA counted as 2, a complex multiply-add as 8): lifting,
+    per layer the pointwise channel mixing and the truncated transform
+    (x: real -> complex onto mx modes, y and z: complex onto my, mz modes),
+    the per-mode complex mixing and the inverse transform, then the
+    two-layer projection."""
+    n = shape.nx * shape.ny * shape.nz
+    W, H, L = shape.width, shape.hidden, shape.layers
+    fwd = (shape.ny * shape.nz * W * shape.nx * shape.mx * 4
+           + shape.nz * shape.mx * W * shape.ny * shape.my * 8
+           + shape.mx * shape.my * W * shape.nz * shape.mz * 8)
+    mix = shape.mx * shape.my * shape.mz * W * W * 8
+    per_layer = n * W * W * 2 + 2 * fwd + mix
+    return float(n * W * shape.c_in * 2 + L * per_layer + n * (W * H * 2 + H * 2))
+
+
+def warm_start_entry(peaks, train_chips: int = 16, epochs: int = 4, eval_chips: int = 8):
+    """The learned warm start on a bounded budget: the network (4 layers,
+    width 32, 12 x 12 x 4 modes) trained on the bases of `train_chips`
+    chips of the 128x128x8 distribution for `epochs` epochs by the library's
+    kernels, then `eval_chips` held-out chips solved from zero and from the
+    prediction (fallback when a column's predicted residual exceeds 1e-2),
+    chosen solver form.  Reports iterations and milliseconds of both, the
+    fallback count, and the network's forward rate against the float32
+    peak."""
+    import torch
+
+    from paper_2510_23221_gb300 import fno, synth
+    from paper_2510_23221_gb300 import warmstart as W
+
+    t0 = time.perf_counter()
+    tr = [synth.FNO_TRAIN_SEED0 + i for i in range(train_chips)]
+    X, Y, t_scale, _ = W.build_dataset(tr)
+    chip0, _ = synth.warm_start_chip(tr[0])
+    shape = W.shape_for(chip0, max_batch=8)
+    net = fno.Fno(shape, W.init_params(shape, 1234))
+    hist = W.train(net, X, Y, epochs, 2e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    xb = X[:8].contiguous()
+    yb = torch.empty((8,) + tuple(Y.shape[1:]), dtype=torch.float32, device="cuda")
+    del X, Y
+    for _ in range(2):
+        net.forward(xb, yb, 8)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record()
+    for _ in range(reps):
+        net.forward(xb, yb, 8)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_sample = e0.elapsed_time(e1) / (reps * 8)
+    fl = fno_flops(shape)
+    achieved = fl / (ms_sample / 1e3) / 1e12
+    ev = W.evaluate(W.WarmStart(net, t_scale), [synth.FNO_HELDOUT_SEED0 + i for i in range(eval_chips)])
+    net.close()
+    keep = ("warm_start_used", "zero_iters_median", "chosen_iters_median", "always_warm_iters_mean",
+            "zero_ms_median", "chosen_ms_median", "pred_ms_mean", "pred_relres_median",
+            "pred_rel_error_median", "all_converged")
+    out = {"workload": f"warm start, 128x128x8 chips, s = 32; {train_chips} training chips x {epochs} epochs, "
+                       f"{eval_chips} held-out chips",
+           "chips": eval_chips, "params": net.n_params, "train_loss": [hist[0], hist[-1]],
+           "train_s": round(train_s, 1), **{k: ev[k] for k in keep},
+           "roofline_forward": {"kernel": "fno_forward", "bound": "alu", "achieved": round(achieved, 3),
+                                "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+                                "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+                                "ms_per_sample": round(ms_sample, 4), "flop_per_sample": fl}}
     return out
 
 
@@ -670,6 +746,24 @@ def oracle_sample(w, seconds: float, orc=None, A=None, Bm=None):
               f"iterations (timed, scaled to {iters}), combine+apply on {mf} of {w.M} fields "
               f"(timed, scaled to {w.M})")
     return w.M / total, sample, total, time.perf_counter() - t_start
+
+
+def oracle_full_step(w, orc=None):
+    """The whole FP64 oracle pipeline on the workload, timed, nothing scaled:
+    assembly, right-hand sides, block CG from zero to the workload's
+    tolerance, combination and operator action of all M fields (in chunks
+    of 500 fields).  Returns (seconds, block-CG iterations)."""
+    if orc is None:
+        from oracle import blockoa_oracle as orc
+    chip = w.chips[0]
+    t0 = time.perf_counter()
+    A = orc.assemble(chip)
+    B = orc.rhs(chip, w.density[0])
+    U, info = orc.block_cg(A, B, rtol=w.rtol)
+    for m0 in range(0, w.M, 500):
+        T = orc.combine(U, w.coeffs[0][:, m0:m0 + 500])
+        orc.apply_operator(A, T)
+    return time.perf_counter() - t0, int(info["iters"])
 
 
 def cpu_threads():
@@ -768,6 +862,8 @@ def oracle_suite(orc, suite):
     import torch
     out = {}
     for name, e in suite.items():
+        if "_dev" not in e:
+            continue
         d = e.pop("_dev")
         w, op, chunk = d["w"], d["op"], d["chunk"]
         s = w.s
@@ -819,6 +915,33 @@ def run_reference(args):
     if rank != 0:
         return
     w = workload(0)
+    threads = cpu_threads()
+    if args.cpu_full:
+        times, its = [], []
+        for k in range(args.warmup + args.steps):
+            sec, it = oracle_full_step(w)
+            if k >= args.warmup:
+                times.append(sec)
+                its.append(it)
+        value = len(times) * w.M / sum(times)
+        sample = (f"the whole workload every step: assembly, block CG from zero to {w.rtol:g} "
+                  f"({its[0]} iterations), combine+apply on all {w.M} fields")
+        out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": round(1e3 * statistics.mean(times), 1), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": w.name, "cells": w.chips[0].n, "s": w.s, "M": w.M,
+                          "precision": "fp64", "rtol": RTOL},
+               "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "estimated": False, "sample": sample,
+                                "step_s": [round(x, 2) for x in times],
+                                "median_s": round(statistics.median(times), 2),
+                                "threads": {"dense_products": threads, "sparse_products": 1},
+                                "host_cores": os.cpu_count(), "cpu_model": cpu_model()},
+               "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                       "d2h_bytes_per_step": 0}}
+        print(json.dumps(out), flush=True)
+        return
     per_step = max(2.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
     vals, totals, took = [], [], []
     sample = ""
@@ -829,7 +952,6 @@ def run_reference(args):
             totals.append(total)
             took.append(t)
     value = len(vals) * w.M / sum(totals)
-    threads = cpu_threads()
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(1e3 * statistics.mean(took), 1), "higher_is_better": True,

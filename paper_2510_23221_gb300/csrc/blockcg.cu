@@ -237,6 +237,31 @@ __device__ __forceinline__ void gram_tile(T *acc, const T *A, const T *B, int i0
   gram_range<T, S>(acc, A, B, i0, j0, grp * G::GC, G::GC);
 }
 
+// float32 -> float64 by integer instructions (float64 instructions issue at
+// 1/64 of the float32 rate on this part): exact for every float, subnormals
+// and non-finite values included.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long m = u & 0x7fffffu;
+  if (ex == 0xffu) return __longlong_as_double((long long)(sgn | 0x7ff0000000000000ull | (m << 29)));
+  if (ex == 0u) {
+    if (m == 0) return __longlong_as_double((long long)sgn);
+    const int b = 63 - __clzll((long long)m);   // leading bit of a subnormal's m 2^-149
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)(b + 874) << 52) |
+                                            ((m ^ (1ull << b)) << (52 - b))));
+  }
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)(ex + 896) << 52) | (m << 29)));
+}
+
+// Add a compensated float32 pair hi + lo (|lo| <= ulp(hi) / 2) to a float64
+// accumulator: two atomics of exact conversions, no float64 arithmetic.
+__device__ __forceinline__ void atomic_add_pair(double *dst, float hi, float lo) {
+  atomicAdd(dst, f2d_exact(hi));
+  if (lo != 0.f) atomicAdd(dst, f2d_exact(lo));
+}
+
 // Reduce the NG groups' 4x4 blocks in shared memory and add the S x S
 // result to the chip's float64 accumulator.  float partial sums (each over
 // at most a few hundred cells of one CTA) are combined across groups with
@@ -264,7 +289,7 @@ __device__ void gram_flush(const T *acc, double *red, double *dst, bool diag) {
         lo += (hi - (sum - bp)) + (v - bp);
         hi = sum;
       }
-      atomicAdd(dst + e, (double)hi + (double)lo);
+      atomic_add_pair(dst + e, hi, lo);
     } else {
       double sum = 0.0;
       for (int gg = 0; gg < G::NG; ++gg) sum += rt[gg * S * S + e];
@@ -298,7 +323,8 @@ __device__ void gram_flush_split(const T *acc, double *red, double *dst_a, doubl
         lo += (hi - (sum - bp)) + (v - bp);
         hi = sum;
       }
-      atomicAdd((half ? dst_b : dst_a) + e, (double)hi + (double)lo);
+      if constexpr (sizeof(T) == 4) atomic_add_pair((half ? dst_b : dst_a) + e, hi, lo);
+      else atomicAdd((half ? dst_b : dst_a) + e, (double)hi + (double)lo);
     }
   }
   __syncthreads();
@@ -320,19 +346,25 @@ struct UnitSched {
   int *work;                  // [0] next unit, [1] CTAs finished (zero between launches)
 };
 
-// Next unit of the calling CTA (n_units when none is left).
-__device__ __forceinline__ int next_unit(const UnitSched &us, const ChipSolveState *state, int *slot) {
+// Next unit of the calling CTA (n_units when none is left).  Thread 0
+// fetches one unit ahead: the atomic for the following unit is issued here
+// and its value (kept in `pend`, thread 0's register) is used at the next
+// call, so the round trip to the counter overlaps the current unit's work
+// instead of stalling the CTA at every unit.
+__device__ __forceinline__ int next_unit(const UnitSched &us, const ChipSolveState *state, int *slot,
+                                         int &pend) {
   __syncthreads();   // every thread has read the previous value
   if (threadIdx.x == 0) {
-    int ui;
+    int ui = pend >= 0 ? pend : atomicAdd(&us.work[0], 1);
     for (;;) {
-      ui = atomicAdd(&us.work[0], 1);
       if (ui >= us.n_units) break;
       const int chip = us.units[ui].chip;
       if (state[chip].active) break;
       atomicMax(&us.work[0], us.chip_unit_end[chip]);   // skip the rest of this chip
+      ui = atomicAdd(&us.work[0], 1);
     }
     *slot = ui;
+    pend = ui < us.n_units ? atomicAdd(&us.work[0], 1) : us.n_units;
   }
   __syncthreads();
   return *slot;
@@ -446,8 +478,9 @@ spmm_gram_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T 
 #pragma unroll
   for (int e = 0; e < NA; ++e) acc[e] = T(0);
   int cur = -1, run = 0;   // chip of the running accumulation and its units
+  int pend = -1;   // thread 0: the unit fetched ahead
   for (;;) {
-    const int ui = next_unit(us, A.state, &s_unit);
+    const int ui = next_unit(us, A.state, &s_unit, pend);
     const int chip = ui < us.n_units ? us.units[ui].chip : -1;
     if (run > 0 && chip != cur) {   // flush the running chip
       if constexpr (SPLIT) {
@@ -536,7 +569,8 @@ __device__ __forceinline__ void update_flush(const T *aw, const T *rn, double *r
         lo += (hi - (s2 - bp)) + (x - bp);
         hi = s2;
       }
-      atomicAdd(A.rn2 + (long long)c * S + t * V + v, (double)hi + (double)lo);
+      if constexpr (sizeof(T) == 4) atomic_add_pair(A.rn2 + (long long)c * S + t * V + v, hi, lo);
+      else atomicAdd(A.rn2 + (long long)c * S + t * V + v, (double)hi + (double)lo);
     }
   }
   __syncthreads();
@@ -571,8 +605,9 @@ update_gram_kernel(const UnitSched us, const T *__restrict__ P, const T *__restr
 #pragma unroll
   for (int v = 0; v < V; ++v) rn[v] = T(0);
   int cur = -1, run = 0;
+  int pend = -1;   // thread 0: the unit fetched ahead
   for (;;) {
-    const int ui = next_unit(us, A.state, &s_unit);
+    const int ui = next_unit(us, A.state, &s_unit, pend);
     const int chip = ui < us.n_units ? us.units[ui].chip : -1;
     if (run > 0 && chip != cur) {   // flush the running chip
       update_flush<T, S>(aw, rn, red, A, cur);
@@ -662,8 +697,9 @@ p_update_kernel(const UnitSched us, const ChipSolveState *__restrict__ state, co
   const int t = threadIdx.x;
   const int j0 = (t % G::TPR) * V, cl0 = (t / G::TPR) * 4;
   int cur = -1;
+  int pend = -1;   // thread 0: the unit fetched ahead
   for (;;) {
-    const int ui = next_unit(us, state, &s_unit);
+    const int ui = next_unit(us, state, &s_unit, pend);
     if (ui >= us.n_units) break;
     const Unit u = us.units[ui];
     if (u.chip != cur) {   // beta of the chip (read after the tile barrier)
@@ -1135,8 +1171,9 @@ update_zline_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const
 #pragma unroll
   for (int v = 0; v < V; ++v) rn[v] = T(0);
   int cur = -1, run = 0;
+  int pend = -1;   // thread 0: the unit fetched ahead
   for (;;) {
-    const int ui = next_unit(us, A.state, &s_unit);
+    const int ui = next_unit(us, A.state, &s_unit, pend);
     const int chip = ui < us.n_units ? us.units[ui].chip : -1;
     if (run > 0 && chip != cur) {
       update_flush<T, S>(aw, rn, red, A, cur, !TWO);
@@ -1292,8 +1329,9 @@ zline2_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T *__
 #pragma unroll
   for (int e = 0; e < 16; ++e) aw[e] = T(0);
   int cur = -1, run = 0;
+  int pend = -1;   // thread 0: the unit fetched ahead
   for (;;) {
-    const int ui = next_unit(us, A.state, &s_unit);
+    const int ui = next_unit(us, A.state, &s_unit, pend);
     const int chip = ui < us.n_units ? us.units[ui].chip : -1;
     if constexpr (!INIT) {
       if (run > 0 && chip != cur) {

@@ -111,12 +111,15 @@ class PairStreamer:
     device result buffers, then queues the device-to-host copy of that
     buffer on a copy stream; the step after next waits for that copy before
     reusing the buffer.  Compute runs on a stream of its own: work on the
-    legacy default stream would wait for every pending copy.  Host outputs
-    must be pinned for the copies to overlap.  ``finish`` makes the caller's
-    stream wait for all queued work.
+    legacy default stream would wait for every pending copy.  Each step's
+    copies are dealt in chunks over ``copy_streams`` streams so that several
+    copy engines share the device-to-host traffic.  Host outputs must be
+    pinned for the copies to overlap.  ``finish`` makes the caller's stream
+    wait for all queued work.
     """
 
-    def __init__(self, op: bo.Operator, s: int, M: int, precision: int, chunk_bytes: int = 256 << 20):
+    def __init__(self, op: bo.Operator, s: int, M: int, precision: int, chunk_bytes: int = 64 << 20,
+                 copy_streams: int = 4):
         import torch
         n = op.n_total
         dev = torch.device("cuda")
@@ -127,9 +130,9 @@ class PairStreamer:
         self.T = [torch.empty(n * M, dtype=fdt, device=dev) for _ in range(2)]
         self.q = [torch.empty(n * M, dtype=fdt, device=dev) for _ in range(2)]
         self.compute_stream = torch.cuda.Stream(device=dev)
-        self.copy_stream = torch.cuda.Stream(device=dev)
+        self.copy_streams = [torch.cuda.Stream(device=dev) for _ in range(max(1, copy_streams))]
         self.ready = [torch.cuda.Event() for _ in range(2)]
-        self.freed = [torch.cuda.Event() for _ in range(2)]
+        self.freed = [[torch.cuda.Event() for _ in self.copy_streams] for _ in range(2)]
         self.chunk = max(1, chunk_bytes // self.T[0].element_size())
         self.k = 0
 
@@ -140,7 +143,8 @@ class PairStreamer:
         cs.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(cs):
             if self.k >= 2:
-                cs.wait_event(self.freed[b])
+                for ev in self.freed[b]:
+                    cs.wait_event(ev)
             dens_d.copy_(dens_h, non_blocking=True)
             C_d.copy_(C_h, non_blocking=True)
             bo.reassemble(self.op, chips)
@@ -149,12 +153,17 @@ class PairStreamer:
             bo.combine(self.op, self.U, C_d, self.T[b], self.s, self.M, self.precision)
             bo.apply_operator(self.op, self.T[b], self.q[b], self.M, self.precision)
             self.ready[b].record(cs)
-        self.copy_stream.wait_event(self.ready[b])
-        with torch.cuda.stream(self.copy_stream):
-            for src, dst in ((self.T[b], T_h), (self.q[b], q_h)):
-                for i in range(0, src.numel(), self.chunk):
+        ncs = len(self.copy_streams)
+        for c in self.copy_streams:
+            c.wait_event(self.ready[b])
+        q = 0
+        for src, dst in ((self.T[b], T_h), (self.q[b], q_h)):
+            for i in range(0, src.numel(), self.chunk):
+                with torch.cuda.stream(self.copy_streams[q % ncs]):
                     dst[i:i + self.chunk].copy_(src[i:i + self.chunk], non_blocking=True)
-            self.freed[b].record(self.copy_stream)
+                q += 1
+        for c, ev in zip(self.copy_streams, self.freed[b]):
+            ev.record(c)
         self.k += 1
         return stats
 
@@ -162,4 +171,5 @@ class PairStreamer:
         import torch
         cur = torch.cuda.current_stream()
         cur.wait_stream(self.compute_stream)
-        cur.wait_stream(self.copy_stream)
+        for c in self.copy_streams:
+            cur.wait_stream(c)
