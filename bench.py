@@ -206,6 +206,8 @@ def algorithmic(kernel: str, n: int, s: int, M: int, precond: str = "zline2"):
         "apply_fields": ("hbm", 8 * n * M, "byte"),
         # combination: write T (float32), read the bf16x3 basis tiles
         "combine_tc": ("hbm", 4 * n * M + 2 * 3 * Sp * n, "byte"),
+        # fused combination + operator action: write T and q (float32)
+        "combine_apply": ("hbm", 8 * n * M, "byte"),
         "residual64": ("alu64", n * S * 14, "flop"),
     }
     return table.get(kernel)
@@ -339,8 +341,7 @@ def run_ours(args):
         op = operator(precision)
         bo.build_rhs(op, inputs.density, B, s)
         st = bo.block_solve(op, B, U, s, rtol=RTOL, raise_on_error=False, **solve)
-        bo.combine(op, U, inputs.C, Tb, s, M, precision)
-        bo.apply_operator(op, Tb, qb, M, precision)
+        pl.fields(op, U, inputs.C, Tb, qb, s, M, precision)
         return op, st
 
     def verify(op, st, Tb, qb, precision):
@@ -423,6 +424,30 @@ def run_ours(args):
     if dfloat:
         dfloat["form"] = "chosen form with double-float (~48-bit) s x s sweeps in the Gram kernels' tails"
 
+    # ---- the fused combination + operator action beside the two calls it
+    # replaces, on the last step's basis (pairs verified like the headline's)
+    fused = None
+    if args.plain_steps > 0:
+        op_m = ops[bo.MIXED]
+        fms, ums, fok = [], [], 0
+        for rep in range(4):
+            flush.zero_()
+            ms_, _ = timed(stream, lambda: bo.combine_apply(op_m, U, inputs.C, T, q, s, M))
+            if rep:
+                fms.append(ms_)
+            fok = int(verify(op_m, solver[-1:] or [st], T, q, bo.MIXED)[0].sum()) if rep == 3 else fok
+            flush.zero_()
+            ms_, _ = timed(stream, lambda: pl.fields(op_m, U, inputs.C, T, q, s, M, bo.MIXED))
+            if rep:
+                ums.append(ms_)
+        fbytes = 8 * n * M
+        fused = {"fused_ms": round(statistics.median(fms), 3), "two_calls_ms": round(statistics.median(ums), 3),
+                 "fused_GBps": round(fbytes / (statistics.median(fms) / 1e3) / 1e9, 1),
+                 "verified_pairs": fok, "in_chosen_form": False,
+                 "note": "T and q written once (8 n M bytes); slower than the two calls on this chip"
+                 if statistics.median(fms) > statistics.median(ums) else
+                 "T and q written once (8 n M bytes)"}
+
     # ---- end to end from pinned host buffers, host<->device copies timed.
     # K steps back to back through pipeline.PairStreamer: each step copies its
     # inputs in from pinned host memory, runs the hot path and streams its
@@ -470,6 +495,7 @@ def run_ours(args):
     if os.path.exists(pp):
         peaks = json.load(open(pp))
     roof = roofline(kt_sum, n, s, M, peaks, precond="zline2", real_launches=real_launches)
+    fused_roof = hbm_entry("combine_apply", kt_sum, n, s, M, peaks)
 
     suite = None
     if rank == 0 and not args.no_suite:
@@ -479,6 +505,10 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, oracle_check = cpu_leg(w, args.cpu_seconds, samples, T.view(M, n), q.view(M, n), suite)
 
+    for e in (suite or {}).values():   # device data the CPU leg did not consume
+        d = e.pop("_dev", None)
+        if d is not None:
+            d["op"].close()
     # pairs verified: library check of every pair, and the oracle's where it looked
     verified = 0
     for k, ok in enumerate(ok_masks):
@@ -519,8 +549,9 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "verification": verification,
             "plain_fp64": plain, "fp64_zline2": fp64_z2, "chosen_double_float_small_solves": dfloat,
+            "fused_combine_apply": fused,
             "e2e": e2e, "gpu_launches": int(launches),
-            "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+            "roofline": roof, "roofline_combine_apply": fused_roof, "cpu_baseline": cpu, "clocks": clk,
             "kernel_timing": kernel_timing_report(kt_sum, real_launches),
             "configs": suite,
             "wall_s_timed": round(wall_s, 3),
@@ -587,8 +618,7 @@ def run_suite(peaks, flush):
                 Mc = min(M, (i + 1) * chunk) - i * chunk
                 a, b = ev(), ev()
                 a.record(stream)
-                bo.combine(op, U, Cs[i], T, s, Mc, prec)
-                bo.apply_operator(op, T, q, Mc, prec)
+                pl.fields(op, U, Cs[i], T, q, s, Mc, prec)
                 b.record(stream)
                 torch.cuda.synchronize()
                 fields_ms += a.elapsed_time(b)
@@ -618,6 +648,7 @@ def run_suite(peaks, flush):
                  "relres_max": max(x.relres_max for x in st), "max_e_pair": worst,
                  "roofline_apply": hbm_entry("apply_fields", kt, n, s, chunk, peaks),
                  "roofline_combine": hbm_entry("combine_tc", kt, n, s, chunk, peaks),
+                 "roofline_combine_apply": hbm_entry("combine_apply", kt, n, s, chunk, peaks),
                  "_dev": {"w": w, "U": U, "T": T, "q": q, "op": op, "chunk": chunk}}
         return entry
 

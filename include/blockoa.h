@@ -323,6 +323,27 @@ int blockoa_combine_ex(blockoa_operator *op, const double *U, const double *C, v
                        int M, int dtype, const blockoa_combine_opts *opts, blockoa_stream stream);
 
 /*
+ * The combination and the operator action in one pass (Eq. 5 then Eq. 6,
+ * Sec. III-B/C, MIXED arithmetic): T = U C as blockoa_combine computes it
+ * (bfloat16x3 on the tensor cores, float32 fields, C bfloat16-exact) and
+ * q = A T from the same on-chip values, so T is never read back: for each
+ * x-row of a chip the kernel also forms the four rows the 7-point stencil
+ * reaches, y -+ 1 and z -+ 1, on the tensor cores.  T is bitwise the field
+ * blockoa_combine stores; q differs from blockoa_apply_operator on that T
+ * by float32 rounding order only.  Covers chips with nx <= 128 and s <= 32;
+ * otherwise it runs blockoa_combine and blockoa_apply_operator in turn.
+ * No noise or normalised weights (use the separate calls for those).
+ * Measured slower than the two separate calls on a 128 x 128 x 8 chip with
+ * s = 32 (2.2 ms against 1.6 ms for 5000 fields on one GB300).
+ * U: device float64 [n_total][s]; C: device float64 [chip][s][M]; T, q:
+ * device float32 fields [chip][M][n_c], not overlapping.  Synchronises the
+ * stream (reads a timeout flag).  Errors: ERR_INVALID, ERR_OOM, ERR_CUDA,
+ * ERR_TIMEOUT (a bounded wait gave up).
+ */
+int blockoa_combine_apply(blockoa_operator *op, const double *U, const double *C, float *T, float *q, int s,
+                          int M, blockoa_stream stream);
+
+/*
  * Operator action on the basis, AU = A U (Eq. 6 applied to the s basis
  * columns), float64.  U, AU: device float64 [n_total][s], cell-major like
  * blockoa_block_solve's X; they must not overlap.  By linearity

@@ -41,6 +41,7 @@ EXPORTED = (
     "blockoa_last_error", "blockoa_kernel_times", "blockoa_reset_kernel_times",
     "blockoa_launch_count", "blockoa_autotune", "blockoa_set_tuning", "blockoa_get_tuning",
     "blockoa_pair_check_static", "blockoa_residual_ratio", "blockoa_inject_chip_status",
+    "blockoa_combine_apply",
 )
 
 # Largest n_chips * M accepted by blockoa_pair_check_static (its fixed device array).
@@ -120,6 +121,7 @@ def _lib():
         lib.blockoa_pair_check_static.argtypes = [vp, vp, vp, i, i, vp, vp]
         lib.blockoa_residual_ratio.argtypes = [vp, vp, vp, i, vp, vp]
         lib.blockoa_inject_chip_status.argtypes = [vp, i, i, i]
+        lib.blockoa_combine_apply.argtypes = [vp, vp, vp, vp, vp, i, i, vp]
         lib.blockoa_export_conductances.argtypes = [vp, i, vp, vp, vp, vp]
         lib.blockoa_destroy.argtypes = [vp]
         lib.blockoa_destroy.restype = None
@@ -333,6 +335,16 @@ def combine(op: Operator, U, C, T, s: int, M: int, dtype: int, stream=None, nois
                     normalize_min=float(normalize_min))
     _check(_lib().blockoa_combine_ex(op.handle, pU, pC, pT, s, M, dtype, ct.byref(o), _stream(stream)),
            "combine_ex")
+
+
+def combine_apply(op: Operator, U, C, T, q, s: int, M: int, stream=None):
+    """T = U C and q = A T in one pass (blockoa_combine_apply; float32 fields)."""
+    import torch
+    _check(_lib().blockoa_combine_apply(op.handle, _ptr(U, torch.float64, "U", op.n_total * s),
+                                        _ptr(C, torch.float64, "C", op.n_chips * s * M),
+                                        _ptr(T, torch.float32, "T", op.n_total * M),
+                                        _ptr(q, torch.float32, "q", op.n_total * M), s, M, _stream(stream)),
+           "combine_apply")
 
 
 def apply_operator(op: Operator, T, q, M: int, dtype: int, stream=None):

@@ -680,7 +680,8 @@ extern "C" void blockoa_destroy(blockoa_operator *op) {
 
 static const char *kKernelNames[KC_COUNT] = {
     "spmm_gram", "alpha_solve", "update_gram", "beta_solve", "p_update",
-    "residual64", "combine_tc", "split_bf16x3", "apply_fields", "combine_fp64", "zline_second"};
+    "residual64", "combine_tc", "split_bf16x3", "apply_fields", "combine_fp64", "zline_second",
+    "combine_apply"};
 
 extern "C" int blockoa_kernel_times(blockoa_operator *op, int max_kernels, double *timed_ms,
                                     long long *timed_launches, long long *launches,

@@ -182,6 +182,20 @@ extern "C" int blockoa_combine(blockoa_operator *op, const double *U, const doub
   return blockoa_combine_ex(op, U, C, T, s, M, dtype, nullptr, stream);
 }
 
+extern "C" int blockoa_combine_apply(blockoa_operator *op, const double *U, const double *C, float *T,
+                                     float *q, int s, int M, blockoa_stream stream) {
+  if (!op || s < 1 || s > 64 || M < 0) return BLOCKOA_ERR_INVALID;
+  if (M == 0) return BLOCKOA_OK;
+  if (!U || !C || !T || !q || T == q) return BLOCKOA_ERR_INVALID;
+  if ((M + 7) / 8 > 65535) return BLOCKOA_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (fa_supported(op, s)) return launch_combine_apply(op, U, C, T, q, s, M, st);
+  CombineEpi epi;   // rows wider than one window: the two calls in turn
+  int rc = launch_combine(op, U, C, T, s, M, BLOCKOA_MIXED, epi, st);
+  if (rc) return rc;
+  return launch_apply_fields(op, T, q, M, BLOCKOA_MIXED, st);
+}
+
 extern "C" int blockoa_apply_basis(const blockoa_operator *op, const double *U, double *AU, int s,
                                    blockoa_stream stream) {
   if (!op || !U || !AU || s < 1 || s > 4096) return BLOCKOA_ERR_INVALID;

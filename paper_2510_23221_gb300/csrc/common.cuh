@@ -48,7 +48,8 @@ static_assert(sizeof(ChipSolveState) % 8 == 0, "chip states are read back in 8-b
 // Kernel classes with live event timing.
 enum KernelClass {
   KC_SPMM_GRAM = 0, KC_ALPHA_SOLVE, KC_UPDATE_GRAM, KC_BETA_SOLVE, KC_P_UPDATE,
-  KC_RESIDUAL64, KC_COMBINE_TC, KC_SPLIT, KC_APPLY, KC_COMBINE_FP64, KC_ZLINE2, KC_COUNT
+  KC_RESIDUAL64, KC_COMBINE_TC, KC_SPLIT, KC_APPLY, KC_COMBINE_FP64, KC_ZLINE2, KC_COMBINE_APPLY,
+  KC_COUNT
 };
 
 struct KernelTimes {
@@ -189,6 +190,11 @@ struct CombineEpi;   // noise.cuh
 // combine_tc.cu (bfloat16x3 on tcgen05; fields in float32)
 int launch_combine_tc(blockoa_operator *op, const double *U, const double *C, float *T, int s,
                       int M, const CombineEpi &epi, cudaStream_t st);
+
+// combine_apply.cu (fused T = U C and q = A T; float32 fields)
+bool fa_supported(const blockoa_operator *op, int s);
+int launch_combine_apply(blockoa_operator *op, const double *U, const double *C, float *T, float *q, int s,
+                         int M, cudaStream_t st);
 
 // combine.cu
 int launch_combine(blockoa_operator *op, const double *U, const double *C, void *T, int s, int M,

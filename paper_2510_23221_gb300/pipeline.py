@@ -43,6 +43,18 @@ class Result:
     timings_ms: dict = field(default_factory=dict)
 
 
+def fields(op, U, C, T, q, s: int, M: int, precision: int, stream=None, fused: bool = False):
+    """The pairs of a solved basis: T = U C and q = A T.  ``fused`` takes the
+    single pass of blockoa_combine_apply (mixed form only; T and q written
+    once, T never read back), otherwise the two calls, which are the faster
+    of the two on the 128 x 128 x 8, s = 32 chip."""
+    if fused and precision == bo.MIXED:
+        bo.combine_apply(op, U, C, T, q, s, M, stream=stream)
+    else:
+        bo.combine(op, U, C, T, s, M, precision, stream=stream)
+        bo.apply_operator(op, T, q, M, precision, stream=stream)
+
+
 def host_inputs(w):
     """Concatenated host arrays (float64) of a workload's density maps and C."""
     dens = np.concatenate([np.ascontiguousarray(d, np.float64).ravel() for d in w.density])
@@ -83,8 +95,7 @@ def run(w, precision: int, inputs: Optional[DeviceInputs] = None, rtol: Optional
     bo.build_rhs(op, inputs.density, B, s, stream=stream)
     stats = bo.block_solve(op, B, U, s, rtol=w.rtol if rtol is None else rtol, maxiter=maxiter,
                            precision=precision, stream=stream, **solve_kw)
-    bo.combine(op, U, inputs.C, T, s, M, precision, stream=stream)
-    bo.apply_operator(op, T, q, M, precision, stream=stream)
+    fields(op, U, inputs.C, T, q, s, M, precision, stream=stream)
     return Result(op, B, U, T, q, stats, s, M, precision)
 
 
@@ -150,8 +161,7 @@ class PairStreamer:
             bo.reassemble(self.op, chips)
             bo.build_rhs(self.op, dens_d, self.B, self.s)
             stats = bo.block_solve(self.op, self.B, self.U, self.s, precision=self.precision, **solve_kw)
-            bo.combine(self.op, self.U, C_d, self.T[b], self.s, self.M, self.precision)
-            bo.apply_operator(self.op, self.T[b], self.q[b], self.M, self.precision)
+            fields(self.op, self.U, C_d, self.T[b], self.q[b], self.s, self.M, self.precision)
             self.ready[b].record(cs)
         ncs = len(self.copy_streams)
         for c in self.copy_streams:

@@ -74,3 +74,41 @@ def test_clock_rows_summary():
     assert bench.ClockSampler.summarize(["x, y\n"]) is None
     hw = bench.ClockSampler.summarize(["0, 900, 2070, 700, 0x8, Active, Active, Not Active, Not Active\n"])
     assert hw["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
+
+
+def test_kernel_timing_separates_noop_launches():
+    # the graph launched 32 iterations' worth of loop kernels for 23 real iterations
+    kt = {"spmm_gram": (4.0, 2, 32), "apply_fields": (1.0, 1, 1)}
+    out = bench.kernel_timing_report(kt, {"spmm_gram": 23})
+    assert out["spmm_gram"]["launches_with_work"] == 23 and out["spmm_gram"]["noop_launches"] == 9
+    assert out["spmm_gram"]["est_total_ms"] == pytest.approx(2.0 * 23)
+    assert out["apply_fields"]["est_total_ms"] == pytest.approx(1.0)
+    r = bench.roofline(kt, N, S, M, PEAKS, real_launches={"spmm_gram": 23})
+    assert r["launches_with_work"] == 23 and r["share_of_kernel_time"] == pytest.approx(46.0 / 47.0, abs=1e-3)
+
+
+def test_fused_entry_counts_both_field_writes():
+    kt = {"combine_apply": (2.0, 2, 2)}   # 1 ms per launch
+    e = bench.hbm_entry("combine_apply", kt, N, S, M, PEAKS)
+    assert e["achieved"] == pytest.approx(8 * N * M / 1e-3 / 1e9, abs=0.1)
+    assert bench.hbm_entry("combine_apply", {}, N, S, M, PEAKS) is None
+
+
+def test_fno_flop_model_pieces():
+    from paper_2510_23221_gb300 import fno
+    # no Fourier layers: lifting and projection only
+    sh = fno.FnoShape(nx=8, ny=4, nz=2, c_in=5, width=32, hidden=128, layers=0, mx=4, my=4, mz=2)
+    n = 8 * 4 * 2
+    assert bench.fno_flops(sh) == n * 32 * 5 * 2 + n * (32 * 128 * 2 + 128 * 2)
+    # each layer adds the same amount, which grows with the retained modes
+    one = bench.fno_flops(fno.FnoShape(nx=8, ny=4, nz=2, layers=1, mx=4, my=4, mz=2))
+    two = bench.fno_flops(fno.FnoShape(nx=8, ny=4, nz=2, layers=2, mx=4, my=4, mz=2))
+    more = bench.fno_flops(fno.FnoShape(nx=8, ny=4, nz=2, layers=1, mx=8, my=4, mz=2))
+    assert two - one == one - bench.fno_flops(fno.FnoShape(nx=8, ny=4, nz=2, layers=0, mx=4, my=4, mz=2))
+    assert more > one
+
+
+def test_spread_fields():
+    f = bench.spread(5000, 32, shift=37)
+    assert len(f) == 32 and f.min() >= 0 and f.max() < 5000
+    assert len(bench.spread(10, 32)) == 10

@@ -358,6 +358,48 @@ def test_fno_basis_scales_and_transposes():
         assert np.array_equal(got[off * s:(off + n) * s].reshape(n, s), ref)
 
 
+@pytest.mark.parametrize("case", ["mixed_small", "chip128_ragged_M", "wide_rows_fallback"])
+def test_fused_combine_apply_matches_the_two_calls(case):
+    """blockoa_combine_apply: T bitwise equal to blockoa_combine's, q within
+    float32 rounding of blockoa_apply_operator on that T, and against the
+    oracle: e_T to U C and e_pair with the oracle's operator."""
+    if case == "mixed_small":
+        chips = [synth.random_small_chip(57, 37, 21, 3), synth.reference_stack_chip(),
+                 synth.random_small_chip(58, 5, 9, 4, h_top=3e4, h_bottom=2e3, h_side=5e2)]
+        s, M = 17, 131
+    elif case == "chip128_ragged_M":
+        chips = [synth.random_small_chip(59, 128, 16, 4)]
+        s, M = 32, 65
+    else:
+        chips = [synth.random_small_chip(60, 150, 6, 2), synth.random_small_chip(61, 9, 7, 3)]
+        s, M = 8, 70
+    rng = np.random.default_rng(56)
+    op = bo.assemble(chips)
+    Us = [rng.standard_normal((c.n, s)) for c in chips]
+    Cs = [synth.coefficients(rng, s, M) for _ in chips]
+    Ud = cuda(np.concatenate([u.ravel() for u in Us]))
+    Cd = cuda(np.concatenate([c.ravel() for c in Cs]))
+    T1 = torch.empty(M * op.n_total, dtype=torch.float32, device="cuda")
+    q1 = torch.empty_like(T1)
+    bo.combine(op, Ud, Cd, T1, s, M, bo.MIXED)
+    bo.apply_operator(op, T1, q1, M, bo.MIXED)
+    T2 = torch.full_like(T1, float("nan"))
+    q2 = torch.full_like(T1, float("nan"))
+    bo.combine_apply(op, Ud, Cd, T2, q2, s, M)
+    assert torch.equal(T1, T2)
+    q1h, q2h = q1.cpu().numpy().astype(np.float64), q2.cpu().numpy().astype(np.float64)
+    T2h = T2.cpu().numpy().astype(np.float64)
+    for c, chip in enumerate(chips):
+        off, n = op.sizes[c]["off"], op.sizes[c]["n"]
+        a = q1h[off * M:(off + n) * M].reshape(M, n)
+        b = q2h[off * M:(off + n) * M].reshape(M, n)
+        assert np.all(relcols(b, a, axis=1) < 2e-6)
+        A = orc.assemble(chip)
+        Tc = T2h[off * M:(off + n) * M].reshape(M, n)
+        e = orc.pair_errors(A, Us[c], Cs[c], Tc, b)
+        assert e["e_T"].max() <= 1e-6 and e["e_pair"].max() <= 1e-6, (e["e_T"].max(), e["e_pair"].max())
+
+
 def test_apply_basis_rejects_bad_arguments():
     op = bo.assemble([synth.random_small_chip(8, 5, 4, 2)])
     with pytest.raises(bo.BlockoaError):
