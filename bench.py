@@ -271,6 +271,38 @@ def hbm_entry(name: str, kt: dict, n: int, s: int, M: int, peaks: dict):
             "peak_source": "measured copy (MEASURED_PEAKS.json)"}
 
 
+# Streaming bytes per cell of one launch of each loop kernel of the chosen
+# (mixed, two-step z-line) form on a single chip, S the padded block width:
+# every float32 block vector it reads or writes touched once, plus the
+# float32 coefficients (16 B per cell) and z-line pivots (4 B per cell).
+LOOP_STREAM_BYTES = {
+    "spmm_gram": lambda S: 12 * S + 16,        # read P, R; write Q
+    "update_gram": lambda S: 28 * S + 20,      # read P, Q, X, R; write X, R, Z1
+    "zline_second": lambda S: 16 * S + 20,     # read Z1, R, Q; write Z
+    "p_update": lambda S: 12 * S,              # read Z, P; write P
+}
+
+
+def loop_hbm(kt: dict, n: int, s: int, peaks: dict):
+    """Effective bandwidth of the loop kernels on one chip (streaming bytes
+    per launch over the average timed launch) against the measured copy
+    peak.  Blocks that fit L2 (the 128 x 128 x 8 chip) read as effective
+    rates only; on larger chips the bytes come from HBM."""
+    S = 8 if s <= 8 else 16 if s <= 16 else 32 if s <= 32 else 64
+    peak = peaks.get("hbm_gbs", 6800.0)
+    out = {}
+    for name, per_cell in LOOP_STREAM_BYTES.items():
+        if name not in kt or kt[name][1] == 0:
+            continue
+        ms, cnt, _ = kt[name]
+        avg = ms / cnt / 1e3
+        b = n * per_cell(S)
+        gbs = b / avg / 1e9
+        out[name] = {"bytes": int(b), "avg_us": round(avg * 1e6, 2), "GBps": round(gbs, 1),
+                     "frac": round(gbs / peak, 4)}
+    return out
+
+
 def kernel_timing_report(kt: dict, real_launches: dict):
     """Per-kernel live timings; loop kernels also report the launches that did
     work (one per block iteration) and the total those imply, apart from the
@@ -553,6 +585,7 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": int(launches),
             "roofline": roof, "roofline_combine_apply": fused_roof, "cpu_baseline": cpu, "clocks": clk,
             "kernel_timing": kernel_timing_report(kt_sum, real_launches),
+            "loop_kernels_hbm": loop_hbm(kt_sum, n, s, peaks),
             "configs": suite,
             "wall_s_timed": round(wall_s, 3),
         }
@@ -649,6 +682,7 @@ def run_suite(peaks, flush):
                  "roofline_apply": hbm_entry("apply_fields", kt, n, s, chunk, peaks),
                  "roofline_combine": hbm_entry("combine_tc", kt, n, s, chunk, peaks),
                  "roofline_combine_apply": hbm_entry("combine_apply", kt, n, s, chunk, peaks),
+                 "loop_kernels_hbm": loop_hbm(kt, n, s, peaks) if op.n_chips == 1 else None,
                  "_dev": {"w": w, "U": U, "T": T, "q": q, "op": op, "chunk": chunk}}
         return entry
 

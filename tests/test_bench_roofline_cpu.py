@@ -112,3 +112,16 @@ def test_spread_fields():
     f = bench.spread(5000, 32, shift=37)
     assert len(f) == 32 and f.min() >= 0 and f.max() < 5000
     assert len(bench.spread(10, 32)) == 10
+
+
+def test_loop_kernel_streaming_bandwidth():
+    # 4,194,304 cells at s = 64 (S = 64): spmm_gram reads P and R and writes
+    # Q (12 S bytes per cell) plus 16 B of coefficients
+    n, s = 4_194_304, 64
+    kt = {"spmm_gram": (4.0, 2, 2), "p_update": (1.0, 1, 1), "alpha_solve": (1.0, 1, 1)}
+    out = bench.loop_hbm(kt, n, s, {"hbm_gbs": 7000.0})
+    assert set(out) == {"spmm_gram", "p_update"}
+    b = n * (12 * 64 + 16)
+    assert out["spmm_gram"]["bytes"] == b
+    assert abs(out["spmm_gram"]["GBps"] - b / 2e-3 / 1e9) < 0.1
+    assert abs(out["p_update"]["frac"] - n * 12 * 64 / 1e-3 / 1e9 / 7000.0) < 1e-4
