@@ -258,8 +258,7 @@ __device__ __forceinline__ double f2d_exact(float f) {
 // Add a compensated float32 pair hi + lo (|lo| <= ulp(hi) / 2) to a float64
 // accumulator: two atomics of exact conversions, no float64 arithmetic.
 __device__ __forceinline__ void atomic_add_pair(double *dst, float hi, float lo) {
-  atomicAdd(dst, f2d_exact(hi));
-  if (lo != 0.f) atomicAdd(dst, f2d_exact(lo));
+  atomicAdd(dst, f2d_exact(hi) + f2d_exact(lo));
 }
 
 // Reduce the NG groups' 4x4 blocks in shared memory and add the S x S
@@ -346,28 +345,55 @@ struct UnitSched {
   int *work;                  // [0] next unit, [1] CTAs finished (zero between launches)
 };
 
+// Thread 0's scheduling registers: the unit fetched ahead, and the last
+// chip whose active flag it read, as 2 chip + flag (flags do not change
+// while a loop kernel runs: a chip is switched off only after its last
+// unit of the launch).
+struct SchedLocal {
+  int pend = -1, ck = -1;
+};
+// The unit handed to the CTA and its chip's geometry, published in shared
+// memory by thread 0 (the geometry is read from global memory only when
+// the chip changes; ch_id is the chip it belongs to).
+struct UnitSlot {
+  Unit u;
+  ChipDev ch;
+  int ui, ch_id;
+};
+
 // Next unit of the calling CTA (n_units when none is left).  Thread 0
 // fetches one unit ahead: the atomic for the following unit is issued here
-// and its value (kept in `pend`, thread 0's register) is used at the next
-// call, so the round trip to the counter overlaps the current unit's work
-// instead of stalling the CTA at every unit.
-__device__ __forceinline__ int next_unit(const UnitSched &us, const ChipSolveState *state, int *slot,
-                                         int &pend) {
+// and its value (kept in `sl.pend`) is used at the next call, so the round
+// trip to the counter overlaps the current unit's work instead of stalling
+// the CTA at every unit.  Thread 0 also publishes the unit's record (and,
+// given `chips`, its chip's geometry) in shared memory and reads a chip's
+// active flag once per chip, so the CTA's threads start on the unit
+// without global round trips of their own.
+__device__ __forceinline__ int next_unit(const UnitSched &us, const ChipSolveState *state, UnitSlot *slot,
+                                         SchedLocal &sl, const ChipDev *chips = nullptr) {
   __syncthreads();   // every thread has read the previous value
   if (threadIdx.x == 0) {
-    int ui = pend >= 0 ? pend : atomicAdd(&us.work[0], 1);
+    if (sl.pend < 0) slot->ch_id = -1;   // first call of the launch
+    int ui = sl.pend >= 0 ? sl.pend : atomicAdd(&us.work[0], 1);
+    Unit u{};
     for (;;) {
       if (ui >= us.n_units) break;
-      const int chip = us.units[ui].chip;
-      if (state[chip].active) break;
-      atomicMax(&us.work[0], us.chip_unit_end[chip]);   // skip the rest of this chip
+      u = us.units[ui];
+      if ((sl.ck >> 1) != u.chip) sl.ck = 2 * u.chip + (state[u.chip].active ? 1 : 0);
+      if (sl.ck & 1) break;
+      atomicMax(&us.work[0], us.chip_unit_end[u.chip]);   // skip the rest of this chip
       ui = atomicAdd(&us.work[0], 1);
     }
-    *slot = ui;
-    pend = ui < us.n_units ? atomicAdd(&us.work[0], 1) : us.n_units;
+    slot->u = u;
+    slot->ui = ui;
+    if (chips && ui < us.n_units && u.chip != slot->ch_id) {
+      slot->ch = chips[u.chip];
+      slot->ch_id = u.chip;
+    }
+    sl.pend = ui < us.n_units ? atomicAdd(&us.work[0], 1) : us.n_units;
   }
   __syncthreads();
-  return *slot;
+  return slot->ui;
 }
 
 // Every CTA calls this once its loop is over; the last one resets the
@@ -462,7 +488,7 @@ spmm_gram_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T 
   T *sQ = sP + S * G::LD;
   T *sR = sQ + S * G::LD;
   double *red = reinterpret_cast<double *>(smem);   // reused between units
-  __shared__ int s_unit;
+  __shared__ UnitSlot s_unit;
   grid_release_next();
   grid_wait_prior();
   const int t = threadIdx.x;
@@ -478,10 +504,10 @@ spmm_gram_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T 
 #pragma unroll
   for (int e = 0; e < NA; ++e) acc[e] = T(0);
   int cur = -1, run = 0;   // chip of the running accumulation and its units
-  int pend = -1;   // thread 0: the unit fetched ahead
+  SchedLocal sl;   // thread 0: the unit fetched ahead, the last chip checked
   for (;;) {
-    const int ui = next_unit(us, A.state, &s_unit, pend);
-    const int chip = ui < us.n_units ? us.units[ui].chip : -1;
+    const int ui = next_unit(us, A.state, &s_unit, sl, chips);
+    const int chip = ui < us.n_units ? s_unit.u.chip : -1;
     if (run > 0 && chip != cur) {   // flush the running chip
       if constexpr (SPLIT) {
         gram_flush_split<T, S>(acc, red, A.gram + (long long)cur * S * S, A.rho + (long long)cur * S * S, A.diag);
@@ -498,10 +524,10 @@ spmm_gram_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T 
       run = 0;
     }
     if (ui >= us.n_units) break;
-    const Unit u = us.units[ui];
+    const Unit u = s_unit.u;
     cur = u.chip;
     ++run;
-    const ChipDev ch = chips[u.chip];
+    const ChipDev ch = s_unit.ch;
     const int nx = ch.nx, ny = ch.ny, nz = ch.nz, nxny = nx * ny;
     for (long long base = u.begin; base < u.end; base += G::TC) {
       T pc[4][V], qv[4][V], rv[4][V];
@@ -592,7 +618,7 @@ update_gram_kernel(const UnitSched us, const T *__restrict__ P, const T *__restr
   T *sR = sQ + S * G::LD;
   T *sA = sR + S * G::LD;
   double *red = reinterpret_cast<double *>(smem);   // reused between units
-  __shared__ int s_unit;
+  __shared__ UnitSlot s_unit;
   grid_release_next();
   grid_wait_prior();
   const int t = threadIdx.x;
@@ -605,10 +631,10 @@ update_gram_kernel(const UnitSched us, const T *__restrict__ P, const T *__restr
 #pragma unroll
   for (int v = 0; v < V; ++v) rn[v] = T(0);
   int cur = -1, run = 0;
-  int pend = -1;   // thread 0: the unit fetched ahead
+  SchedLocal sl;   // thread 0: the unit fetched ahead, the last chip checked
   for (;;) {
-    const int ui = next_unit(us, A.state, &s_unit, pend);
-    const int chip = ui < us.n_units ? us.units[ui].chip : -1;
+    const int ui = next_unit(us, A.state, &s_unit, sl);
+    const int chip = ui < us.n_units ? s_unit.u.chip : -1;
     if (run > 0 && chip != cur) {   // flush the running chip
       update_flush<T, S>(aw, rn, red, A, cur);
       // mixed form: the flush that completes the chip forms beta and tests convergence
@@ -623,7 +649,7 @@ update_gram_kernel(const UnitSched us, const T *__restrict__ P, const T *__restr
       run = 0;
     }
     if (ui >= us.n_units) break;
-    const Unit u = us.units[ui];
+    const Unit u = s_unit.u;
     if (u.chip != cur) {   // alpha of the chip (the tiles below read sA after a barrier)
       const T *al = reinterpret_cast<const T *>(A.alpha) + (long long)u.chip * S * S;
       for (int e = t; e < S * S; e += 256) sA[e] = al[e];
@@ -691,17 +717,17 @@ p_update_kernel(const UnitSched us, const ChipSolveState *__restrict__ state, co
   extern __shared__ __align__(16) unsigned char smem[];
   T *sP = reinterpret_cast<T *>(smem);
   T *sB = sP + S * G::LD;
-  __shared__ int s_unit;
+  __shared__ UnitSlot s_unit;
   grid_release_next();
   grid_wait_prior();
   const int t = threadIdx.x;
   const int j0 = (t % G::TPR) * V, cl0 = (t / G::TPR) * 4;
   int cur = -1;
-  int pend = -1;   // thread 0: the unit fetched ahead
+  SchedLocal sl;   // thread 0: the unit fetched ahead, the last chip checked
   for (;;) {
-    const int ui = next_unit(us, state, &s_unit, pend);
+    const int ui = next_unit(us, state, &s_unit, sl);
     if (ui >= us.n_units) break;
-    const Unit u = us.units[ui];
+    const Unit u = s_unit.u;
     if (u.chip != cur) {   // beta of the chip (read after the tile barrier)
       const T *be = beta + (long long)u.chip * S * S;
       for (int e = t; e < S * S; e += 256) sB[e] = be[e];
@@ -1158,7 +1184,7 @@ update_zline_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const
   T *sF = sE + G::TC;
   T *sI = sF + G::TC;
   double *red = reinterpret_cast<double *>(smem);   // reused between units
-  __shared__ int s_unit;
+  __shared__ UnitSlot s_unit;
   grid_release_next();
   grid_wait_prior();
   const int t = threadIdx.x;
@@ -1171,10 +1197,10 @@ update_zline_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const
 #pragma unroll
   for (int v = 0; v < V; ++v) rn[v] = T(0);
   int cur = -1, run = 0;
-  int pend = -1;   // thread 0: the unit fetched ahead
+  SchedLocal sl;   // thread 0: the unit fetched ahead, the last chip checked
   for (;;) {
-    const int ui = next_unit(us, A.state, &s_unit, pend);
-    const int chip = ui < us.n_units ? us.units[ui].chip : -1;
+    const int ui = next_unit(us, A.state, &s_unit, sl, chips);
+    const int chip = ui < us.n_units ? s_unit.u.chip : -1;
     if (run > 0 && chip != cur) {
       update_flush<T, S>(aw, rn, red, A, cur, !TWO);
       if constexpr (sizeof(T) == 4 && !TWO) {
@@ -1188,14 +1214,14 @@ update_zline_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const
       run = 0;
     }
     if (ui >= us.n_units) break;
-    const Unit u = us.units[ui];
+    const Unit u = s_unit.u;
     if (u.chip != cur) {
       const T *al = reinterpret_cast<const T *>(A.alpha) + (long long)u.chip * S * S;
       for (int e = t; e < S * S; e += 256) sA[e] = al[e];
     }
     cur = u.chip;
     ++run;
-    const ChipDev ch = chips[u.chip];
+    const ChipDev ch = s_unit.ch;
     const ColGeom cg(ch, G::TC);
     // (z, dx) of this thread's four slots and of its tridiagonal-factor slot
     int sz[4], sdx[4];
@@ -1318,7 +1344,7 @@ zline2_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T *__
   T *sF = sE + G::TC;
   T *sI = sF + G::TC;
   double *red = reinterpret_cast<double *>(smem);   // reused between units
-  __shared__ int s_unit;
+  __shared__ UnitSlot s_unit;
   grid_release_next();
   grid_wait_prior();
   const int t = threadIdx.x;
@@ -1329,10 +1355,10 @@ zline2_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T *__
 #pragma unroll
   for (int e = 0; e < 16; ++e) aw[e] = T(0);
   int cur = -1, run = 0;
-  int pend = -1;   // thread 0: the unit fetched ahead
+  SchedLocal sl;   // thread 0: the unit fetched ahead, the last chip checked
   for (;;) {
-    const int ui = next_unit(us, A.state, &s_unit, pend);
-    const int chip = ui < us.n_units ? us.units[ui].chip : -1;
+    const int ui = next_unit(us, A.state, &s_unit, sl, chips);
+    const int chip = ui < us.n_units ? s_unit.u.chip : -1;
     if constexpr (!INIT) {
       if (run > 0 && chip != cur) {
         gram_flush<T, S>(aw, red, A.wg + (long long)cur * S * S, A.diag);
@@ -1346,10 +1372,10 @@ zline2_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T *__
       }
     }
     if (ui >= us.n_units) break;
-    const Unit u = us.units[ui];
+    const Unit u = s_unit.u;
     cur = u.chip;
     ++run;
-    const ChipDev ch = chips[u.chip];
+    const ChipDev ch = s_unit.ch;
     const ColGeom cg(ch, G::TC);
     const long long nxny = (long long)ch.nx * ch.ny;
     int sz[4], sdx[4];
