@@ -595,8 +595,8 @@ __device__ __forceinline__ void update_flush(const T *aw, const T *rn, double *r
         lo += (hi - (s2 - bp)) + (x - bp);
         hi = s2;
       }
-      if constexpr (sizeof(T) == 4) atomic_add_pair(A.rn2 + (long long)c * S + t * V + v, hi, lo);
-      else atomicAdd(A.rn2 + (long long)c * S + t * V + v, (double)hi + (double)lo);
+      if constexpr (sizeof(T) == 4) atomic_add_pair(A.rn2 + rn2_at(c, S, t * V + v), hi, lo);
+      else atomicAdd(A.rn2 + rn2_at(c, S, t * V + v), (double)hi + (double)lo);
     }
   }
   __syncthreads();
@@ -1792,7 +1792,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     BLOCKOA_CUDA(ws_alloc(ws, &ws->perm, sizeof(int) * (size_t)nc * S));
     BLOCKOA_CUDA(ws_alloc(ws, &ws->alpha, sizeof(T) * (size_t)nc * S * S));
     BLOCKOA_CUDA(ws_alloc(ws, &ws->beta, sizeof(T) * (size_t)nc * S * S));
-    BLOCKOA_CUDA(ws_alloc(ws, &ws->rn2, sv));
+    BLOCKOA_CUDA(ws_alloc(ws, &ws->rn2, sv * kRn2Stride));
     BLOCKOA_CUDA(ws_alloc(ws, &ws->rn64, sv));
     BLOCKOA_CUDA(ws_alloc(ws, &ws->bn2, sv));
     BLOCKOA_CUDA(ws_alloc(ws, &ws->target2, sv));
@@ -1908,7 +1908,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     BLOCKOA_CUDA(cudaMemset(ws->gram, 0, sm));
     BLOCKOA_CUDA(cudaMemset(ws->rho, 0, sm));
     BLOCKOA_CUDA(cudaMemset(ws->wg, 0, sm));
-    BLOCKOA_CUDA(cudaMemset(ws->rn2, 0, sv));
+    BLOCKOA_CUDA(cudaMemset(ws->rn2, 0, sv * kRn2Stride));
     BLOCKOA_CUDA(cudaMemset(ws->ginv, 0, sm));
     BLOCKOA_CUDA(cudaMemset(ws->rank, 0, sizeof(int) * (size_t)nc));
   }
@@ -2061,7 +2061,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       BLOCKOA_CUDA(cudaMemsetAsync(ws->gram, 0, sm, st));
       BLOCKOA_CUDA(cudaMemsetAsync(ws->rho, 0, sm, st));
       BLOCKOA_CUDA(cudaMemsetAsync(ws->wg, 0, sm, st));
-      BLOCKOA_CUDA(cudaMemsetAsync(ws->rn2, 0, sv, st));
+      BLOCKOA_CUDA(cudaMemsetAsync(ws->rn2, 0, sv * kRn2Stride, st));
       BLOCKOA_CUDA(cudaMemsetAsync(ws->ticket, 0, sizeof(int) * 2 * (size_t)nc, st));
       BLOCKOA_CUDA(cudaMemsetAsync(ws->work, 0, sizeof(int) * 8, st));
     }

@@ -41,12 +41,21 @@
 
 namespace blockoa {
 
+// The ||R_j||^2 accumulators receive one float64 atomic per column from
+// every CTA of the update pass; one cache line per entry spreads them over
+// L2 slices (packed, a chip's S entries share one or two lines, and the
+// few hundred CTAs' atomics queue at those lines' slices).
+constexpr int kRn2Stride = 16;
+__host__ __device__ __forceinline__ long long rn2_at(int c, int S, int j) {
+  return ((long long)c * S + j) * kRn2Stride;
+}
+
 struct SmallArgs {
   ChipSolveState *state;
   double *gram;     // [chip][S][S] Gamma accumulator
   double *rho;      // [chip][S][S] rho = P^T R accumulator
   double *wg;       // [chip][S][S] W = Q^T Z accumulator
-  double *rn2;      // [chip][S] ||R_j||^2 accumulator
+  double *rn2;      // [chip][S][kRn2Stride] ||R_j||^2 accumulator (entry (c, j) at rn2_at)
   const double *target2;  // [chip][S] squared per-column targets
   void *ginv;       // [chip][S][S] (G_KK)^-1, zero outside K (small-solve arithmetic type);
                     //   float64 form: substitution factors F
@@ -504,13 +513,13 @@ __device__ __noinline__ void chip_beta(const SmallArgs &A, int c) {
   if (warp == 0) {
     int conv = 1, bad = 0;
     for (int i = t; i < S; i += 32) {
-      const double v = __ldcg(A.rn2 + (long long)c * S + i);
+      const double v = __ldcg(A.rn2 + rn2_at(c, S, i));
       if (!isfinite(v)) bad = 1;
       if (!(v <= A.target2[(long long)c * S + i])) conv = 0;
     }
     conv = __all_sync(0xffffffffu, conv);
     bad = __any_sync(0xffffffffu, bad);
-    for (int i = t; i < S; i += 32) A.rn2[(long long)c * S + i] = 0.0;   // consumed
+    for (int i = t; i < S; i += 32) A.rn2[rn2_at(c, S, i)] = 0.0;   // consumed
     if (t == 0) {
       st.iters += 1;
       if (bad) {

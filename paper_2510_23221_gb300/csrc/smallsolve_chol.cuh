@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kCholThreads) chol_alpha_kernel(SmallArgs A) {
   }
   if (j == 0) {   // W and ||R||^2 of the previous iteration were read by its beta solve
     for (int e = t; e < S * S; e += kCholThreads) A.wg[(long long)c * S * S + e] = 0.0;
-    if (t < S) A.rn2[(long long)c * S + t] = 0.0;
+    if (t < S) A.rn2[rn2_at(c, S, t)] = 0.0;
   }
   __syncthreads();
   {   // strict lower part of D (Gamma + Gamma^T) / 2 D; non-finite entries fail the chip
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(kCholThreads) chol_beta_kernel(SmallArgs A) {
   if (t >= 32) return;
   int conv = 1, bad = 0;
   for (int i = t; i < S; i += 32) {
-    const double v = A.rn2[(long long)c * S + i];
+    const double v = A.rn2[rn2_at(c, S, i)];
     if (!isfinite(v)) bad = 1;
     if (!(v <= A.target2[(long long)c * S + i])) conv = 0;
   }

@@ -713,7 +713,7 @@ int launch_residual_ratio(const blockoa_operator *op, const double *B, const dou
 
 int launch_residual64(const blockoa_operator *op, const double *B, const double *X, double *R,
                       int S, double *rn2, cudaStream_t st) {
-  std::vector<Unit> units = make_units(op, 1024);
+  std::vector<Unit> units = make_units(op, 512);   // float64-bound: enough CTAs for every SM
   blockoa_operator *mop = const_cast<blockoa_operator *>(op);
   void *d_units = nullptr;
   int rc = pool_alloc(mop, &d_units, sizeof(Unit) * units.size(), st);
