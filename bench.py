@@ -455,6 +455,10 @@ def run_ours(args):
     dfloat = variant(dict(CHOSEN, small_solve=bo.SMALL_AUTO), torch.float32, max(args.plain_steps, 2))
     if dfloat:
         dfloat["form"] = "chosen form with double-float (~48-bit) s x s sweeps in the Gram kernels' tails"
+    detf = variant(dict(CHOSEN, deterministic=True), torch.float32, max(args.plain_steps, 3))
+    if detf:
+        detf["form"] = ("chosen form, deterministic (static unit schedules, partial sums reduced in a fixed "
+                        "order): the iteration counts and bits repeat from step to step")
 
     # ---- the fused combination + operator action beside the two calls it
     # replaces, on the last step's basis (pairs verified like the headline's)
@@ -581,7 +585,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "verification": verification,
             "plain_fp64": plain, "fp64_zline2": fp64_z2, "chosen_double_float_small_solves": dfloat,
-            "fused_combine_apply": fused,
+            "fused_combine_apply": fused, "chosen_deterministic": detf,
             "e2e": e2e, "gpu_launches": int(launches),
             "roofline": roof, "roofline_combine_apply": fused_roof, "cpu_baseline": cpu, "clocks": clk,
             "kernel_timing": kernel_timing_report(kt_sum, real_launches),

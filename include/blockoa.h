@@ -101,6 +101,16 @@ typedef struct {
                            baseline: every off-diagonal entry of Gamma, P^T R and
                            Q^T Z is dropped, so alpha_jj = (p_j . r_j) / (p_j . A p_j)
                            and beta_jj = -(A p_j . z_j) / (p_j . A p_j) */
+  int deterministic;    /* 0: the loop kernels' partial sums reach the float64
+                           accumulators by atomics in whatever order the CTAs
+                           finish (results can differ in the last bits, and the
+                           iteration count by a few, from run to run);
+                           1: bitwise reproducible on a given GPU and operator --
+                           static unit schedules, every partial sum stored and
+                           reduced in a fixed order (the stencil pass, the
+                           update, the second z-line step, ||B_j||^2 and the
+                           float64 residual), float64 Cholesky small solves;
+                           two or three more kernel launches per iteration */
 } blockoa_solve_opts;
 
 enum { BLOCKOA_PRECOND_NONE = 0, BLOCKOA_PRECOND_JACOBI = 1, BLOCKOA_PRECOND_ZLINE = 2,

@@ -74,7 +74,7 @@ class SolveOpts(ct.Structure):
                 ("inner_rtol", ct.c_double), ("max_refine", ct.c_int),
                 ("deflate_tol", ct.c_double), ("x0", ct.c_void_p), ("check_every", ct.c_int),
                 ("precond", ct.c_int),
-                ("small_solve", ct.c_int), ("independent", ct.c_int)]
+                ("small_solve", ct.c_int), ("independent", ct.c_int), ("deterministic", ct.c_int)]
 
 
 class SolveStats(ct.Structure):
@@ -298,13 +298,14 @@ class Stats:
 def block_solve(op: Operator, B, X, s: int, rtol: float = 1e-12, maxiter: int = 100000,
                 precision: int = FP64, inner_rtol: float = 0.0, max_refine: int = 0,
                 deflate_tol: float = 0.0, x0=None, check_every: int = 0, precond: int = PRECOND_NONE,
-                small_solve: int = SMALL_AUTO, independent: bool = False,
+                small_solve: int = SMALL_AUTO, independent: bool = False, deterministic: bool = False,
                 stream=None, raise_on_error: bool = True) -> List[Stats]:
     import torch
     o = SolveOpts(rtol=rtol, maxiter=maxiter, precision=precision, inner_rtol=inner_rtol,
                   max_refine=max_refine, deflate_tol=deflate_tol,
                   x0=_ptr(x0, torch.float64, "x0", op.n_total * s), check_every=check_every, precond=precond,
-                  small_solve=small_solve, independent=int(bool(independent)))
+                  small_solve=small_solve, independent=int(bool(independent)),
+                  deterministic=int(deterministic))
     st = (SolveStats * op.n_chips)()
     code = _lib().blockoa_block_solve(op.handle, _ptr(B, torch.float64, "B", op.n_total * s),
                                       _ptr(X, torch.float64, "X", op.n_total * s), s, ct.byref(o), st,

@@ -261,6 +261,21 @@ __device__ __forceinline__ void atomic_add_pair(double *dst, float hi, float lo)
   atomicAdd(dst, f2d_exact(hi) + f2d_exact(lo));
 }
 
+// Where a flush puts its per-entry partial sums: added to the chip's
+// float64 accumulator by atomics (entry e at acc[e * stride]), or, in a
+// deterministic solve, stored in the CTA's slot (entry e at slot[e]) for a
+// reduction in a fixed order (ordered_reduce_kernel).
+struct Sink {
+  double *acc;
+  double *slot;
+  int stride;
+  __device__ __forceinline__ void put(int e, double v) const {
+    if (slot) slot[e] = v;
+    else atomicAdd(acc + (long long)e * stride, v);
+  }
+};
+__device__ __forceinline__ Sink sink(double *acc, double *slot, int stride = 1) { return Sink{acc, slot, stride}; }
+
 // Reduce the NG groups' 4x4 blocks in shared memory and add the S x S
 // result to the chip's float64 accumulator.  float partial sums (each over
 // at most a few hundred cells of one CTA) are combined across groups with
@@ -268,7 +283,7 @@ __device__ __forceinline__ void atomic_add_pair(double *dst, float hi, float lo)
 // one float64 atomic per CTA; float64 arithmetic runs at 1/64 of the float32
 // rate on this part.
 template <typename T, int S>
-__device__ void gram_flush(const T *acc, double *red, double *dst, bool diag) {
+__device__ void gram_flush(const T *acc, double *red, const Sink &dst, bool diag) {
   using G = BK<T, S>;
   const int t = threadIdx.x;
   const int g = t / G::NT, w = t % G::NT;
@@ -288,11 +303,11 @@ __device__ void gram_flush(const T *acc, double *red, double *dst, bool diag) {
         lo += (hi - (sum - bp)) + (v - bp);
         hi = sum;
       }
-      atomic_add_pair(dst + e, hi, lo);
+      dst.put(e, f2d_exact(hi) + f2d_exact(lo));
     } else {
       double sum = 0.0;
       for (int gg = 0; gg < G::NG; ++gg) sum += rt[gg * S * S + e];
-      atomicAdd(dst + e, sum);
+      dst.put(e, sum);
     }
   }
   __syncthreads();
@@ -300,7 +315,7 @@ __device__ void gram_flush(const T *acc, double *red, double *dst, bool diag) {
 
 // Flush when the first NG/2 groups hold P^T Q partials and the rest P^T R.
 template <typename T, int S>
-__device__ void gram_flush_split(const T *acc, double *red, double *dst_a, double *dst_b, bool diag) {
+__device__ void gram_flush_split(const T *acc, double *red, const Sink &dst_a, const Sink &dst_b, bool diag) {
   using G = BK<T, S>;
   const int t = threadIdx.x;
   const int g = t / G::NT, w = t % G::NT;
@@ -322,8 +337,8 @@ __device__ void gram_flush_split(const T *acc, double *red, double *dst_a, doubl
         lo += (hi - (sum - bp)) + (v - bp);
         hi = sum;
       }
-      if constexpr (sizeof(T) == 4) atomic_add_pair((half ? dst_b : dst_a) + e, hi, lo);
-      else atomicAdd((half ? dst_b : dst_a) + e, (double)hi + (double)lo);
+      if constexpr (sizeof(T) == 4) (half ? dst_b : dst_a).put(e, f2d_exact(hi) + f2d_exact(lo));
+      else (half ? dst_b : dst_a).put(e, (double)hi + (double)lo);
     }
   }
   __syncthreads();
@@ -343,7 +358,10 @@ struct UnitSched {
   int n_units;
   const int *chip_unit_end;   // [chip] index of the first unit past the chip
   int *work;                  // [0] next unit, [1] CTAs finished (zero between launches)
+  int stat;                   // 1: static schedule (deterministic solves): CTA b takes units b, b + G, ...
 };
+// First unit of chip c.
+__device__ __forceinline__ int unit0(const UnitSched &us, int c) { return c > 0 ? us.chip_unit_end[c - 1] : 0; }
 
 // Thread 0's scheduling registers: the unit fetched ahead, and the last
 // chip whose active flag it read, as 2 chip + flag (flags do not change
@@ -372,7 +390,27 @@ struct UnitSlot {
 __device__ __forceinline__ int next_unit(const UnitSched &us, const ChipSolveState *state, UnitSlot *slot,
                                          SchedLocal &sl, const ChipDev *chips = nullptr) {
   __syncthreads();   // every thread has read the previous value
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && us.stat) {   // static: units b, b + G, ... of active chips, in order
+    if (sl.pend < 0) slot->ch_id = -1;   // first call of the launch
+    const int G = (int)gridDim.x, b = (int)blockIdx.x;
+    int ui = sl.pend >= 0 ? sl.pend : b;
+    Unit u{};
+    while (ui < us.n_units) {
+      u = us.units[ui];
+      if ((sl.ck >> 1) != u.chip) sl.ck = 2 * u.chip + (state[u.chip].active ? 1 : 0);
+      if (sl.ck & 1) break;
+      const int e = us.chip_unit_end[u.chip];   // this CTA's first unit past the chip
+      ui = e + (((b - e) % G) + G) % G;
+    }
+    if (ui > us.n_units) ui = us.n_units;
+    slot->u = u;
+    slot->ui = ui;
+    if (chips && ui < us.n_units && u.chip != slot->ch_id) {
+      slot->ch = chips[u.chip];
+      slot->ch_id = u.chip;
+    }
+    sl.pend = ui < us.n_units ? ui + G : us.n_units;
+  } else if (threadIdx.x == 0) {
     if (sl.pend < 0) slot->ch_id = -1;   // first call of the launch
     int ui = sl.pend >= 0 ? sl.pend : atomicAdd(&us.work[0], 1);
     Unit u{};
@@ -400,7 +438,7 @@ __device__ __forceinline__ int next_unit(const UnitSched &us, const ChipSolveSta
 // counters for the next launch (no CTA fetches after it has finished).
 __device__ __forceinline__ void sched_finish(const UnitSched &us) {
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && !us.stat) {
     __threadfence();
     if (atomicAdd(&us.work[1], 1) == (int)gridDim.x - 1) {
       us.work[0] = 0;
@@ -503,17 +541,21 @@ spmm_gram_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T 
   T acc[NA];
 #pragma unroll
   for (int e = 0; e < NA; ++e) acc[e] = T(0);
-  int cur = -1, run = 0;   // chip of the running accumulation and its units
+  int cur = -1, run = 0, run_first = 0;   // chip of the running accumulation and its units
   SchedLocal sl;   // thread 0: the unit fetched ahead, the last chip checked
   for (;;) {
     const int ui = next_unit(us, A.state, &s_unit, sl, chips);
     const int chip = ui < us.n_units ? s_unit.u.chip : -1;
     if (run > 0 && chip != cur) {   // flush the running chip
+      double *slot = A.det_spmm ? A.det_spmm + (long long)(A.det_base[cur] + run_first - unit0(us, cur)) * 2 * S * S
+                                : nullptr;
+      const Sink sg = sink(A.gram + (long long)cur * S * S, slot);
+      const Sink sr = sink(A.rho + (long long)cur * S * S, slot ? slot + S * S : nullptr);
       if constexpr (SPLIT) {
-        gram_flush_split<T, S>(acc, red, A.gram + (long long)cur * S * S, A.rho + (long long)cur * S * S, A.diag);
+        gram_flush_split<T, S>(acc, red, sg, sr, A.diag);
       } else {
-        gram_flush<T, S>(acc, red, A.gram + (long long)cur * S * S, A.diag);
-        gram_flush<T, S>(acc + 16, red, A.rho + (long long)cur * S * S, A.diag);
+        gram_flush<T, S>(acc, red, sg, A.diag);
+        gram_flush<T, S>(acc + 16, red, sr, A.diag);
       }
       // mixed form: the flush that completes the chip sweeps Gamma and forms alpha
       if constexpr (sizeof(T) == 4) {
@@ -526,6 +568,7 @@ spmm_gram_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T 
     if (ui >= us.n_units) break;
     const Unit u = s_unit.u;
     cur = u.chip;
+    if (run == 0) run_first = ui;
     ++run;
     const ChipDev ch = s_unit.ch;
     const int nx = ch.nx, ny = ch.ny, nz = ch.nz, nxny = nx * ny;
@@ -575,11 +618,13 @@ spmm_gram_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T 
 // same columns).
 template <typename T, int S>
 __device__ __forceinline__ void update_flush(const T *aw, const T *rn, double *red, const SmallArgs &A, int c,
-                                             bool with_w = true) {
+                                             bool with_w, double *slot) {
   using G = BK<T, S>;
   constexpr int V = G::V;
   const int t = threadIdx.x;
-  if (with_w) gram_flush<T, S>(aw, red, A.wg + (long long)c * S * S, A.diag);
+  // slot layout of a deterministic solve: W (with_w), then ||R_j||^2
+  const Sink rs = sink(A.rn2 + rn2_at(c, S, 0), slot ? slot + (with_w ? S * S : 0) : nullptr, kRn2Stride);
+  if (with_w) gram_flush<T, S>(aw, red, sink(A.wg + (long long)c * S * S, slot), A.diag);
   T *rt = reinterpret_cast<T *>(red);
 #pragma unroll
   for (int v = 0; v < V; ++v) rt[t * V + v] = rn[v];
@@ -595,8 +640,8 @@ __device__ __forceinline__ void update_flush(const T *aw, const T *rn, double *r
         lo += (hi - (s2 - bp)) + (x - bp);
         hi = s2;
       }
-      if constexpr (sizeof(T) == 4) atomic_add_pair(A.rn2 + rn2_at(c, S, t * V + v), hi, lo);
-      else atomicAdd(A.rn2 + rn2_at(c, S, t * V + v), (double)hi + (double)lo);
+      if constexpr (sizeof(T) == 4) rs.put(t * V + v, f2d_exact(hi) + f2d_exact(lo));
+      else rs.put(t * V + v, (double)hi + (double)lo);
     }
   }
   __syncthreads();
@@ -630,13 +675,15 @@ update_gram_kernel(const UnitSched us, const T *__restrict__ P, const T *__restr
   for (int e = 0; e < 16; ++e) aw[e] = T(0);
 #pragma unroll
   for (int v = 0; v < V; ++v) rn[v] = T(0);
-  int cur = -1, run = 0;
+  int cur = -1, run = 0, run_first = 0;
   SchedLocal sl;   // thread 0: the unit fetched ahead, the last chip checked
   for (;;) {
     const int ui = next_unit(us, A.state, &s_unit, sl);
     const int chip = ui < us.n_units ? s_unit.u.chip : -1;
     if (run > 0 && chip != cur) {   // flush the running chip
-      update_flush<T, S>(aw, rn, red, A, cur);
+      update_flush<T, S>(aw, rn, red, A, cur, true,
+                         A.det_upd ? A.det_upd + (long long)(A.det_ubase[cur] + run_first - unit0(us, cur)) * (S * S + S)
+                                   : nullptr);
       // mixed form: the flush that completes the chip forms beta and tests convergence
       if constexpr (sizeof(T) == 4) {
         if (A.tail && last_flush_of_chip(A.ticket + A.n_chips + cur, run, A.unit_count[cur]))
@@ -655,6 +702,7 @@ update_gram_kernel(const UnitSched us, const T *__restrict__ P, const T *__restr
       for (int e = t; e < S * S; e += 256) sA[e] = al[e];
     }
     cur = u.chip;
+    if (run == 0) run_first = ui;
     ++run;
     for (long long base = u.begin; base < u.end; base += G::TC) {
       {
@@ -1196,13 +1244,16 @@ update_zline_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const
   for (int e = 0; e < 16; ++e) aw[e] = T(0);
 #pragma unroll
   for (int v = 0; v < V; ++v) rn[v] = T(0);
-  int cur = -1, run = 0;
+  int cur = -1, run = 0, run_first = 0;
   SchedLocal sl;   // thread 0: the unit fetched ahead, the last chip checked
   for (;;) {
     const int ui = next_unit(us, A.state, &s_unit, sl, chips);
     const int chip = ui < us.n_units ? s_unit.u.chip : -1;
     if (run > 0 && chip != cur) {
-      update_flush<T, S>(aw, rn, red, A, cur, !TWO);
+      update_flush<T, S>(aw, rn, red, A, cur, !TWO,
+                         A.det_upd ? A.det_upd + (long long)(A.det_ubase[cur] + run_first - unit0(us, cur)) *
+                                                     ((TWO ? 0 : S * S) + S)
+                                   : nullptr);
       if constexpr (sizeof(T) == 4 && !TWO) {
         if (A.tail && last_flush_of_chip(A.ticket + A.n_chips + cur, run, A.zunit_count[cur]))
           chip_beta<T, S>(A, cur);
@@ -1220,6 +1271,7 @@ update_zline_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const
       for (int e = t; e < S * S; e += 256) sA[e] = al[e];
     }
     cur = u.chip;
+    if (run == 0) run_first = ui;
     ++run;
     const ChipDev ch = s_unit.ch;
     const ColGeom cg(ch, G::TC);
@@ -1354,14 +1406,18 @@ zline2_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T *__
   T aw[16];
 #pragma unroll
   for (int e = 0; e < 16; ++e) aw[e] = T(0);
-  int cur = -1, run = 0;
+  int cur = -1, run = 0, run_first = 0;
   SchedLocal sl;   // thread 0: the unit fetched ahead, the last chip checked
   for (;;) {
     const int ui = next_unit(us, A.state, &s_unit, sl, chips);
     const int chip = ui < us.n_units ? s_unit.u.chip : -1;
     if constexpr (!INIT) {
       if (run > 0 && chip != cur) {
-        gram_flush<T, S>(aw, red, A.wg + (long long)cur * S * S, A.diag);
+        gram_flush<T, S>(aw, red,
+                         sink(A.wg + (long long)cur * S * S,
+                              A.det_z2 ? A.det_z2 + (long long)(A.det_zbase[cur] + run_first - unit0(us, cur)) * S * S
+                                       : nullptr),
+                         A.diag);
         if constexpr (sizeof(T) == 4) {
           if (A.tail && last_flush_of_chip(A.ticket + A.n_chips + cur, run, A.zunit_count[cur]))
             chip_beta<T, S>(A, cur);
@@ -1374,6 +1430,7 @@ zline2_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T *__
     if (ui >= us.n_units) break;
     const Unit u = s_unit.u;
     cur = u.chip;
+    if (run == 0) run_first = ui;
     ++run;
     const ChipDev ch = s_unit.ch;
     const ColGeom cg(ch, G::TC);
@@ -1447,6 +1504,58 @@ zline2_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T *__
   sched_finish(us);
 }
 
+// ---------------------------------------------------------------- ordered reduction
+// Deterministic solves: for every chip c (active ones, given `state`) and
+// entry e, the sum over k in [0, count[c]) of slots[(begin[c] + k) * n + e]
+// in an order fixed by the sizes alone -- lane l of the entry's warp adds
+// k = l, l + 32, ... in turn, then the 32 lane sums combine in a fixed
+// butterfly -- written to the entry's accumulator (mode: 0 Gamma then rho,
+// 1 ||R_j||^2, 2 W then ||R_j||^2, 3 W, 4 a plain [chip][S] vector).  In
+// independent-column solves the off-diagonal Gram entries are zero.
+__global__ void ordered_reduce_kernel(const double *__restrict__ slots, int n, const int *__restrict__ begin,
+                                      const int *__restrict__ count, const ChipSolveState *__restrict__ state,
+                                      int n_chips, int mode, int S, double *__restrict__ a, double *__restrict__ b,
+                                      int diag) {
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= (long long)n_chips * n) return;
+  const int c = (int)(wid / n), e = (int)(wid % n);
+  if (state && !state[c].active) return;
+  const double *p = slots + (long long)begin[c] * n + e;
+  double v = 0.0;
+  for (int k = lane; k < count[c]; k += 32) v += p[(long long)k * n];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    // the partner's value, added in lane order so both partners hold the same sum
+    const double w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = (lane & o) ? w + v : v + w;
+  }
+  if (lane != 0) return;
+  const int SS = S * S;
+  const bool gram_entry = (mode == 0) || ((mode == 2 || mode == 3) && e < SS);
+  if (diag && gram_entry) {
+    const int k = e % SS;
+    if (k / S != k % S) v = 0.0;
+  }
+  switch (mode) {
+    case 0: (e < SS ? a : b)[(long long)c * SS + (e % SS)] = v; break;
+    case 1: a[rn2_at(c, S, e)] = v; break;
+    case 2: if (e < SS) a[(long long)c * SS + e] = v; else b[rn2_at(c, S, e - SS)] = v; break;
+    case 3: a[(long long)c * SS + e] = v; break;
+    default: a[(long long)c * S + e] = v; break;
+  }
+}
+
+cudaError_t launch_ordered_reduce(const double *slots, int n, const int *begin, const int *count,
+                                  const ChipSolveState *state, int n_chips, int mode, int S, double *a, double *b,
+                                  int diag, cudaStream_t st) {
+  const long long threads = (long long)n_chips * n * 32;
+  const unsigned blocks = (unsigned)((threads + 255) / 256);
+  ordered_reduce_kernel<<<blocks, 256, 0, st>>>(slots, n, begin, count, state, n_chips, mode, S, a, b, diag);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- glue kernels
 // dst[a][j] = src[a][j] for j < s, 0 for s <= j < S (float64).
 __global__ void pad_cols_kernel(const double *__restrict__ src, double *__restrict__ dst,
@@ -1472,7 +1581,7 @@ __global__ void unpad_cols_kernel(const double *__restrict__ src, double *__rest
 // Squared column norms of a float64 block per chip: out[chip][j] += sum_a v^2.
 template <int S>
 __global__ void col_norms_kernel(const Unit *__restrict__ units, const double *__restrict__ V,
-                                 double *__restrict__ out) {
+                                 double *__restrict__ out, double *__restrict__ slot) {
   const Unit u = units[blockIdx.x];
   const int j = threadIdx.x % S;
   const int r0 = threadIdx.x / S;
@@ -1488,7 +1597,8 @@ __global__ void col_norms_kernel(const Unit *__restrict__ units, const double *_
   if (threadIdx.x < S) {
     double acc = 0.0;
     for (int k = threadIdx.x; k < 256; k += S) acc += red[k];
-    atomicAdd(out + (long long)u.chip * S + threadIdx.x, acc);
+    if (slot) slot[(long long)blockIdx.x * S + threadIdx.x] = acc;   // deterministic: ordered reduction
+    else atomicAdd(out + (long long)u.chip * S + threadIdx.x, acc);
   }
 }
 
@@ -1576,6 +1686,13 @@ struct SolveWS {
   cudaEvent_t tev[kMaxLoopKernels + 1] = {};   // recorded around the kernels of each chunk's first iteration
   int graph_iters = 0, graph_maxiter = -1, graph_s = -1, graph_pc = -1, graph_ch = -1, graph_diag = -1;
   double graph_tol = -1.0;
+  int graph_det = -1;
+  // deterministic solves (allocated by the first one): slot buffers and, per
+  // kernel, each chip's [first slot | slot count] ranges
+  std::vector<int> h_ucnt, h_zcnt, h_scnt;   // units per chip: loop, column-tile, elementwise
+  double *det_spmm = nullptr, *det_upd = nullptr, *det_z2 = nullptr, *det_small = nullptr;
+  int *det_rng_s = nullptr, *det_rng_u = nullptr, *det_rng_z = nullptr, *det_rng_small = nullptr;
+  int det_pc = -1;              // preconditioner the update slots were laid out for
   std::vector<void *> allocs;
 };
 
@@ -1707,12 +1824,23 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
   };
   auto launched = [&]() { chain = true; };
   mark();
-  const UnitSched us_s{ws->units, ws->n_units, ws->chip_unit_end, ws->work};
-  const UnitSched us_u{ws->units, ws->n_units, ws->chip_unit_end, ws->work + 2};
-  const UnitSched us_p{ws->units, ws->n_units, ws->chip_unit_end, ws->work + 4};
+  // deterministic solves: static schedules, and each Gram kernel's slots
+  // reduced in a fixed order right after it
+  const int det = sa.det_spmm != nullptr;
+  auto reduce = [&](const double *slots, int n, const int *rng, int mode, double *a, double *b) {
+    if (!det) return;
+    const long long threads = (long long)ws->n_chips * n * 32;
+    ordered_reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+        slots, n, rng, rng + ws->n_chips, ws->state, ws->n_chips, mode, S, a, b, sa.diag);
+    chain = false;
+  };
+  const UnitSched us_s{ws->units, ws->n_units, ws->chip_unit_end, ws->work, det};
+  const UnitSched us_u{ws->units, ws->n_units, ws->chip_unit_end, ws->work + 2, det};
+  const UnitSched us_p{ws->units, ws->n_units, ws->chip_unit_end, ws->work + 4, 0};
   launch_chained(spmm_gram_kernel<T, S>, ws->grid_spmm, 256, spmm_smem<T, S>(), st, chain,
                  us_s, op->d_chips, g, (const T *)ws->P, (const T *)ws->R, (T *)ws->Q, sa);
   launched();
+  reduce(ws->det_spmm, 2 * S * S, ws->det_rng_s, 0, ws->gram, ws->rho);
   if constexpr (CH) {
     mark();
     launch_chained(chol_alpha_kernel<T, S>, ws->n_chips * S, kCholThreads, chol_smem_bytes<S>(), st, chain, sa);
@@ -1720,24 +1848,31 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
   }
   mark();
   if constexpr (PCM == 2 || PCM == 3) {
-    const UnitSched us_z{ws->zunits, ws->n_zunits, ws->zchip_unit_end, ws->work + 2};
+    const UnitSched us_z{ws->zunits, ws->n_zunits, ws->zchip_unit_end, ws->work + 2, det};
     const T *zinv = sizeof(T) == 4 ? (const T *)op->zinv32 : (const T *)op->zinv64;
     launch_chained(update_zline_kernel<T, S, PCM == 3>, ws->grid_zupdate, 256, zupdate_smem<T, S>(), st, chain,
                    us_z, op->d_chips, g, zinv, (const T *)ws->P, (const T *)ws->Q, (T *)ws->D, (T *)ws->R,
                    (T *)ws->Zb, sa);
     if constexpr (PCM == 3) {   // second step: Zb2 = M^-1 (2 R - A Zb), W = Q^T Zb2, beta tail
       launched();
+      reduce(ws->det_upd, S, ws->det_rng_u, 1, ws->rn2, nullptr);
       mark();
-      const UnitSched us_z2{ws->zunits, ws->n_zunits, ws->zchip_unit_end, ws->work + 6};
+      const UnitSched us_z2{ws->zunits, ws->n_zunits, ws->zchip_unit_end, ws->work + 6, det};
       launch_chained(zline2_kernel<T, S, false>, ws->grid_z2, 256, zline2_smem<T, S>(), st, chain,
                      us_z2, op->d_chips, g, zinv, (const T *)ws->Zb, (const T *)ws->R, (const T *)ws->Q,
                      (T *)ws->Zb2, sa);
+      launched();
+      reduce(ws->det_z2, S * S, ws->det_rng_z, 3, ws->wg, nullptr);
+    } else {
+      launched();
+      reduce(ws->det_upd, S * S + S, ws->det_rng_u, 2, ws->wg, ws->rn2);
     }
   } else {
     launch_chained(update_gram_kernel<T, S, PCM>, ws->grid_update, 256, update_smem<T, S>(), st, chain,
                    us_u, (const T *)ws->P, (const T *)ws->Q, (T *)ws->D, (T *)ws->R, dinv, sa);
+    launched();
+    reduce(ws->det_upd, S * S + S, ws->det_rng_u, 2, ws->wg, ws->rn2);
   }
-  launched();
   if constexpr (CH) {
     mark();
     launch_chained(chol_beta_kernel<T, S>, ws->n_chips * S, kCholThreads, 0, st, chain, sa);
@@ -1759,6 +1894,56 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
                    us_p, ws->state, (const T *)ws->beta, (const T *)ws->R, (T *)ws->P, dinv, (const T *)zfin);
   launched();
   mark();
+}
+
+// Slot ranges of a persistent loop kernel with a static schedule: CTA b of
+// G takes units b, b + G, ..., so min(units, G) CTAs hold partial sums of a
+// chip; a chip's slots follow the previous chip's.  rng = [first | count].
+static std::vector<int> det_ranges(const std::vector<int> &cnt, int G, long long &total) {
+  const int nc = (int)cnt.size();
+  std::vector<int> r(2 * (size_t)nc);
+  total = 0;
+  for (int c = 0; c < nc; ++c) {
+    const int k = G > 0 ? std::min(cnt[c], G) : cnt[c];
+    r[c] = (int)total;
+    r[nc + c] = k;
+    total += k;
+  }
+  return r;
+}
+
+// Buffers of deterministic solves for preconditioner pc (allocated once per
+// workspace and layout).
+template <typename T, int S>
+static int det_setup(SolveWS *ws, int pc) {
+  if (ws->det_spmm && ws->det_pc == pc) return BLOCKOA_OK;
+  const int nc = ws->n_chips;
+  auto upload = [&](int **dst, const std::vector<int> &v) -> cudaError_t {
+    cudaError_t e = ws_alloc(ws, dst, sizeof(int) * v.size());
+    return e == cudaSuccess ? cudaMemcpy(*dst, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice) : e;
+  };
+  long long ns = 0, nu = 0, nz = 0, nsm = 0;
+  const std::vector<int> rs = det_ranges(ws->h_ucnt, ws->grid_spmm, ns);
+  const bool zl = pc == 2 || pc == 3;
+  const std::vector<int> ru = zl ? det_ranges(ws->h_zcnt, ws->grid_zupdate, nu) : det_ranges(ws->h_ucnt, ws->grid_update, nu);
+  const std::vector<int> rz = det_ranges(ws->h_zcnt, ws->grid_z2, nz);
+  std::vector<int> rsm(2 * (size_t)nc);   // elementwise units: one slot per unit, in unit order
+  for (int c = 0; c < nc; ++c) {
+    rsm[c] = (int)nsm;
+    rsm[nc + c] = ws->h_scnt[c];
+    nsm += ws->h_scnt[c];
+  }
+  const size_t upd_n = pc == 3 ? S : (size_t)S * S + S;
+  BLOCKOA_CUDA(ws_alloc(ws, &ws->det_spmm, sizeof(double) * std::max<long long>(ns, 1) * 2 * S * S));
+  BLOCKOA_CUDA(ws_alloc(ws, &ws->det_upd, sizeof(double) * std::max<long long>(nu, 1) * upd_n));
+  BLOCKOA_CUDA(ws_alloc(ws, &ws->det_z2, sizeof(double) * std::max<long long>(nz, 1) * S * S));
+  BLOCKOA_CUDA(ws_alloc(ws, &ws->det_small, sizeof(double) * std::max<long long>(nsm, 1) * S));
+  BLOCKOA_CUDA(upload(&ws->det_rng_s, rs));
+  BLOCKOA_CUDA(upload(&ws->det_rng_u, ru));
+  BLOCKOA_CUDA(upload(&ws->det_rng_z, rz));
+  BLOCKOA_CUDA(upload(&ws->det_rng_small, rsm));
+  ws->det_pc = pc;
+  return BLOCKOA_OK;
 }
 
 template <typename T, int S>
@@ -1840,6 +2025,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
         cnt[units[i].chip] += 1;
         uend[units[i].chip] = (int)i + 1;
       }
+      ws->h_ucnt = cnt;
       BLOCKOA_CUDA(ws_alloc(ws, &ws->unit_count, sizeof(int) * (size_t)nc));
       BLOCKOA_CUDA(cudaMemcpy(ws->unit_count, cnt.data(), sizeof(int) * (size_t)nc, cudaMemcpyHostToDevice));
       BLOCKOA_CUDA(ws_alloc(ws, &ws->chip_unit_end, sizeof(int) * (size_t)nc));
@@ -1884,6 +2070,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
         BLOCKOA_CUDA(cudaMemcpy(ws->zunits, zu.data(), sizeof(Unit) * zu.size(), cudaMemcpyHostToDevice));
       BLOCKOA_CUDA(ws_alloc(ws, &ws->zunit_count, sizeof(int) * (size_t)nc));
       BLOCKOA_CUDA(cudaMemcpy(ws->zunit_count, zcnt.data(), sizeof(int) * (size_t)nc, cudaMemcpyHostToDevice));
+      ws->h_zcnt = zcnt;
       BLOCKOA_CUDA(ws_alloc(ws, &ws->zchip_unit_end, sizeof(int) * (size_t)nc));
       BLOCKOA_CUDA(cudaMemcpy(ws->zchip_unit_end, zend.data(), sizeof(int) * (size_t)nc, cudaMemcpyHostToDevice));
       ws->grid_zupdate = (int)std::max<long long>(1, std::min<long long>(ws->n_zunits, (long long)std::max(occ_z, 1) * nsm));
@@ -1899,6 +2086,8 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     ws->grid_pupd = (int)std::min<long long>(ws->n_units, (long long)std::max(occ_p, 1) * nsm);
     std::vector<Unit> us = make_units(op, 256);   // element-wise set-up kernels: ~512 CTAs on a 131K-cell chip
     ws->n_units_small = (int)us.size();
+    ws->h_scnt.assign(nc, 0);
+    for (const Unit &u : us) ws->h_scnt[u.chip] += 1;
     BLOCKOA_CUDA(ws_alloc(ws, &ws->units_small, sizeof(Unit) * us.size()));
     BLOCKOA_CUDA(cudaMemcpy(ws->units_small, us.data(), sizeof(Unit) * us.size(), cudaMemcpyHostToDevice));
     BLOCKOA_CUDA(cudaMallocHost((void **)&ws->h_state, sizeof(ChipSolveState) * nc));
@@ -1926,9 +2115,22 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     return BLOCKOA_ERR_INVALID;
   }
   // the float64 form always factors by Cholesky in kernels of their own
-  const bool ch = prec == BLOCKOA_FP64 || o->small_solve == BLOCKOA_SMALL_FP64_CHOLESKY;
+  // deterministic solves run the float64 Cholesky small solves (the tails
+  // of the sweep form add to the accumulators while other CTAs flush)
+  const bool det = o->deterministic != 0;
+  const bool ch = prec == BLOCKOA_FP64 || o->small_solve == BLOCKOA_SMALL_FP64_CHOLESKY || det;
+  if (det) {
+    const int rc = det_setup<T, S>(ws, pc);
+    if (rc) return rc;
+  }
 
   SmallArgs sa;
+  sa.det_spmm = det ? ws->det_spmm : nullptr;
+  sa.det_upd = det ? ws->det_upd : nullptr;
+  sa.det_z2 = det ? ws->det_z2 : nullptr;
+  sa.det_base = ws->det_rng_s;
+  sa.det_ubase = ws->det_rng_u;
+  sa.det_zbase = ws->det_rng_z;
   sa.state = ws->state; sa.gram = ws->gram; sa.rho = ws->rho; sa.wg = ws->wg; sa.rn2 = ws->rn2;
   sa.target2 = ws->target2; sa.ginv = ws->ginv; sa.dsc = ws->dsc; sa.rank = ws->rank;
   sa.rinv = ws->rinv; sa.perm = ws->perm;
@@ -1941,7 +2143,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
   // Build (or reuse) the graph of `check_every` iterations.
   if (!ws->graph || ws->graph_iters != check_every || ws->graph_maxiter != maxiter ||
       ws->graph_s != s || ws->graph_tol != tol || ws->graph_pc != pc || ws->graph_ch != (int)ch ||
-      ws->graph_diag != sa.diag) {
+      ws->graph_diag != sa.diag || ws->graph_det != (int)det) {
     if (ws->graph) { cudaGraphExecDestroy(ws->graph); ws->graph = nullptr; }
     cudaGraph_t graph = nullptr;
     for (int i = 0; i <= kMaxLoopKernels; ++i)
@@ -1974,6 +2176,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     ws->graph_pc = pc;
     ws->graph_ch = (int)ch;
     ws->graph_diag = sa.diag;
+    ws->graph_det = (int)det;
   }
 
   // Inputs: padded B and X0, ||B_j||^2.
@@ -1982,8 +2185,11 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
   pad_cols_kernel<<<eb, 256, 0, st>>>(B, ws->B64, n, s, S);
   pad_cols_kernel<<<eb, 256, 0, st>>>(o->x0, ws->X64, n, s, S);
   BLOCKOA_CUDA(cudaMemsetAsync(ws->bn2, 0, sizeof(double) * nc * S, st));
-  col_norms_kernel<S><<<ws->n_units_small, 256, 0, st>>>(ws->units_small, ws->B64, ws->bn2);
+  col_norms_kernel<S><<<ws->n_units_small, 256, 0, st>>>(ws->units_small, ws->B64, ws->bn2,
+                                                          det ? ws->det_small : nullptr);
   BLOCKOA_CUDA(cudaGetLastError());
+  if (det) BLOCKOA_CUDA(launch_ordered_reduce(ws->det_small, S, ws->det_rng_small, ws->det_rng_small + nc, nullptr,
+                                              nc, 4, S, ws->bn2, nullptr, 0, st));
   std::vector<double> bn2((size_t)nc * S);
   BLOCKOA_CUDA(read_small(ws->h_small, ws->bn2, sizeof(double) * nc * S, st));
   BLOCKOA_CUDA(cudaStreamSynchronize(st));
@@ -2000,7 +2206,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       BLOCKOA_CUDA(cudaMemcpyAsync(ws->rn64, ws->bn2, sizeof(double) * nc * S, cudaMemcpyDeviceToDevice, st));
     } else {
       BLOCKOA_CUDA(cudaMemsetAsync(ws->rn64, 0, sizeof(double) * nc * S, st));
-      int rc = launch_residual64(op, ws->B64, ws->X64, ws->R64, S, ws->rn64, st);
+      int rc = launch_residual64(op, ws->B64, ws->X64, ws->R64, S, ws->rn64, st, det);
       if (rc) return rc;
     }
     BLOCKOA_CUDA(read_small(ws->h_small, ws->rn64, sizeof(double) * nc * S, st));
@@ -2109,7 +2315,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
         BLOCKOA_CUDA(cudaStreamSynchronize(st));
         op->inject_chip = -1;
       }
-      g_launches += (long long)loop_kernels(ch, pc) * check_every;
+      g_launches += (long long)(loop_kernels(ch, pc) + (det ? (pc == 3 ? 3 : 2) : 0)) * check_every;
       for (int i = 0; i < loop_kernels(ch, pc); ++i) add_launches(op, loop_class(ch, pc, i), check_every);
       BLOCKOA_CUDA(cudaGraphLaunch(ws->graph, st));
       BLOCKOA_CUDA(read_small(ws->h_state, ws->state, sizeof(ChipSolveState) * nc, st));
@@ -2174,6 +2380,7 @@ extern "C" int blockoa_block_solve(blockoa_operator *op, const double *B, double
     return BLOCKOA_ERR_INVALID;
   if (opts->small_solve != BLOCKOA_SMALL_AUTO && opts->small_solve != BLOCKOA_SMALL_FP64_CHOLESKY)
     return BLOCKOA_ERR_INVALID;
+  if (opts->deterministic != 0 && opts->deterministic != 1) return BLOCKOA_ERR_INVALID;
   if (s == 0) {
     for (int c = 0; c < op->n_chips; ++c) stats[c].status = BLOCKOA_OK;
     return BLOCKOA_OK;

@@ -175,7 +175,7 @@ int launch_pair_check(const blockoa_operator *op, const void *T, const void *q, 
 // R = B - A X (float64) on a padded block [n_total][S]; also accumulates
 // per-chip column norms ||R_j||^2 into rn2 [chip][S] (must be zeroed).
 int launch_residual64(const blockoa_operator *op, const double *B, const double *X, double *R,
-                      int S, double *rn2, cudaStream_t st);
+                      int S, double *rn2, cudaStream_t st, bool det = false);
 // ratio[chip][j] = ||B_j - A X_j|| / ||B_j|| for float64 blocks [n_total][s], s <= 64.
 int launch_residual_ratio(const blockoa_operator *op, const double *B, const double *X, int s,
                           double *ratio, cudaStream_t st);
@@ -184,6 +184,12 @@ int launch_apply_block64(const blockoa_operator *op, const double *U, double *AU
 
 // blockcg.cu
 void free_solve_ws(void *ws);
+// Deterministic reduction of per-unit or per-CTA partial sums (slots) into
+// per-chip accumulators (ordered_reduce_kernel); state may be null (every
+// chip).
+cudaError_t launch_ordered_reduce(const double *slots, int n, const int *begin, const int *count,
+                                  const ChipSolveState *state, int n_chips, int mode, int S, double *a, double *b,
+                                  int diag, cudaStream_t st);
 
 struct CombineEpi;   // noise.cuh
 

@@ -71,6 +71,16 @@ struct SmallArgs {
   int n_chips;
   int tail;         // 1: the Gram kernels' last CTAs solve (mixed form, sweep)
   int diag;         // 1: independent columns -- only the diagonals of Gamma, rho, W accumulate
+  // deterministic solves: the loop kernels store each CTA's partial sums in
+  // a slot (nullptr: atomics into the accumulators above); a chip's slots
+  // start at det_base / det_ubase / det_zbase[chip] (the stencil pass, the
+  // update, the second z-line step), one per CTA that takes a unit of it
+  double *det_spmm;         // [slot][2 S^2]: P^T Q, then P^T R
+  double *det_upd;          // [slot][S^2 + S] or [slot][S]: W (when the update forms it), then ||R_j||^2
+  double *det_z2;           // [slot][S^2]: W of the second z-line step
+  const int *det_base;
+  const int *det_ubase;
+  const int *det_zbase;
   int s;            // caller's columns (for deflation counts)
   int maxiter;      // limit on total iterations per chip
   double tol;       // deflation threshold on scaled pivots

@@ -538,7 +538,8 @@ template <int S>
 __global__ void __launch_bounds__(256)
 residual64_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ chips,
                   const double *__restrict__ g, const double *__restrict__ B,
-                  const double *__restrict__ X, double *__restrict__ R, double *__restrict__ rn2) {
+                  const double *__restrict__ X, double *__restrict__ R, double *__restrict__ rn2,
+                  double *__restrict__ slot) {
   constexpr int TPC = S / 2;           // threads per cell
   constexpr int CPB = 256 / TPC;       // cells per pass
   const Unit u = units[blockIdx.x];
@@ -579,8 +580,13 @@ residual64_kernel(const Unit *__restrict__ units, const ChipDev *__restrict__ ch
   if (threadIdx.x < TPC) {
     double a0 = 0.0, a1 = 0.0;
     for (int t = threadIdx.x; t < 256; t += TPC) { a0 += red[2 * t]; a1 += red[2 * t + 1]; }
-    atomicAdd(&rn2[(long long)u.chip * S + j], a0);
-    atomicAdd(&rn2[(long long)u.chip * S + j + 1], a1);
+    if (slot) {   // deterministic: this unit's partial sums, reduced in a fixed order afterwards
+      slot[(long long)blockIdx.x * S + j] = a0;
+      slot[(long long)blockIdx.x * S + j + 1] = a1;
+    } else {
+      atomicAdd(&rn2[(long long)u.chip * S + j], a0);
+      atomicAdd(&rn2[(long long)u.chip * S + j + 1], a1);
+    }
   }
 }
 
@@ -712,32 +718,51 @@ int launch_residual_ratio(const blockoa_operator *op, const double *B, const dou
 }
 
 int launch_residual64(const blockoa_operator *op, const double *B, const double *X, double *R,
-                      int S, double *rn2, cudaStream_t st) {
+                      int S, double *rn2, cudaStream_t st, bool det) {
   std::vector<Unit> units = make_units(op, 512);   // float64-bound: enough CTAs for every SM
   blockoa_operator *mop = const_cast<blockoa_operator *>(op);
-  void *d_units = nullptr;
+  void *d_units = nullptr, *d_slot = nullptr, *d_range = nullptr;
   int rc = pool_alloc(mop, &d_units, sizeof(Unit) * units.size(), st);
   if (rc) return rc;
+  auto done = [&](int code) {
+    pool_free(d_units, st);
+    pool_free(d_slot, st);
+    pool_free(d_range, st);
+    return code;
+  };
+  std::vector<int> range(2 * (size_t)op->n_chips, 0);   // first unit and unit count of each chip
+  if (det) {
+    for (size_t k = units.size(); k-- > 0;) range[units[k].chip] = (int)k;
+    for (const Unit &u : units) range[op->n_chips + u.chip] += 1;
+    rc = pool_alloc(mop, &d_slot, sizeof(double) * units.size() * S, st);
+    if (!rc) rc = pool_alloc(mop, &d_range, sizeof(int) * range.size(), st);
+    if (rc) return done(rc);
+  }
   cudaError_t e = cudaMemcpyAsync(d_units, units.data(), sizeof(Unit) * units.size(),
                                   cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && det)
+    e = cudaMemcpyAsync(d_range, range.data(), sizeof(int) * range.size(), cudaMemcpyHostToDevice, st);
   cudaEvent_t ev = nullptr;
   if (e == cudaSuccess) {
     const unsigned nb = (unsigned)units.size();
     const Unit *du = (const Unit *)d_units;
+    double *sl = (double *)d_slot;
     time_begin(mop, st, &ev);
     g_launches += 1;
     switch (S) {
-      case 8: residual64_kernel<8><<<nb, 256, 0, st>>>(du, op->d_chips, op->g64, B, X, R, rn2); break;
-      case 16: residual64_kernel<16><<<nb, 256, 0, st>>>(du, op->d_chips, op->g64, B, X, R, rn2); break;
-      case 32: residual64_kernel<32><<<nb, 256, 0, st>>>(du, op->d_chips, op->g64, B, X, R, rn2); break;
-      case 64: residual64_kernel<64><<<nb, 256, 0, st>>>(du, op->d_chips, op->g64, B, X, R, rn2); break;
-      default: pool_free(d_units, st); return BLOCKOA_ERR_INVALID;
+      case 8: residual64_kernel<8><<<nb, 256, 0, st>>>(du, op->d_chips, op->g64, B, X, R, rn2, sl); break;
+      case 16: residual64_kernel<16><<<nb, 256, 0, st>>>(du, op->d_chips, op->g64, B, X, R, rn2, sl); break;
+      case 32: residual64_kernel<32><<<nb, 256, 0, st>>>(du, op->d_chips, op->g64, B, X, R, rn2, sl); break;
+      case 64: residual64_kernel<64><<<nb, 256, 0, st>>>(du, op->d_chips, op->g64, B, X, R, rn2, sl); break;
+      default: return done(BLOCKOA_ERR_INVALID);
     }
     e = cudaGetLastError();
     time_end(mop, st, KC_RESIDUAL64, ev);
+    if (e == cudaSuccess && det)
+      e = launch_ordered_reduce(sl, S, (const int *)d_range, (const int *)d_range + op->n_chips, nullptr,
+                                op->n_chips, 4, S, rn2, nullptr, 0, st);
   }
-  pool_free(d_units, st);
-  return cuda_status(e, "residual64");
+  return done(cuda_status(e, "residual64"));
 }
 
 }  // namespace blockoa

@@ -657,6 +657,56 @@ def test_independent_columns_are_single_rhs_cg(precision):
         assert stb.iters < st.iters, (stb.iters, st.iters)
 
 
+@pytest.mark.parametrize("precision,pc", [(bo.MIXED, bo.PRECOND_ZLINE2), (bo.MIXED, bo.PRECOND_JACOBI),
+                                          (bo.FP64, bo.PRECOND_NONE)])
+def test_deterministic_solves_repeat_bitwise(precision, pc):
+    """deterministic=True: static unit schedules and every partial sum
+    reduced in a fixed order -- two solves of the same inputs give the same
+    bits and the same iteration counts, on a batch of uneven chips with
+    several units each, and reach the dense solution."""
+    chips = small_chips()[1:] + [synth.random_small_chip(112, 48, 40, 6), synth.random_small_chip(113, 37, 21, 5)]
+    rng = np.random.default_rng(83)
+    for s in (12, 32):
+        Bs = [rng.uniform(0, 1e-2, (c.n, s)) for c in chips]
+        runs = []
+        for _ in range(2):
+            Xs, stats = _solve(chips, Bs, s, precision, 1e-11, precond=pc, deterministic=True)
+            runs.append((Xs, [(st.status, st.iters, st.refine_steps) for st in stats]))
+        assert runs[0][1] == runs[1][1], (s, runs[0][1], runs[1][1])
+        for a, b in zip(runs[0][0], runs[1][0]):
+            assert np.array_equal(a, b)
+        for c, ch in enumerate(chips):
+            assert runs[0][1][c][0] == bo.OK
+            ref = np.linalg.solve(orc.assemble(ch).toarray(), Bs[c])
+            assert np.all(relcols(runs[0][0][c], ref) < 1e-8), (s, c)
+
+
+def test_deterministic_headline_chip_repeats_bitwise():
+    """The 128 x 128 x 8 chip at s = 32 in the chosen form, deterministic:
+    three solves, identical bits and iteration counts."""
+    w = synth.single_chip_workload(128, 128, 8, s=32, M=4)
+    op = bo.assemble(w.chips)
+    B = torch.empty(op.n_total * 32, dtype=torch.float64, device="cuda")
+    bo.build_rhs(op, pl.upload(w).density, B, 32)
+    outs = []
+    for _ in range(3):
+        U = torch.empty_like(B)
+        st = bo.block_solve(op, B, U, 32, rtol=1e-6, deterministic=True, **pl.CHOSEN_SOLVE)
+        assert st[0].status == bo.OK and st[0].relres_max <= 1e-6
+        outs.append((U.cpu().numpy(), st[0].iters, st[0].refine_steps))
+    for U, it, rf in outs[1:]:
+        assert it == outs[0][1] and rf == outs[0][2]
+        assert np.array_equal(U, outs[0][0])
+
+
+def test_deterministic_flag_is_validated():
+    op = bo.assemble([synth.random_small_chip(8, 5, 4, 2)])
+    B = torch.ones(op.n_total * 4, dtype=torch.float64, device="cuda")
+    X = torch.empty_like(B)
+    with pytest.raises(bo.BlockoaError):
+        bo.block_solve(op, B, X, 4, precision=bo.MIXED, deterministic=2)
+
+
 def test_zline_needs_columns_that_fit_a_tile():
     chip = synth.random_small_chip(106, 3, 3, 70)          # 70 cells in z > the 64-cell tile at s = 64
     op = bo.assemble([chip])
