@@ -681,7 +681,11 @@ def run_suite(peaks, flush):
                  "ms": {"assemble_rhs_solve": round(solve_ms, 3), "combine_apply": round(fields_ms, 3),
                         "total": round(total, 3)},
                  "iters": {"min": min(its), "median": statistics.median(its), "max": max(its)},
-                 "slowest_chip": {"index": slow, "cells": op.sizes[slow]["n"], "iters": its[slow]},
+                 "slowest_chip": {"index": slow, "cells": op.sizes[slow]["n"], "iters": its[slow],
+                                  # block iterations run after 90% of the chips had converged
+                                  "iters_after_p90": int(max(its) - np.percentile(its, 90)),
+                                  "share_of_iterations_after_p90":
+                                      round(float((max(its) - np.percentile(its, 90)) / max(max(its), 1)), 3)},
                  "relres_max": max(x.relres_max for x in st), "max_e_pair": worst,
                  "roofline_apply": hbm_entry("apply_fields", kt, n, s, chunk, peaks),
                  "roofline_combine": hbm_entry("combine_tc", kt, n, s, chunk, peaks),

@@ -359,9 +359,12 @@ struct UnitSched {
   const int *chip_unit_end;   // [chip] index of the first unit past the chip
   int *work;                  // [0] next unit, [1] CTAs finished (zero between launches)
   int stat;                   // 1: static schedule (deterministic solves): CTA b takes units b, b + G, ...
+  const int *chip_unit_count; // [chip] units of the chip (chips' units are contiguous, largest chip first)
 };
 // First unit of chip c.
-__device__ __forceinline__ int unit0(const UnitSched &us, int c) { return c > 0 ? us.chip_unit_end[c - 1] : 0; }
+__device__ __forceinline__ int unit0(const UnitSched &us, int c) {
+  return us.chip_unit_end[c] - us.chip_unit_count[c];
+}
 
 // Thread 0's scheduling registers: the unit fetched ahead, and the last
 // chip whose active flag it read, as 2 chip + flag (flags do not change
@@ -1834,9 +1837,9 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
         slots, n, rng, rng + ws->n_chips, ws->state, ws->n_chips, mode, S, a, b, sa.diag);
     chain = false;
   };
-  const UnitSched us_s{ws->units, ws->n_units, ws->chip_unit_end, ws->work, det};
-  const UnitSched us_u{ws->units, ws->n_units, ws->chip_unit_end, ws->work + 2, det};
-  const UnitSched us_p{ws->units, ws->n_units, ws->chip_unit_end, ws->work + 4, 0};
+  const UnitSched us_s{ws->units, ws->n_units, ws->chip_unit_end, ws->work, det, ws->unit_count};
+  const UnitSched us_u{ws->units, ws->n_units, ws->chip_unit_end, ws->work + 2, det, ws->unit_count};
+  const UnitSched us_p{ws->units, ws->n_units, ws->chip_unit_end, ws->work + 4, 0, ws->unit_count};
   launch_chained(spmm_gram_kernel<T, S>, ws->grid_spmm, 256, spmm_smem<T, S>(), st, chain,
                  us_s, op->d_chips, g, (const T *)ws->P, (const T *)ws->R, (T *)ws->Q, sa);
   launched();
@@ -1848,7 +1851,7 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
   }
   mark();
   if constexpr (PCM == 2 || PCM == 3) {
-    const UnitSched us_z{ws->zunits, ws->n_zunits, ws->zchip_unit_end, ws->work + 2, det};
+    const UnitSched us_z{ws->zunits, ws->n_zunits, ws->zchip_unit_end, ws->work + 2, det, ws->zunit_count};
     const T *zinv = sizeof(T) == 4 ? (const T *)op->zinv32 : (const T *)op->zinv64;
     launch_chained(update_zline_kernel<T, S, PCM == 3>, ws->grid_zupdate, 256, zupdate_smem<T, S>(), st, chain,
                    us_z, op->d_chips, g, zinv, (const T *)ws->P, (const T *)ws->Q, (T *)ws->D, (T *)ws->R,
@@ -1857,7 +1860,7 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
       launched();
       reduce(ws->det_upd, S, ws->det_rng_u, 1, ws->rn2, nullptr);
       mark();
-      const UnitSched us_z2{ws->zunits, ws->n_zunits, ws->zchip_unit_end, ws->work + 6, det};
+      const UnitSched us_z2{ws->zunits, ws->n_zunits, ws->zchip_unit_end, ws->work + 6, det, ws->zunit_count};
       launch_chained(zline2_kernel<T, S, false>, ws->grid_z2, 256, zline2_smem<T, S>(), st, chain,
                      us_z2, op->d_chips, g, zinv, (const T *)ws->Zb, (const T *)ws->R, (const T *)ws->Q,
                      (T *)ws->Zb2, sa);
@@ -2017,7 +2020,19 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
     if (op->tune_tpu > 0) tpu = op->tune_tpu;   // chosen by blockoa_autotune or the caller
     ws->tune_tpu = op->tune_tpu;
     ws->tune_ztpu = op->tune_ztpu;
-    std::vector<Unit> units = make_units(op, tpu * G::TC);
+    // chips largest first (longest processing time first): a launch's last
+    // units are small ones, so its CTAs finish together
+    std::vector<int> order(nc);
+    for (int c = 0; c < nc; ++c) order[c] = c;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return op->chips[a].n > op->chips[b].n; });
+    std::vector<Unit> units;
+    {
+      const std::vector<Unit> by_chip = make_units(op, tpu * G::TC);
+      std::vector<std::vector<Unit>> per(nc);
+      for (const Unit &u : by_chip) per[u.chip].push_back(u);
+      for (int c : order) units.insert(units.end(), per[c].begin(), per[c].end());
+    }
     ws->n_units = (int)units.size();
     {
       std::vector<int> cnt(nc, 0), uend(nc, 0);
@@ -2046,7 +2061,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       long long ztpu = ztiles / (16LL * std::max(occ_z, 1) * nsm);
       ztpu = std::min<long long>(std::max<long long>(ztpu, 1), 8);
       if (op->tune_ztpu > 0) ztpu = op->tune_ztpu;
-      for (int c = 0; c < nc; ++c) {
+      for (int c : order) {
         const ChipDev &cd = op->chips[c];
         if (cd.nz > G::TC) continue;   // no z-line units: such chips cannot use PRECOND_ZLINE
         const int xt = G::TC / cd.nz;
@@ -2293,7 +2308,7 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
                                                    (const T *)ws->R, (T *)ws->P, (T *)ws->Zb);
         g_launches += 1;
         if (pc == 3) {   // two-step: P = Z = M^-1 (2 R - A M^-1 R)
-          const UnitSched us_z2{ws->zunits, ws->n_zunits, ws->zchip_unit_end, ws->work + 6};
+          const UnitSched us_z2{ws->zunits, ws->n_zunits, ws->zchip_unit_end, ws->work + 6, 0, ws->zunit_count};
           zline2_kernel<T, S, true><<<ws->grid_z2, 256, zline2_smem<T, S>(), st>>>(
               us_z2, op->d_chips, gco, zinv, (const T *)ws->Zb, (const T *)ws->R, (const T *)ws->Q,
               (T *)ws->P, sa);
