@@ -35,6 +35,7 @@ def main():
     p.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     p.add_argument("--precond", choices=["none", "jacobi", "zline", "zline2"], default="jacobi")
     p.add_argument("--small", choices=["auto", "fp64-cholesky"], default="auto")
+    p.add_argument("--deterministic", action="store_true", help="static schedules, ordered reductions")
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--reps", type=int, default=10)
     a = p.parse_args()
@@ -60,7 +61,8 @@ def main():
     def call():
         if a.call == "solve":
             stats[:] = bo.block_solve(op, B, U, s, rtol=1e-6, precision=prec, precond=pc,
-                                      small_solve=bo.SMALL_AUTO if a.small == "auto" else bo.SMALL_FP64_CHOLESKY)
+                                      small_solve=bo.SMALL_AUTO if a.small == "auto" else bo.SMALL_FP64_CHOLESKY,
+                                      deterministic=a.deterministic)
         elif a.call == "apply":
             bo.apply_operator(op, T, q, M, prec)
         else:

@@ -102,7 +102,7 @@ def test_chosen_form_throughput_mode_full_size(chip128):
 
 def test_double_float_small_solves_give_the_same_verified_pairs(chip128):
     w = chip128
-    kw = dict(pl.CHOSEN_SOLVE, small_solve=bo.SMALL_AUTO)
+    kw = dict(pl.CHOSEN_SOLVE, small_solve=bo.SMALL_AUTO, deterministic=False)
     res = pl.run(w, rtol=w.rtol, **kw)
     st = res.stats[0]
     assert st.status == bo.OK and st.relres_max <= w.rtol, st

@@ -691,7 +691,7 @@ def test_deterministic_headline_chip_repeats_bitwise():
     outs = []
     for _ in range(3):
         U = torch.empty_like(B)
-        st = bo.block_solve(op, B, U, 32, rtol=1e-6, deterministic=True, **pl.CHOSEN_SOLVE)
+        st = bo.block_solve(op, B, U, 32, rtol=1e-6, **dict(pl.CHOSEN_SOLVE, deterministic=True))
         assert st[0].status == bo.OK and st[0].relres_max <= 1e-6
         outs.append((U.cpu().numpy(), st[0].iters, st[0].refine_steps))
     for U, it, rf in outs[1:]:
