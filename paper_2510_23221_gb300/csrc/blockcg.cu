@@ -498,7 +498,8 @@ struct TileWalk {
     const int G = (int)gridDim.x;
     while (u < us.n_units) {
       const Unit un = us.units[u];
-      if (state[un.chip].active) {
+      // the chip being walked is active (flags do not change while the kernel runs)
+      if (un.chip == chip || state[un.chip].active) {
         ui = u; chip = un.chip; base = un.begin; end = un.end;
         return;
       }
@@ -989,8 +990,9 @@ p_update_tc_kernel(const UnitSched us, ChipSolveState *__restrict__ state, const
   cp_async_commit();
   int bchip = -1, fail_chip = -1;
   uint32_t phase = 0;
-  for (int k = 0; cur.valid(us); ++k, cur.next<TCP_M>(us, state)) {
+  for (int k = 0; cur.valid(us); ++k) {
     const int sc = k & 1;
+    const TileWalk after = pre;   // tile k + 1: the walker staged one tile ahead already found it
     if (pre.valid(us)) {
       stage(sc ^ 1, pre.base, pre.end);
       pre.next<TCP_M>(us, state);
@@ -1068,6 +1070,7 @@ p_update_tc_kernel(const UnitSched us, ChipSolveState *__restrict__ state, const
             *reinterpret_cast<const float4 *>(tZ + SG::off(row, q));
     }
     __syncthreads();   // stage sc, the planes and TMEM are reused
+    cur = after;
   }
   cp_async_wait<0>();
   if (fail_chip >= 0 && t == 0) {   // MMA completion timed out: report, let it land, release TMEM
