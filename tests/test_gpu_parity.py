@@ -658,7 +658,8 @@ def test_independent_columns_are_single_rhs_cg(precision):
 
 
 @pytest.mark.parametrize("precision,pc", [(bo.MIXED, bo.PRECOND_ZLINE2), (bo.MIXED, bo.PRECOND_JACOBI),
-                                          (bo.FP64, bo.PRECOND_NONE)])
+                                          (bo.MIXED, bo.PRECOND_ZLINE), (bo.FP64, bo.PRECOND_NONE),
+                                          (bo.FP64, bo.PRECOND_ZLINE2)])
 def test_deterministic_solves_repeat_bitwise(precision, pc):
     """deterministic=True: static unit schedules and every partial sum
     reduced in a fixed order -- two solves of the same inputs give the same
@@ -666,7 +667,7 @@ def test_deterministic_solves_repeat_bitwise(precision, pc):
     several units each, and reach the dense solution."""
     chips = small_chips()[1:] + [synth.random_small_chip(112, 48, 40, 6), synth.random_small_chip(113, 37, 21, 5)]
     rng = np.random.default_rng(83)
-    for s in (12, 32):
+    for s in (5, 12, 32):
         Bs = [rng.uniform(0, 1e-2, (c.n, s)) for c in chips]
         runs = []
         for _ in range(2):
@@ -679,6 +680,24 @@ def test_deterministic_solves_repeat_bitwise(precision, pc):
             assert runs[0][1][c][0] == bo.OK
             ref = np.linalg.solve(orc.assemble(ch).toarray(), Bs[c])
             assert np.all(relcols(runs[0][0][c], ref) < 1e-8), (s, c)
+
+
+def test_deterministic_independent_columns():
+    """Independent columns (only the Grams' diagonals) in the deterministic
+    mode: bitwise repetition and the dense solution."""
+    chip = synth.random_small_chip(114, 23, 17, 4)
+    s = 20
+    rng = np.random.default_rng(14)
+    B = np.stack([synth.rect_power_map(rng, chip.nx, chip.ny) for _ in range(s)])
+    Bc = orc.rhs(chip, B)
+    dense = np.linalg.solve(orc.assemble(chip).toarray(), Bc)
+    for precision in (bo.MIXED, bo.FP64):
+        runs = [_solve([chip], [Bc], s, precision, 1e-10, independent=True, deterministic=True) for _ in range(2)]
+        (X0,), (s0,) = runs[0]
+        (X1,), (s1,) = runs[1]
+        assert s0.status == bo.OK and (s0.iters, s0.refine_steps) == (s1.iters, s1.refine_steps)
+        assert np.array_equal(X0, X1)
+        assert np.all(relcols(X0, dense) < 1e-7)
 
 
 def test_deterministic_headline_chip_repeats_bitwise():
