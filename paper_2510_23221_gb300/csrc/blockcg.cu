@@ -189,6 +189,41 @@ template <typename T, int S>
 __device__ __forceinline__ void gram_range(T *acc, const T *A, const T *B, int i0, int j0,
                                            int cbeg, int nc) {
   using G = BK<T, S>;
+  if constexpr (sizeof(T) == 4 && S == 32 && G::LD % 32 == 0) {
+    if ((cbeg & 31) == 0 && (nc & 31) == 0) {
+      // Same products and order, addresses without per-load swizzle arithmetic:
+      // rows i0..i0+3 (j0..j0+3) share the swizzle key (row / 4) & 7, and for
+      // a range starting at a multiple of 32 cells the 16-byte unit of cell
+      // step u is (u & ~7) + ((u & 7) ^ key).
+      const int kA = (i0 >> 2) & 7, kB = (j0 >> 2) & 7;
+      const float *a0 = A + i0 * G::LD + cbeg, *b0 = B + j0 * G::LD + cbeg;
+      float2 pr[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) pr[e] = make_float2(0.f, 0.f);
+#pragma unroll 1
+      for (int u8 = 0; u8 < nc / 4; u8 += 8)
+#pragma unroll
+      for (int uu = 0; uu < 8; ++uu) {
+        const int oa = (u8 + (uu ^ kA)) * 4, ob = (u8 + (uu ^ kB)) * 4;
+        float a[4][4], b[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          vload<float>(a[q], a0 + q * G::LD + oa);
+          vload<float>(b[q], b0 + q * G::LD + ob);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            pr[q * 4 + r] = __ffma2_rn(make_float2(a[q][0], a[q][1]), make_float2(b[r][0], b[r][1]), pr[q * 4 + r]);
+            pr[q * 4 + r] = __ffma2_rn(make_float2(a[q][2], a[q][3]), make_float2(b[r][2], b[r][3]), pr[q * 4 + r]);
+          }
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) acc[e] += pr[e].x + pr[e].y;
+      return;
+    }
+  }
   if constexpr (sizeof(T) == 4) {
     float2 pr[16];
 #pragma unroll
