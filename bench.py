@@ -453,10 +453,11 @@ def run_ours(args):
     if fp64_z2:
         fp64_z2["form"] = "float64, two-step z-line block CG, float64 fields (the chosen preconditioner)"
     dfloat = variant(dict(CHOSEN, small_solve=bo.SMALL_AUTO, deterministic=False), torch.float32,
-                     max(args.plain_steps, 2))
+                     max(args.plain_steps, 2) if args.plain_steps > 0 else 0)
     if dfloat:
         dfloat["form"] = "chosen form with double-float (~48-bit) s x s sweeps in the Gram kernels' tails"
-    detf = variant(dict(CHOSEN, deterministic=True), torch.float32, max(args.plain_steps, 3))
+    detf = variant(dict(CHOSEN, deterministic=True), torch.float32,
+                   max(args.plain_steps, 3) if args.plain_steps > 0 else 0)
     if detf:
         detf["form"] = ("chosen form, deterministic (static unit schedules, partial sums reduced in a fixed "
                         "order): the iteration counts and bits repeat from step to step")
