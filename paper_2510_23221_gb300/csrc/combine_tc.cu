@@ -31,6 +31,7 @@ namespace blockoa {
 constexpr int TC_M = 128;       // cells per tile (MMA M, TMEM lanes)
 constexpr int TC_N = 256;       // fields per chunk (MMA N, TMEM columns)
 constexpr int TC_THREADS = 128;
+static_assert(TC_N % 64 == 0, "the drain takes 64 tensor-memory columns per wait");
 
 __host__ __device__ inline int tc_kpad(int s) { return (s + 15) / 16 * 16; }
 
@@ -188,39 +189,45 @@ combine_tc_kernel(const TcTile *__restrict__ tiles, const ChipDev *__restrict__ 
     const bool valid = cell < tile.ncells;
     const int f0 = q * TC_N;
     float *out = tbase + cell;
+    // 64 columns per wait: two tensor-memory loads in flight together
 #pragma unroll 1
-    for (int cc = 0; cc < TC_N / 32; ++cc) {
-      uint32_t r[32];
-      BLOCKOA_TMEM_LD32(tmem + ((uint32_t)(warp * 32) << 16) + cc * 32, r);
+    for (int c2 = 0; c2 < TC_N / 32; c2 += 2) {
+      uint32_t rr[2][32];
+      BLOCKOA_TMEM_LD32(tmem + ((uint32_t)(warp * 32) << 16) + c2 * 32, rr[0]);
+      BLOCKOA_TMEM_LD32(tmem + ((uint32_t)(warp * 32) << 16) + (c2 + 1) * 32, rr[1]);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      const int fb = f0 + cc * 32;
-      if (valid) {
-        if (epi.inv_sum) {   // normalised weights of Eq. 5: (U C)_m / sum_j C_jm
-          const double *inv = epi.inv_sum + (long long)tile.chip * M + fb;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        uint32_t (&r)[32] = rr[hh];
+        const int fb = f0 + (c2 + hh) * 32;
+        if (valid) {
+          if (epi.inv_sum) {   // normalised weights of Eq. 5: (U C)_m / sum_j C_jm
+            const double *inv = epi.inv_sum + (long long)tile.chip * M + fb;
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (fb + i < M) r[i] = __float_as_uint(__uint_as_float(r[i]) * (float)__ldg(inv + i));
+          }
+          if (nz.amp > 0.0 && nz.kind == NOISE_UNIFORM) {   // epsilon of Eq. 5, 4 fields per block (fb % 32 == 0)
+#pragma unroll   // constant indices keep r[] in registers
+            for (int g = 0; g < 8; ++g) {
+              float eps[4];
+              noise4f(nz, tile.cell0 + cell, (fb + 4 * g) / 4, eps);
+#pragma unroll
+              for (int i = 0; i < 4; ++i) r[4 * g + i] = __float_as_uint(__uint_as_float(r[4 * g + i]) + eps[i]);
+            }
+          } else if (nz.amp > 0.0) {   // Gaussian epsilon, 2 fields per generator block
+#pragma unroll
+            for (int g = 0; g < 16; ++g) {
+              float eps[2];
+              gauss2f(nz, tile.cell0 + cell, (fb + 2 * g) / 2, eps);
+#pragma unroll
+              for (int i = 0; i < 2; ++i) r[2 * g + i] = __float_as_uint(__uint_as_float(r[2 * g + i]) + eps[i]);
+            }
+          }
 #pragma unroll
           for (int i = 0; i < 32; ++i)
-            if (fb + i < M) r[i] = __float_as_uint(__uint_as_float(r[i]) * (float)__ldg(inv + i));
+            if (fb + i < M) __stcs(out + (long long)(fb + i) * ch.n, __uint_as_float(r[i]));
         }
-        if (nz.amp > 0.0 && nz.kind == NOISE_UNIFORM) {   // epsilon of Eq. 5, 4 fields per block (fb % 32 == 0)
-#pragma unroll   // constant indices keep r[] in registers
-          for (int g = 0; g < 8; ++g) {
-            float eps[4];
-            noise4f(nz, tile.cell0 + cell, (fb + 4 * g) / 4, eps);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) r[4 * g + i] = __float_as_uint(__uint_as_float(r[4 * g + i]) + eps[i]);
-          }
-        } else if (nz.amp > 0.0) {   // Gaussian epsilon, 2 fields per generator block
-#pragma unroll
-          for (int g = 0; g < 16; ++g) {
-            float eps[2];
-            gauss2f(nz, tile.cell0 + cell, (fb + 2 * g) / 2, eps);
-#pragma unroll
-            for (int i = 0; i < 2; ++i) r[2 * g + i] = __float_as_uint(__uint_as_float(r[2 * g + i]) + eps[i]);
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < 32; ++i)
-          if (fb + i < M) __stcs(out + (long long)(fb + i) * ch.n, __uint_as_float(r[i]));
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
