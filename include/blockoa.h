@@ -418,7 +418,7 @@ int blockoa_pair_check(const blockoa_operator *op, const void *T, const void *q,
  * BLOCKOA_STATIC_PAIR_MAX returns ERR_INVALID before anything is launched
  * (blockoa_last_error() says why).  The first call on a device looks up
  * that array's device address (once per device, with that device
- * current), so make the first call before any stream capture.  All calls
+ * current).  All calls
  * on a device share the array, which keeps the last call's contents; each
  * call clears it on its stream first, so calls that overlap on the GPU
  * (different streams, or concurrent host threads) race and must be
