@@ -1256,9 +1256,13 @@ __device__ __forceinline__ void zline_solve_tile(T *sV, const T *sE, const T *sF
 // solves run in shared memory (one thread per (column of the block, x
 // position)), Z is stored for the P update, and W += Q^T Z.
 // TWO (two-step z-line): Z1 = M^-1 R_new is stored and ||R_j||^2 flushed; the
-// second step, W and the beta tail belong to zline2_kernel.
+// second step, W and the beta tail belong to zline2_kernel.  The float32
+// two-step form at 32 columns runs three CTAs per SM (80 registers, ~100
+// bytes of spills; measured 38.4 -> 37.5 us a launch on a 131K-cell chip);
+// the one-step form spills ~0.5 KB at 80 and keeps two, as do the other
+// widths (not measured at three).
 template <typename T, int S, bool TWO>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && TWO && S == 32) ? 3 : 2)
 update_zline_kernel(const UnitSched us, const ChipDev *__restrict__ chips, const T *__restrict__ g,
                     const T *__restrict__ zinv, const T *__restrict__ P, const T *__restrict__ Q,
                     T *__restrict__ X, T *__restrict__ R, T *__restrict__ Zb, const SmallArgs A) {
@@ -1710,7 +1714,7 @@ struct SolveWS {
   int n_units = 0;
   int grid_spmm = 0, grid_update = 0, grid_pupd = 0;   // persistent CTAs per loop kernel
   Unit *zunits = nullptr;       // column-tile units of the z-line update
-  int n_zunits = 0, grid_zupdate = 0;
+  int n_zunits = 0, grid_zupdate = 0, grid_zupdate2 = 0;   // one-step, two-step z-line update
   int *zunit_count = nullptr, *zchip_unit_end = nullptr;
   bool zline_ok = false;        // every chip has nz <= TC
   void *Zb = nullptr;           // z-line Z = M^-1 R in the loop's precision
@@ -1891,7 +1895,8 @@ static void launch_iteration(const blockoa_operator *op, SolveWS *ws, const Smal
   if constexpr (PCM == 2 || PCM == 3) {
     const UnitSched us_z{ws->zunits, ws->n_zunits, ws->zchip_unit_end, ws->work + 2, det, ws->zunit_count};
     const T *zinv = sizeof(T) == 4 ? (const T *)op->zinv32 : (const T *)op->zinv64;
-    launch_chained(update_zline_kernel<T, S, PCM == 3>, ws->grid_zupdate, 256, zupdate_smem<T, S>(), st, chain,
+    launch_chained(update_zline_kernel<T, S, PCM == 3>, PCM == 3 ? ws->grid_zupdate2 : ws->grid_zupdate, 256,
+                   zupdate_smem<T, S>(), st, chain,
                    us_z, op->d_chips, g, zinv, (const T *)ws->P, (const T *)ws->Q, (T *)ws->D, (T *)ws->R,
                    (T *)ws->Zb, sa);
     if constexpr (PCM == 3) {   // second step: Zb2 = M^-1 (2 R - A Zb), W = Q^T Zb2, beta tail
@@ -1966,7 +1971,8 @@ static int det_setup(SolveWS *ws, int pc) {
   long long ns = 0, nu = 0, nz = 0, nsm = 0;
   const std::vector<int> rs = det_ranges(ws->h_ucnt, ws->grid_spmm, ns);
   const bool zl = pc == 2 || pc == 3;
-  const std::vector<int> ru = zl ? det_ranges(ws->h_zcnt, ws->grid_zupdate, nu) : det_ranges(ws->h_ucnt, ws->grid_update, nu);
+  const std::vector<int> ru = zl ? det_ranges(ws->h_zcnt, pc == 3 ? ws->grid_zupdate2 : ws->grid_zupdate, nu)
+                                 : det_ranges(ws->h_ucnt, ws->grid_update, nu);
   const std::vector<int> rz = det_ranges(ws->h_zcnt, ws->grid_z2, nz);
   std::vector<int> rsm(2 * (size_t)nc);   // elementwise units: one slot per unit, in unit order
   for (int c = 0; c < nc; ++c) {
@@ -2127,6 +2133,10 @@ static int solve_impl(blockoa_operator *op, const double *B, double *X, int s,
       BLOCKOA_CUDA(ws_alloc(ws, &ws->zchip_unit_end, sizeof(int) * (size_t)nc));
       BLOCKOA_CUDA(cudaMemcpy(ws->zchip_unit_end, zend.data(), sizeof(int) * (size_t)nc, cudaMemcpyHostToDevice));
       ws->grid_zupdate = (int)std::max<long long>(1, std::min<long long>(ws->n_zunits, (long long)std::max(occ_z, 1) * nsm));
+      int occ_z2u = 1;
+      BLOCKOA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_z2u, update_zline_kernel<T, S, true>, 256,
+                                                                 zupdate_smem<T, S>()));
+      ws->grid_zupdate2 = (int)std::max<long long>(1, std::min<long long>(ws->n_zunits, (long long)std::max(occ_z2u, 1) * nsm));
       BLOCKOA_CUDA(ws_alloc(ws, &ws->Zb, sizeof(T) * (size_t)n * S));
       BLOCKOA_CUDA(ws_alloc(ws, &ws->Zb2, sizeof(T) * (size_t)n * S));
       int occ_z2 = 1;
