@@ -8,7 +8,10 @@
 //   D Gamma D = L L^T by diagonal-pivoted Cholesky, stopping at the first
 //   pivot <= tol (deflation), then
 //   alpha = Gamma^+ rho and beta = -Gamma^+ W on the kept columns by
-//   forward and backward substitution; deflated rows are zero.
+//   forward and backward substitution; deflated rows are zero.  In the
+//   float32 loop beta is the product -Gamma^+ W instead, with Gamma^+
+//   formed column by column by the same substitution (the float32 P update
+//   cannot resolve the difference; the Galerkin conditions rest on alpha).
 // A substitution leaves a small-system residual of the order of the
 // rounding of Gamma itself, so the Galerkin conditions P^T R = 0 hold to
 // float64 accuracy and the iteration tracks the exact-arithmetic one down to
@@ -18,10 +21,11 @@
 //
 // chol_alpha_kernel runs one CTA per (chip, column j): every CTA of a chip
 // factors the same matrix with the same instruction sequence (bitwise the
-// same factor), then solves its column of alpha; CTA j = 0 publishes the
-// substitution factors and clears W and ||R||^2 (read by the previous beta
-// solve).  chol_beta_kernel solves one column of beta per single-warp CTA;
-// CTA 0 also clears Gamma and rho and tests convergence.
+// same factor), then solves its column of alpha (and, in the float32
+// loop, its column of Gamma^+); CTA j = 0 publishes the substitution
+// factors (float64 loop) and clears W and ||R||^2 (read by the previous
+// beta solve).  chol_beta_kernel forms one column of beta per CTA; CTA 0
+// also clears Gamma and rho and tests convergence.
 #pragma once
 
 #include "smallsolve.cuh"
@@ -90,7 +94,9 @@ __device__ __forceinline__ int chol_select(const double *dg, const int *gone, do
 // Solve column j of Gamma_KK x = rhs_K with the pivot-order substitution
 // factors F (F[i][k] = L[i][k] / L[k][k] below the diagonal, L[k][i] / L[k][k]
 // above, zero on it) and write sign * D x into column j of out (zero rows
-// for deflated columns).  One warp; lane i holds rows i + 32 q.
+// for deflated columns).  rhs == nullptr stands for the unit vector e_j, so
+// that out receives column j of Gamma^+.  One warp; lane i holds rows
+// i + 32 q.
 template <typename T, int S, int LDF>
 __device__ __forceinline__ void chol_solve_column(const double *F, const double *rv, const double *d,
                                                   const int *perm, int r, const double *rhs, int j,
@@ -103,7 +109,7 @@ __device__ __forceinline__ void chol_solve_column(const double *F, const double 
   for (int q = 0; q < RL; ++q) {
     const int i = lane + 32 * q;
     pr[q] = i < r ? perm[i] : -1;
-    y[q] = i < r ? d[pr[q]] * rhs[(long long)pr[q] * S + j] : 0.0;
+    y[q] = i < r ? d[pr[q]] * (rhs ? rhs[(long long)pr[q] * S + j] : (pr[q] == j ? 1.0 : 0.0)) : 0.0;
   }
   // L z = y: y_i -= F[i][k] y_k (i > k), then z_i = y_i / L[i][i]
   for (int k = 0; k < r; ++k) {
@@ -354,8 +360,10 @@ __global__ void __launch_bounds__(kCholThreads) chol_alpha_kernel(SmallArgs A) {
   }
   __syncthreads();
   if (j == 0) {   // publish the factor for the beta solve, update the chip state
-    double *F = reinterpret_cast<double *>(A.ginv) + (long long)c * S * S;
-    for (int e = t; e < S * S; e += kCholThreads) F[e] = sh.W[e / S][e % S];
+    if constexpr (sizeof(T) != 4) {   // the float32 loop's beta solve reads Gamma^+ instead
+      double *F = reinterpret_cast<double *>(A.ginv) + (long long)c * S * S;
+      for (int e = t; e < S * S; e += kCholThreads) F[e] = sh.W[e / S][e % S];
+    }
     if (t < S) {
       A.rinv[(long long)c * S + t] = t < r ? sh.rv[t] : 0.0;
       reinterpret_cast<double *>(A.dsc)[(long long)c * S + t] = sh.d[t];
@@ -371,19 +379,34 @@ __global__ void __launch_bounds__(kCholThreads) chol_alpha_kernel(SmallArgs A) {
       }
     }
   }
-  if (r == 0 || warp != 0) return;
-  chol_solve_column<T, S, S + 1>(&sh.W[0][0], sh.rv, sh.d, sh.perm, r, A.rho + (long long)c * S * S, j, 1.0,
-                                 reinterpret_cast<T *>(A.alpha) + (long long)c * S * S);
+  if (r == 0) return;
+  if (warp == 0) {
+    chol_solve_column<T, S, S + 1>(&sh.W[0][0], sh.rv, sh.d, sh.perm, r, A.rho + (long long)c * S * S, j, 1.0,
+                                   reinterpret_cast<T *>(A.alpha) + (long long)c * S * S);
+  } else if (sizeof(T) == 4 && warp == 1) {
+    // float32 loop: column j of Gamma^+ by the same substitution, beside
+    // the alpha column (warp 1 issues on its own scheduler), for the beta
+    // product of chol_beta_kernel
+    chol_solve_column<double, S, S + 1>(&sh.W[0][0], sh.rv, sh.d, sh.perm, r, nullptr, j, 1.0,
+                                        reinterpret_cast<double *>(A.ginv) + (long long)c * S * S);
+  }
 }
 
 // beta = -Gamma^+ W, column j; CTA 0 of each chip also clears Gamma and rho
 // and runs the per-column convergence test of the updated residual.  Four
 // warps load the factor (independent loads in flight together), warp 0
-// substitutes.
+// substitutes.  In the float32 loop the factor is replaced by Gamma^+
+// itself, formed column by column by substitution in chol_alpha_kernel
+// (zero outside the kept rows and columns), and warp 0 takes the product
+// -Gamma^+ W_j: independent float64 FMAs instead of the two dependent
+// substitution chains (float64 instructions issue at 1/64 of the float32
+// rate here).
 template <typename T, int S>
 __global__ void __launch_bounds__(kCholThreads) chol_beta_kernel(SmallArgs A) {
+  constexpr int RL = (S + 31) / 32;
+  static_assert(S % 4 == 0, "the product takes four columns per step");
   __shared__ double F[S][S + 1];
-  __shared__ double rv[S], d[S];
+  __shared__ double rv[S], d[S], wj[S];
   __shared__ int perm[S];
   const int c = blockIdx.x / S, j = blockIdx.x % S;
   const int t = threadIdx.x;
@@ -391,19 +414,41 @@ __global__ void __launch_bounds__(kCholThreads) chol_beta_kernel(SmallArgs A) {
   grid_wait_prior();
   ChipSolveState &st = A.state[c];
   if (!st.active) return;
-  const int r = A.rank[c];
   const double *Fg = reinterpret_cast<const double *>(A.ginv) + (long long)c * S * S;
 #pragma unroll 8
   for (int e = t; e < S * S; e += kCholThreads) F[e / S][e % S] = Fg[e];
-  for (int i = t; i < S; i += kCholThreads) {
-    rv[i] = A.rinv[(long long)c * S + i];
-    d[i] = reinterpret_cast<const double *>(A.dsc)[(long long)c * S + i];
-    perm[i] = A.perm[(long long)c * S + i];
+  if constexpr (sizeof(T) == 4) {
+    for (int i = t; i < S; i += kCholThreads) wj[i] = A.wg[(long long)c * S * S + (long long)i * S + j];
+    __syncthreads();
+    if (t < 32) {
+      T *out = reinterpret_cast<T *>(A.beta) + (long long)c * S * S;
+#pragma unroll
+      for (int q = 0; q < RL; ++q) {
+        const int i = t + 32 * q;
+        if (i < S) {
+          double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll 2
+          for (int k = 0; k < S; k += 4) {
+            a0 = __fma_rn(F[i][k], wj[k], a0);
+            a1 = __fma_rn(F[i][k + 1], wj[k + 1], a1);
+            a2 = __fma_rn(F[i][k + 2], wj[k + 2], a2);
+            a3 = __fma_rn(F[i][k + 3], wj[k + 3], a3);
+          }
+          out[(long long)i * S + j] = (T)(0.0 - ((a0 + a1) + (a2 + a3)));
+        }
+      }
+    }
+  } else {
+    for (int i = t; i < S; i += kCholThreads) {
+      rv[i] = A.rinv[(long long)c * S + i];
+      d[i] = reinterpret_cast<const double *>(A.dsc)[(long long)c * S + i];
+      perm[i] = A.perm[(long long)c * S + i];
+    }
+    __syncthreads();
+    if (t < 32)
+      chol_solve_column<T, S, S + 1>(&F[0][0], rv, d, perm, A.rank[c], A.wg + (long long)c * S * S, j, -1.0,
+                                     reinterpret_cast<T *>(A.beta) + (long long)c * S * S);
   }
-  __syncthreads();
-  if (t < 32)
-    chol_solve_column<T, S, S + 1>(&F[0][0], rv, d, perm, r, A.wg + (long long)c * S * S, j, -1.0,
-                                   reinterpret_cast<T *>(A.beta) + (long long)c * S * S);
   if (j != 0) return;
   for (int e = t; e < S * S; e += kCholThreads) {
     A.gram[(long long)c * S * S + e] = 0.0;
