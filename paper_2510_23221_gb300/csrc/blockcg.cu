@@ -290,12 +290,6 @@ __device__ __forceinline__ double f2d_exact(float f) {
   return __longlong_as_double((long long)(sgn | ((unsigned long long)(ex + 896) << 52) | (m << 29)));
 }
 
-// Add a compensated float32 pair hi + lo (|lo| <= ulp(hi) / 2) to a float64
-// accumulator: two atomics of exact conversions, no float64 arithmetic.
-__device__ __forceinline__ void atomic_add_pair(double *dst, float hi, float lo) {
-  atomicAdd(dst, f2d_exact(hi) + f2d_exact(lo));
-}
-
 // Where a flush puts its per-entry partial sums: added to the chip's
 // float64 accumulator by atomics (entry e at acc[e * stride]), or, in a
 // deterministic solve, stored in the CTA's slot (entry e at slot[e]) for a
